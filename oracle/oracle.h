@@ -1,0 +1,131 @@
+/*
+ * oracle.h -- CPU oracle for the bit-sliced Gillespie method
+ *             (Castellana & Lacoste, "Parallelization of Gillespie algorithm
+ *             based on binary words", arXiv 2412.16613).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  The product path
+ * (libbitssa) never links, loads or calls it, and the two share no code.
+ *
+ * What it computes: one run at a time, a plain serial Gillespie simulation of
+ * a conserved mass-action network with integer counts (Sec. 2-3), driven by a
+ * fixed counter-based random stream so that any single run can be recomputed
+ * on its own:
+ *
+ *   run j lives in group g = j / 32 at lane l = j % 32;
+ *   word k of the (g, step s, attempt a, tag) stream is element k % 4 of
+ *     Philox4x32-10(key = (seed lo, seed hi),
+ *                   ctr = (g, s lo32, (s hi16) | a << 16 | tag << 24, k / 4));
+ *   n   = sum_{i<K} bit_l(w_i) 2^i, redrawn from attempt a+1 while n >= Lambda_int
+ *         (a uniform integer in [0, Lambda_int), Sec. 3 step 5(i) and step a);
+ *   tau = -log(u) / Lambda from the whole words w_K, w_{K+1} of attempt 0
+ *         (Eq. equation-tau, with the uniformisation rate of Eq. equation-z):
+ *         fp64 u = (x + 1) 2^-53 with x = w_{K+1} << 21 | w_K >> 11; the fp32
+ *         modes take u = ((w_{K+1} >> 8) + 1) 2^-24, the top 24 of those bits;
+ *   the fired reaction is the smallest r with n < S_r = sum_{p<=r} h_p
+ *         (the CDF walk of Sec. 3 step 5 / Fig. 2); none fires when n >= S_R
+ *         (a ghost reaction, Eqs. 4-6);
+ *   non-unit rates: reaction r is kept iff U < T_r = floor(k_r / k_max 2^q), U
+ *         the q-bit number whose bit q-1-i is bit_l(w_{K+2+i}) of attempt 0.
+ *
+ * Everything here is fp64 (or fp32 where a precision mode asks for it),
+ * compiled with -ffp-contract=off so that x86-64 and aarch64 hosts agree.
+ */
+#ifndef BITSSA_ORACLE_H
+#define BITSSA_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_SPECIES 8
+#define ORC_MAX_REACTIONS 8
+
+/* precision modes of the waiting-time clock */
+#define ORC_P64 0        /* u from 53 bits, tau = -log(u)/Lambda, double sum */
+#define ORC_P32_KAHAN 1  /* u from 24 bits, tau = -logf(u)*(float)(1/Lambda), Kahan float sum */
+#define ORC_P32_D64ACC 2 /* float tau as above, double accumulator */
+
+/* status codes */
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ETIMEOUT -5
+#define ORC_ERANGE -6    /* 64 redraw attempts exhausted, or a count left its range */
+
+typedef struct {
+  int32_t n_species;        /* S, 1..ORC_MAX_SPECIES */
+  int32_t n_reactions;      /* R, 1..ORC_MAX_REACTIONS */
+  const int32_t* reactants; /* [R][S] reactant multiplicities, order <= 2 */
+  const int32_t* products;  /* [R][S] product multiplicities */
+  const double* rates;      /* [R] k_r >= 0, max > 0 */
+  int64_t n_tot;            /* conserved total count, >= 1 */
+  uint64_t seed;            /* Philox key */
+  int32_t precision;        /* ORC_P64 | ORC_P32_KAHAN | ORC_P32_D64ACC */
+  int32_t thin_bits;        /* q, 1..64 */
+  double t_end;             /* stop before the first event later than t_end */
+  const double* snap_times; /* [n_snap] ascending, <= t_end (may be NULL if n_snap == 0) */
+  int32_t n_snap;
+  int64_t step_budget;      /* max steps per run, 0 = unlimited */
+} orc_problem;
+
+/* Derived constants of a problem, computed from their definitions. */
+typedef struct {
+  uint64_t lambda_int;      /* integer uniformisation bound: sum_r h_r <= lambda_int */
+  int32_t K;                /* random planes for n: bit length of lambda_int */
+  double k_max;
+  double lambda;            /* k_max * lambda_int */
+  int32_t thin_always[ORC_MAX_REACTIONS]; /* 1: T_r = 2^q, always kept */
+  uint64_t thin_T[ORC_MAX_REACTIONS];     /* T_r when not always kept */
+  int32_t any_thinning;
+} orc_derived;
+
+/* Per-run result. */
+typedef struct {
+  int64_t final_counts[ORC_MAX_SPECIES];
+  double t_abs;        /* time of the event that made every real propensity 0; +inf if none */
+  double t_last;       /* time of the last committed step */
+  int32_t outcome;     /* -1 not absorbed; >= 0 the one species left; -2 absorbed with several */
+  int32_t status;
+  int64_t steps;       /* committed steps, null ones included */
+  int64_t reactions;   /* real reactions */
+  int64_t redraws;     /* extra attempts spent on n >= lambda_int */
+  double margin;       /* smallest relative gap between a snapshot / t_end and the
+                          committed event times on either side of it */
+} orc_result;
+
+int orc_derive(const orc_problem* p, orc_derived* d);
+
+/* Philox4x32-10 block function (Salmon et al., SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Word k of a stream, as defined above. */
+uint32_t orc_stream_word(uint64_t seed, uint64_t group, uint64_t step, uint32_t attempt,
+                         uint32_t tag, uint32_t k);
+
+/* h_r(state) for every r, and the reaction the CDF walk picks for integer n
+ * (-1 = none).  Exposed for the exhaustive tests of the selection rule. */
+int orc_propensities(const orc_problem* p, const int64_t* state, int64_t* h);
+int32_t orc_select(const orc_problem* p, const int64_t* state, uint64_t n);
+
+/* One run.  snap_counts: [n_snap][S] or NULL. */
+int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index,
+            const int64_t* init, orc_result* out, int64_t* snap_counts);
+
+/* Many runs on n_threads host threads.  Run i is global run run_ids[i] (or
+ * first_run + i when run_ids is NULL).  init is [S] (init_per_run = 0) or
+ * [n_runs][S].  Outputs are per run, indexed by i; any may be NULL except out.
+ * snap_counts is [n_snap][n_runs][S].  Returns the first non-OK status. */
+int orc_run_many(const orc_problem* p, int64_t first_run, const int64_t* run_ids, int64_t n_runs,
+                 const int64_t* init, int32_t init_per_run, orc_result* out,
+                 int64_t* snap_counts, int32_t n_threads);
+
+/* Enantiomeric-excess bin of (L, D): 64 bins over [-1, 1] by floor(64 L / (L + D)),
+ * the top edge folded into bin 63; bin 64 holds L + D == 0. */
+int32_t orc_ee_bin(int64_t L, int64_t D);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

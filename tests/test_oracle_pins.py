@@ -1,0 +1,455 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: an
+independent Philox implementation, exhaustive enumeration of the reaction
+rule, the chemical master equation solved by expm / linear algebra, closed
+forms of single-reaction networks, exact one-step probabilities, and the
+invariants of the Frank model (Sec. 2).
+"""
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from tests import _master_equation as me
+
+FRANK_REAC = [[1, 0, 1], [0, 1, 1], [1, 1, 0]]
+FRANK_PROD = [[2, 0, 0], [0, 2, 0], [0, 0, 2]]
+
+
+def frank_h(L, D, A):
+    """Eq. equation-as: a1 = A L, a2 = A D, a3 = L D (k_A = k_I = 1)."""
+    return [A * L, A * D, L * D]
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: the oracle's implementation against Triton's, run on the CPU
+# by Triton's interpreter (an implementation written by other people).
+# --------------------------------------------------------------------------
+def test_philox_matches_triton_interpreter(orc):
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    ctrs = rng.integers(0, 2**32, size=(64, 4), dtype=np.uint64)
+    ctrs[0] = 0
+    ctrs[1] = 2**32 - 1
+    seed = 0x0123456789ABCDEF
+    code = textwrap.dedent("""
+        import os, sys, json
+        os.environ["TRITON_INTERPRET"] = "1"
+        import torch, triton, triton.language as tl
+        @triton.jit
+        def k(c_ptr, o_ptr, seed, N: tl.constexpr):
+            i = tl.arange(0, N)
+            c0 = tl.load(c_ptr + 4 * i + 0)
+            c1 = tl.load(c_ptr + 4 * i + 1)
+            c2 = tl.load(c_ptr + 4 * i + 2)
+            c3 = tl.load(c_ptr + 4 * i + 3)
+            a, b, c, d = tl.philox(seed, c0, c1, c2, c3)
+            tl.store(o_ptr + 4 * i + 0, a)
+            tl.store(o_ptr + 4 * i + 1, b)
+            tl.store(o_ptr + 4 * i + 2, c)
+            tl.store(o_ptr + 4 * i + 3, d)
+        ctr = torch.tensor(json.loads(sys.argv[1]), dtype=torch.int64).to(torch.uint32)
+        out = torch.zeros_like(ctr)
+        k[(1,)](ctr, out, int(sys.argv[2]), N=ctr.shape[0])
+        print(json.dumps(out.to(torch.int64).tolist()))
+    """)
+    import json
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", code, json.dumps(ctrs.tolist()), str(seed)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        pytest.skip(f"triton interpreter unavailable: {r.stderr[-300:]}")
+    theirs = json.loads(r.stdout.strip().splitlines()[-1])
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for c, t in zip(ctrs.tolist(), theirs):
+        assert orc.philox4x32_10(c, key) == t
+
+
+def test_stream_word_layout(orc):
+    """Word k of a stream is element k % 4 of Philox call k // 4 on the documented counter."""
+    seed, g, s = 0xDEADBEEFCAFEF00D, 12345, (7 << 32) | 99
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for attempt, tag in [(0, 0), (3, 0), (0, 1)]:
+        for k in range(10):
+            ctr = [g, s & 0xFFFFFFFF, ((s >> 32) & 0xFFFF) | (attempt << 16) | (tag << 24), k // 4]
+            assert orc.stream_word(seed, g, s, attempt, tag, k) == orc.philox4x32_10(ctr, key)[k % 4]
+
+
+# --------------------------------------------------------------------------
+# The uniformisation constant (Eq. equation-z) and its generalisation.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,K", [(64, 11), (1024, 19), (10000, 26), (65536, 31)])
+def test_lambda_frank_is_Z(orc, N, K):
+    d = orc.derive(orc.frank(), N)
+    assert d.lambda_int == N * (N - 1) // 2          # Eq. equation-z
+    assert d.K == K and 2 ** (K - 1) <= d.lambda_int < 2 ** K
+    assert d.lambda_ == float(N * (N - 1) // 2)
+
+
+def test_lambda_is_a_bound_by_brute_force(orc):
+    """max over all states of sum_r h_r <= lambda_int, with equality for Frank + ghosts."""
+    nets = [
+        (FRANK_REAC, FRANK_PROD),
+        ([[1, 0, 1], [1, 0, 1], [0, 2, 0]], [[2, 0, 0], [0, 1, 1], [1, 1, 0]]),  # pair used twice
+        ([[1, 0, 0], [0, 1, 0], [1, 1, 0]], [[0, 1, 0], [1, 0, 0], [0, 0, 2]]),  # first order
+    ]
+    for reac, prod in nets:
+        net = orc.Network(reac, prod, [1.0] * len(reac))
+        for N in (5, 9, 16):
+            d = orc.derive(net, N)
+            best = max(sum(me.propensity(r, s) for r in reac) for s in me.states(3, N))
+            assert best <= d.lambda_int
+    # Frank: sum of the three real and three ghost propensities is exactly Z for every state
+    for s in me.states(3, 12):
+        L, D, A = s
+        ghosts = L * (L - 1) // 2 + D * (D - 1) // 2 + A * (A - 1) // 2
+        assert sum(frank_h(L, D, A)) + ghosts == 12 * 11 // 2
+
+
+# --------------------------------------------------------------------------
+# The reaction rule: the CDF walk (Sec. 3 step 5, Fig. 2) must give each
+# reaction exactly h_r of the lambda_int integers, ghosts the rest.
+# --------------------------------------------------------------------------
+def test_select_exhaustive_small(orc):
+    net = orc.frank()
+    for N in (2, 3, 7, 12):
+        Z = N * (N - 1) // 2
+        for (L, D, A) in me.states(3, N):
+            counts = [0, 0, 0, 0]
+            for n in range(Z):
+                counts[orc.select(net, (L, D, A), n) + 1] += 1
+            h = frank_h(L, D, A)
+            assert counts[1:] == h
+            assert counts[0] == Z - sum(h)
+
+
+def test_select_boundaries_N64(orc):
+    net = orc.frank()
+    N, Z = 64, 2016
+    for (L, D, A) in me.states(3, N):
+        h = frank_h(L, D, A)
+        S = np.cumsum(h)
+        lo = 0
+        for r in range(3):
+            if h[r]:
+                assert orc.select(net, (L, D, A), lo) == r
+                assert orc.select(net, (L, D, A), S[r] - 1) == r
+            lo = S[r]
+        if S[2] < Z:
+            assert orc.select(net, (L, D, A), S[2]) == -1
+            assert orc.select(net, (L, D, A), Z - 1) == -1
+
+
+def test_propensities_definition(orc):
+    net = orc.frank()
+    for (L, D, A) in me.states(3, 9):
+        assert list(orc.propensities(net, (L, D, A))) == frank_h(L, D, A)
+
+
+# --------------------------------------------------------------------------
+# One step: the drawn integer is uniform on [0, lambda_int), so the first
+# reaction has probability k_r h_r / (k_max lambda_int) exactly.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rates", [(1.0, 1.0, 1.0), (1.0, 0.5, 0.25), (0.7, 2.0, 1.3)])
+def test_first_step_probabilities(orc, rates):
+    net = orc.frank(*rates)
+    init = (16, 16, 32)
+    n = 200_000
+    r = orc.run(net, init, n, seed=11, step_budget=1, check=False)
+    assert np.all((r["run_status"] == orc.OK) | (r["run_status"] == orc.ETIMEOUT))
+    delta = r["final_counts"] - np.array(init)
+    fired = np.full(n, 3)
+    fired[(delta == [1, 0, -1]).all(1)] = 0
+    fired[(delta == [0, 1, -1]).all(1)] = 1
+    fired[(delta == [-1, -1, 2]).all(1)] = 2
+    assert np.all((fired == 3) == (delta == 0).all(1))
+    Z = 64 * 63 // 2
+    kmax = max(rates)
+    h = frank_h(16, 16, 32)
+    p = [rates[i] * h[i] / (kmax * Z) for i in range(3)]
+    p.append(1 - sum(p))
+    obs = np.bincount(fired, minlength=4)
+    chi2, pval = stats.chisquare(obs, np.array(p) * n)
+    assert pval > 1e-4, (obs, np.array(p) * n)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_waiting_time_exponential(orc, precision):
+    """Eq. equation-tau: tau ~ Exp(Lambda), one clock per 32-lane group."""
+    net = orc.frank()
+    N = 64
+    Z = N * (N - 1) // 2
+    groups = 40_000
+    r = orc.run(net, (16, 16, 32), run_ids=np.arange(groups) * 32, seed=3, step_budget=1,
+                precision=precision, check=False)
+    tau = r["t_last"] * Z
+    assert abs(tau.mean() - 1.0) < 4.5 / math.sqrt(groups)
+    assert stats.kstest(tau, "expon").pvalue > 1e-4
+    # lanes of one group share the clock
+    r2 = orc.run(net, (16, 16, 32), run_ids=np.arange(8) * 32 + 5, seed=3, step_budget=1,
+                 precision=precision, check=False)
+    assert np.array_equal(r2["t_last"], r["t_last"][:8])
+
+
+def test_redraw_rate(orc):
+    """n >= lambda_int is redrawn: extra attempts per step are geometric with p = 1 - Z / 2^K."""
+    net = orc.frank()
+    r = orc.run(net, (16, 16, 32), 4096, seed=5, t_end=np.inf)
+    p = 1 - 2016 / 2048
+    steps = r["steps"].sum()
+    expected = steps * p / (1 - p)
+    assert abs(r["redraws"].sum() - expected) < 5 * math.sqrt(expected)
+
+
+# --------------------------------------------------------------------------
+# The chemical master equation, N_tot = 12 (91 states).
+# --------------------------------------------------------------------------
+def _frank_me(N, rates=(1.0, 1.0, 1.0)):
+    return me.generator(FRANK_REAC, FRANK_PROD, list(rates), N)
+
+
+@pytest.mark.parametrize("lane", [0, 17])
+def test_master_equation_distribution(orc, lane):
+    N, init = 12, (3, 3, 6)
+    st, index, Q = _frank_me(N)
+    snaps = [0.02, 0.05, 0.1, 0.2, 0.4]
+    runs = 40_000
+    # one lane per group: groups draw from independent counters
+    r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32 + lane, seed=21, t_end=0.5,
+                snap_times=snaps)
+    p0 = np.zeros(len(st))
+    p0[index[init]] = 1.0
+    for s, t in enumerate(snaps):
+        p = me.distribution(Q, p0, t)
+        obs = np.zeros(len(st))
+        for c in r["snap_counts"][s]:
+            obs[index[tuple(int(x) for x in c)]] += 1
+        exp = p * runs
+        big = exp >= 5
+        o = np.append(obs[big], obs[~big].sum())
+        e = np.append(exp[big], exp[~big].sum())
+        if e[-1] < 5:
+            o, e = o[:-1], e[:-1]
+            e *= o.sum() / e.sum()
+        stat, pval = stats.power_divergence(o, e, lambda_="log-likelihood")
+        assert pval > 1e-4, (t, pval)
+
+
+def test_master_equation_absorption(orc):
+    """Absorption probabilities and mean absorption time from the fundamental matrix."""
+    N, init = 12, (5, 2, 5)
+    st, index, Q = _frank_me(N)
+    absorbing, B, T, transient = me.absorption(Q)
+    i0 = transient.index(index[init])
+    runs = 40_000
+    r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32, seed=33, t_end=np.inf)
+    assert np.all(r["outcome"] >= 0)
+    for col, a in enumerate(absorbing):
+        survivor = int(np.argmax(st[a]))
+        p = B[i0, col]
+        frac = np.mean(r["outcome"] == survivor)
+        assert abs(frac - p) < 4.5 * math.sqrt(p * (1 - p) / runs) + 1e-12, (st[a], frac, p)
+    se = r["t_abs"].std() / math.sqrt(runs)
+    assert abs(r["t_abs"].mean() - T[i0]) < 4.5 * se
+
+
+# --------------------------------------------------------------------------
+# Closed forms of single-reaction networks.
+# --------------------------------------------------------------------------
+def test_closed_form_inhibition_only(orc):
+    """L+D->2A alone from L = D = m0: T = sum_{m=1}^{m0} Exp(m^2)."""
+    net = orc.Network([[1, 1, 0]], [[0, 0, 2]], [1.0])
+    m0, A0 = 8, 4
+    runs = 40_000
+    r = orc.run(net, (m0, m0, A0), run_ids=np.arange(runs) * 32, seed=44, t_end=np.inf)
+    assert np.all(r["final_counts"] == [0, 0, 2 * m0 + A0])
+    mean = sum(1 / m**2 for m in range(1, m0 + 1))
+    var = sum(1 / m**4 for m in range(1, m0 + 1))
+    assert abs(r["t_abs"].mean() - mean) < 4.5 * math.sqrt(var / runs)
+    assert abs(r["t_abs"].var() - var) < 0.05 * var
+    assert np.all(r["reactions"] == m0)
+
+
+def test_closed_form_autocatalysis_only(orc):
+    """A+L->2L alone from (L0, 0, N-L0): T = sum_{L=L0}^{N-1} Exp(L (N-L))."""
+    net = orc.Network([[1, 0, 1]], [[2, 0, 0]], [1.0])
+    N, L0 = 20, 3
+    runs = 40_000
+    r = orc.run(net, (L0, 0, N - L0), run_ids=np.arange(runs) * 32 + 3, seed=45, t_end=np.inf)
+    assert np.all(r["final_counts"] == [N, 0, 0])
+    rates = [L * (N - L) for L in range(L0, N)]
+    mean = sum(1 / a for a in rates)
+    var = sum(1 / a**2 for a in rates)
+    assert abs(r["t_abs"].mean() - mean) < 4.5 * math.sqrt(var / runs)
+
+
+@pytest.mark.parametrize("init,final", [((1, 1, 0), (0, 0, 2)), ((1, 0, 1), (2, 0, 0))])
+def test_two_molecules_exponential(orc, init, final):
+    runs = 40_000
+    r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32, seed=46, t_end=np.inf)
+    assert np.all(r["final_counts"] == final)
+    assert stats.kstest(r["t_abs"], "expon").pvalue > 1e-4
+
+
+# --------------------------------------------------------------------------
+# Invariants of the Frank model (Sec. 2) and the L <-> D symmetry.
+# --------------------------------------------------------------------------
+def test_frank_invariants_and_symmetry(orc):
+    runs = 20_000
+    snaps = [0.01, 0.05, 0.1, 0.3]
+    r = orc.run(orc.frank(), (16, 16, 32), runs, seed=8, t_end=1e9, snap_times=snaps)
+    fc = r["final_counts"]
+    assert np.all(fc.sum(1) == 64)
+    assert np.all((fc > 0).sum(1) == 1)               # a single species survives
+    assert np.all(r["outcome"] == np.argmax(fc, 1))
+    assert np.all(r["snap_counts"].sum(2) == 64)
+    pL = np.mean(r["outcome"] == 0)
+    pD = np.mean(r["outcome"] == 1)
+    se = math.sqrt((pL + pD) / runs)
+    assert abs(pL - pD) < 4.5 * se
+    for s in range(len(snaps)):
+        L = r["snap_counts"][s, :, 0].astype(float)
+        D = r["snap_counts"][s, :, 1].astype(float)
+        ee = np.where(L + D > 0, (L - D) / np.maximum(L + D, 1), 0.0)
+        assert abs(ee.mean()) < 4.5 * ee.std() / math.sqrt(runs) + 1e-12
+
+
+def test_precision_modes_share_the_trajectory(orc):
+    """The integer stream does not depend on the clock: counts and steps agree across modes."""
+    base = orc.run(orc.frank(), (16, 16, 32), 512, seed=9, t_end=np.inf)
+    for prec in (orc.P32_KAHAN, orc.P32_D64ACC):
+        r = orc.run(orc.frank(), (16, 16, 32), 512, seed=9, t_end=np.inf, precision=prec)
+        assert np.array_equal(r["final_counts"], base["final_counts"])
+        assert np.array_equal(r["steps"], base["steps"])
+        # the fp32 uniform is the top 24 bits of the fp64 one, so the clocks are paired
+        rel = np.abs(r["t_abs"] / base["t_abs"] - 1)
+        assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-3
+
+
+def test_ee_bin_definition(orc):
+    assert orc.ee_bin(0, 0) == 64
+    assert orc.ee_bin(0, 7) == 0          # ee = -1
+    assert orc.ee_bin(7, 0) == 63         # ee = +1 folds into the top bin
+    assert orc.ee_bin(5, 5) == 32         # ee = 0
+    for L in range(0, 40):
+        for D in range(0, 40):
+            if L + D:
+                ee = (L - D) / (L + D)
+                assert orc.ee_bin(L, D) == min(63, math.floor((ee + 1) / 2 * 64 + 1e-12))
+
+
+# --------------------------------------------------------------------------
+# Degenerate cases and errors.
+# --------------------------------------------------------------------------
+def test_degenerate_cases(orc):
+    net = orc.frank()
+    r = orc.run(net, (1, 0, 0), 3, seed=1, t_end=5.0, snap_times=[0.0, 1.0])  # N = 1: no pair
+    assert np.all(r["t_abs"] == 0.0) and np.all(r["outcome"] == 0) and np.all(r["steps"] == 0)
+    assert np.all(r["snap_counts"] == [1, 0, 0])
+    r = orc.run(net, (0, 0, 30), 3, seed=1, t_end=5.0)           # absorbed all-A start
+    assert np.all(r["t_abs"] == 0.0) and np.all(r["outcome"] == 2)
+    r = orc.run(net, (10, 10, 10), 64, seed=1, t_end=0.0, snap_times=[0.0])  # nothing happens by t=0
+    assert np.all(r["final_counts"] == [10, 10, 10]) and np.all(r["steps"] == 0)
+    assert np.all(r["outcome"] == -1) and np.all(np.isinf(r["t_abs"]))
+    assert np.all(r["snap_counts"] == [10, 10, 10])
+    r = orc.run(net, (10, 10, 10), 4, seed=1, t_end=np.inf, step_budget=5, check=False)
+    assert r["status"] == orc.ETIMEOUT and np.all(r["steps"] == 5)
+
+
+@pytest.mark.parametrize("reac,prod,rates", [
+    ([[1, 1, 1]], [[3, 0, 0]], [1.0]),          # order 3
+    ([[1, 0, 1]], [[2, 0, 1]], [1.0]),          # not conserving
+    ([[1, 0, 1]], [[2, 0, 0]], [-1.0]),         # negative rate
+    ([[1, 0, 1]], [[2, 0, 0]], [0.0]),          # no positive rate
+])
+def test_invalid_networks(orc, reac, prod, rates):
+    with pytest.raises(ValueError):
+        orc.derive(orc.Network(reac, prod, rates), 10)
+
+
+def test_invalid_snapshots(orc):
+    with pytest.raises(ValueError):
+        orc.derive(orc.frank(), 10, t_end=1.0, snap_times=[0.5, 0.2])
+    with pytest.raises(ValueError):
+        orc.derive(orc.frank(), 10, t_end=1.0, snap_times=[2.0])
+
+
+# --------------------------------------------------------------------------
+# The paper's printed rules and examples (tests/golden).
+# --------------------------------------------------------------------------
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _appendix_rules():
+    rules = []
+    with open(os.path.join(GOLDEN, "appendix_a_increments.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                r, a, expr = line.split()
+                rules.append((int(r), a, expr))
+    return rules
+
+
+def test_appendix_a_increments_match_products():
+    """App. A (Eqs. equation-a-nobit-1..3): each printed increment, in pre-update counts,
+    equals the change of the recomputed product; unlisted propensities do not change."""
+    nu = {1: (1, 0, -1), 2: (0, 1, -1), 3: (-1, -1, 2)}     # Eq. eq_nu
+
+    def a_all(L, D, A):
+        return {"a1": A * L, "a2": A * D, "a3": L * D, "a4": L * (L - 1) // 2,
+                "a5": D * (D - 1) // 2, "a6": A * (A - 1) // 2}
+
+    rules = _appendix_rules()
+    for N in range(2, 31):
+        for (L, D, A) in me.states(3, N):
+            before = a_all(L, D, A)
+            for r, (dL, dD, dA) in nu.items():
+                if min(L + dL, D + dD, A + dA) < 0:
+                    continue
+                after = a_all(L + dL, D + dD, A + dA)
+                listed = {a: eval(expr, {}, {"L": L, "D": D, "A": A})
+                          for rr, a, expr in rules if rr == r}
+                for name in before:
+                    assert after[name] - before[name] == listed.get(name, 0), (r, name, L, D, A)
+                assert sum(after.values()) == sum(before.values())  # Z is conserved
+
+
+def _golden_examples():
+    vals = {}
+    with open(os.path.join(GOLDEN, "paper_bitwise_examples.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split("=")
+                vals[k.strip()] = [int(x) for x in v.split()]
+    return vals
+
+
+def test_sum_pseudocode_reading():
+    """Sec. 3.1: the printed partial sum s = b1 & b2 cannot give Fig. 1's 1 + 1 = 2;
+    the full-adder sum s = b1 ^ b2 ^ c with the printed carry can."""
+    g = _golden_examples()
+
+    def ripple(x, y, width, printed):
+        c, out = 0, 0
+        for i in range(width):
+            b1, b2 = (x >> i) & 1, (y >> i) & 1
+            s = (b1 & b2) if printed else (b1 ^ b2 ^ c)
+            c = (b2 & (b1 | c)) | (b1 & c)          # the carry as printed
+            out |= s << i
+        return out | (c << width)
+
+    a, b, want = g["fig1_augend"][0], g["fig1_addend"][0], g["fig1_sum"][0]
+    assert ripple(a, b, 1, printed=False) == want
+    assert ripple(a, b, 1, printed=True) != want
+    for x in range(16):
+        for y in range(16):
+            assert ripple(x, y, 4, printed=False) == x + y
+    assert [p & q for p, q in zip(g["and_b1"], g["and_b2"])] == g["and_out"]
