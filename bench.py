@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark of the bit-sliced Gillespie hot path on GB300.
+
+Workload (one "step" = one full pass of the hot path over one batch): Frank's
+model with unit rates, N_tot = 1024 from (L, D, A) = (256, 256, 512), 2^20 runs
+per GPU (32768 groups of 32 runs), seed 0, fp64 clock, t_end = 50, 10
+log-spaced snapshot times 50 * 10^(4 (s - 9) / 9) with the 65-bin
+enantiomeric-excess histogram at each, the absorption time of every run.  Every
+step restarts from t = 0, so all steps do the same work.
+
+Prints one JSON line: lane-reactions/s (real reactions only) as `value`, with
+absorbed runs/s, lane-steps/s, the roofline of the kernel against the
+integer-ALU issue peak, the end-to-end figure through the C ABI with host
+buffers, the one-thread-per-run GPU baseline on the same workload, and the CPU
+oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: launched by torch.distributed.run, one rank per GPU; rank r holds
+runs [r 2^20, (r+1) 2^20) of one ensemble (weak scaling, no data-path
+collective; the per-rank histograms are summed after the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "lane-reactions/s and absorbed runs/s on 1 GB300, bit-sliced vs 1-thread-per-run SSA"
+N_TOT = 1024
+INIT = (256, 256, 512)
+RUNS_PER_GPU = 1 << 20
+SEED = 0
+T_END = 50.0
+N_SNAP = 10
+SNAPS = [T_END * 10.0 ** (4.0 * (s - (N_SNAP - 1)) / (N_SNAP - 1)) for s in range(N_SNAP)]
+L2_BYTES = 129 * 2**20
+SMS = 152
+MAX_SM_MHZ = 2070.0
+
+
+def algorithmic_ops_per_group_step(K: int, b: int) -> int:
+    """Word operations one group step must do (27K + 6b logic plus 20 LOP3 per Philox call
+    for the ceil((K+2)/4) calls of n and tau)."""
+    return 27 * K + 6 * b + 20 * ((K + 2 + 3) // 4)
+
+
+def bit_length(v: int) -> int:
+    return int(v).bit_length()
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int, path: str):
+        self.path, self.proc = path, None
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sample_runs: int, threads: int):
+    """The oracle as it stands, on the host cores, on runs 0..sample_runs-1 of the workload."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.run(oracle.frank(), INIT, sample_runs, seed=SEED, t_end=T_END, snap_times=SNAPS,
+                   threads=threads)
+    dt = time.perf_counter() - t0
+    reactions = int(r["reactions"].sum())
+    return {"value": reactions / dt, "unit": "lane-reactions/s", "cores": threads, "kind": "oracle",
+            "sample": f"runs 0..{sample_runs - 1} of the workload (all snapshots, to absorption or t_end), "
+                      f"{dt:.1f} s wall on {threads} threads",
+            "absorbed_runs_per_s": int((r["outcome"] >= 0).sum()) / dt, "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle on the same workload and metric, bounded samples."""
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    per_step = args.ref_runs
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.run(oracle.frank(), INIT, 64, seed=SEED, t_end=T_END, snap_times=SNAPS, threads=threads)
+    total_react, total_abs, total_t = 0, 0, 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.run(oracle.frank(), INIT, per_step, first_run=k * per_step, seed=SEED, t_end=T_END,
+                       snap_times=SNAPS, threads=threads)
+        total_t += time.perf_counter() - t0
+        total_react += int(r["reactions"].sum())
+        total_abs += int((r["outcome"] >= 0).sum())
+    value = total_react / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "lane-reactions/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": workload_config(world),
+            "absorbed_runs_per_s": total_abs / total_t,
+            "cpu_baseline": {"value": value, "unit": "lane-reactions/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} runs per step of the workload (runs k*{per_step}.. for "
+                                       f"step k), host threads"},
+            "e2e": {"value": value, "unit": "lane-reactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(world):
+    return {"workload": f"frank_N{N_TOT}_{INIT[0]}-{INIT[1]}-{INIT[2]}_runs{RUNS_PER_GPU}xgpu_tend{T_END:g}"
+                        f"_snap{N_SNAP}log_p64",
+            "model": "Frank (A+L->2L, A+D->2D, L+D->2A), k=(1,1,1)", "N_tot": N_TOT, "init": list(INIT),
+            "runs": RUNS_PER_GPU * world, "runs_per_gpu": RUNS_PER_GPU, "groups_per_gpu": RUNS_PER_GPU // 32,
+            "seed": SEED, "t_end": T_END, "snapshots": SNAPS, "precision": "P64 (product clock)",
+            "global_batch": RUNS_PER_GPU * world, "parallelism": f"replicas x{world} (run shards)",
+            "l2": "L2 flushed between timed steps (256 MiB write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-runs", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=8192)
+    ap.add_argument("--no-baselines", action="store_true", help="skip the K7 and CPU legs")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0)
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import paper_2412_16613_gb300 as pkg
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.build()
+    pkg.use_torch_allocator()
+    stream = torch.cuda.current_stream()
+    opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
+                                  block_size=args.block, first_run=rank * RUNS_PER_GPU)
+    ctx = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
+                         RUNS_PER_GPU, SEED, opt)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        pkg.ssa_run(ctx, T_END, SNAPS)
+    barrier()
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    reactions = absorbed = lane_steps = group_steps = 0
+    barrier()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k)  # L2 flush, outside the kernel's event pair
+        ev[k][0].record(stream)
+        pkg.ssa_run(ctx, T_END, SNAPS)
+        ev[k][1].record(stream)
+        c = pkg.ssa_fetch(ctx, pkg.SSA_FIELD_COUNTERS)
+        reactions += int(c[2])
+        lane_steps += int(c[1])
+        group_steps += int(c[0])
+        absorbed += int(c[5])
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(kernel_ms) / 1e3
+    hist = pkg.ssa_fetch(ctx, pkg.SSA_FIELD_EE_HIST).reshape(N_SNAP, 65)
+    # max over ranks of the device time; totals over ranks
+    totals = torch.tensor([reactions, absorbed, lane_steps, group_steps], dtype=torch.float64, device="cuda")
+    tmax = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+    htot = torch.from_numpy(hist.astype(np.float64)).cuda()
+    if dist is not None:
+        dist.all_reduce(totals)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(htot)
+    reactions, absorbed, lane_steps, group_steps = [float(x) for x in totals.tolist()]
+    t_dev = float(tmax.item())
+
+    # ---- roofline of the bit-sliced kernel (one launch per step)
+    K, b = bit_length(N_TOT * (N_TOT - 1) // 2), bit_length(N_TOT)
+    ops_unit = algorithmic_ops_per_group_step(K, b)
+    gs_per_launch = group_steps / world / args.steps
+    achieved = ops_unit * gs_per_launch / (statistics.mean(kernel_ms) / 1e3) / 1e9
+    peak_ops_per_clk = float(os.environ.get("BITSSA_ALU_OPS_PER_CLK_PER_SM", "64"))
+    peak = SMS * peak_ops_per_clk * MAX_SM_MHZ * 1e6 / 1e9
+    micro = None
+    try:
+        micro = pkg.bitssa_bench_alu(local, 4000)[0] / 1e9
+    except Exception:
+        pass
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                "frac": achieved / peak, "traffic": None,
+                "ops_per_group_step": ops_unit, "group_steps_per_launch": gs_per_launch,
+                "peak_basis": f"{SMS} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {MAX_SM_MHZ:g} MHz",
+                "lop3_microbench_gops": micro}
+
+    result = {"metric": METRIC, "value": reactions / t_dev, "unit": "lane-reactions/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+              "data": "synthetic", "config": workload_config(world),
+              "absorbed_runs_per_s": absorbed / t_dev, "lane_steps_per_s": lane_steps / t_dev,
+              "reactions_per_step": reactions / args.steps, "wall_s": wall,
+              "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
+              "hist_checksum": float(htot.sum().item())}
+
+    # ---- end to end through the C ABI with host buffers (create from host arrays, run, read every
+    # per-run output into pinned host memory, destroy), rank-local
+    pinned = {f: torch.empty(pkg.ssa_field_bytes(ctx, f), dtype=torch.uint8, pin_memory=True)
+              for f in (pkg.SSA_FIELD_FINAL_COUNTS, pkg.SSA_FIELD_ABSORB_TIME, pkg.SSA_FIELD_ABSORB_OUTCOME,
+                        pkg.SSA_FIELD_EE_HIST)}
+    host_in = {"reac": pkg.FRANK_REACTANTS, "prod": pkg.FRANK_PRODUCTS, "rates": np.ones(3),
+               "init": np.array(INIT, dtype=np.int64)}
+    h2d = sum(v.nbytes for v in host_in.values()) + 8 * (N_SNAP + 1)
+    d2h = sum(t.numel() for t in pinned.values())
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_react = 0
+    for _ in range(e2e_steps):
+        c2 = pkg.ssa_create(host_in["reac"], host_in["prod"], host_in["rates"], host_in["init"], RUNS_PER_GPU,
+                            SEED, opt)
+        pkg.ssa_run(c2, T_END, SNAPS)
+        for f, t in pinned.items():
+            pkg.ssa_fetch(c2, f, t.numpy())
+        e2e_react += int(pkg.ssa_fetch(c2, pkg.SSA_FIELD_COUNTERS)[2])
+        pkg.ssa_destroy(c2)
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    result["e2e"] = {"value": e2e_react * world / e2e_t, "unit": "lane-reactions/s", "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+    pkg.ssa_destroy(ctx)
+
+    # ---- the one-thread-per-run GPU baseline on the same workload and precision
+    if not args.no_baselines:
+        o7 = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
+                                     engine=pkg.SSA_ENGINE_THREAD_PER_RUN, first_run=rank * RUNS_PER_GPU)
+        c7 = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
+                            RUNS_PER_GPU, SEED, o7)
+        pkg.ssa_run(c7, T_END, SNAPS)
+        torch.cuda.synchronize()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        a.record(stream)
+        pkg.ssa_run(c7, T_END, SNAPS)
+        b2.record(stream)
+        c = pkg.ssa_fetch(c7, pkg.SSA_FIELD_COUNTERS)
+        ms7 = a.elapsed_time(b2)
+        pkg.ssa_destroy(c7)
+        r7 = int(c[2]) / (ms7 / 1e3)
+        result["thread_per_run"] = {"value": r7 * world, "unit": "lane-reactions/s", "ms_per_step": ms7,
+                                    "absorbed_runs_per_s": int(c[5]) * world / (ms7 / 1e3),
+                                    "speedup_bitsliced_over_thread_per_run": (reactions / t_dev) / (r7 * world)}
+        if rank == 0:
+            result["cpu_baseline"] = cpu_baseline(args.cpu_sample, os.cpu_count() or 1)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

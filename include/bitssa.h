@@ -1,0 +1,196 @@
+/*
+ * bitssa.h -- C ABI of libbitssa, a GB300 (sm_103a) implementation of the
+ * bit-sliced exact stochastic simulation algorithm of Castellana & Lacoste,
+ * "Parallelization of Gillespie algorithm based on binary words"
+ * (arXiv 2412.16613).
+ *
+ * The method (Sec. 3): M independent runs of a conserved mass-action network
+ * are packed one per bit of a machine word, species counts live as bit-planes
+ * (Eqs. eq3, eq1, eq2, eq4, eq6), and one Gillespie step for all M runs is
+ * done with word-wide logic: a uniform integer n in [0, Lambda) per run, the
+ * comparator / changer words that pick the reaction by walking the integer
+ * CDF (steps a-d, Eq. equation-changer), masked count updates (Eq.
+ * equation-v) and incremental propensity updates (Eqs. equation-a-1..3,
+ * App. B).  Ghost reactions (Eqs. 4-6) make the total rate the constant
+ * Lambda = k_max * N (N - 1) / 2 (Eq. equation-z), so the waiting time
+ * tau ~ Exp(Lambda) (Eq. equation-tau) does not depend on the state.
+ *
+ * Here a word is 32 bits and holds one *group* of 32 runs; run j is lane
+ * j % 32 of group j / 32.  Every group draws its random bits from a Philox4x32-10
+ * counter stream keyed by (seed, group, step), so results do not depend on the
+ * launch shape: run j's trajectory is a fixed function of (network, N0, seed, j).
+ * One waiting time is drawn per group and step: the 32 runs of a group share
+ * their event times (each run is still an exact sample path; runs of
+ * different groups are independent).
+ *
+ * Conventions for every entry point:
+ *   - return value: an ssa_status (0 = SSA_OK, negative = error); no entry point
+ *     aborts, throws or exits.  ssa_last_error() gives a message.
+ *   - inputs are copied at the call; the caller keeps ownership of its arrays.
+ *   - device buffers are owned by the context.  They come from the allocator
+ *     set by ssa_set_allocator() (default cudaMalloc / cudaFree) and are used on
+ *     the stream given in ssa_options.cuda_stream.
+ *   - arrays are C order (row-major), integers little-endian, no padding.
+ */
+#ifndef BITSSA_H
+#define BITSSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssa_ctx ssa_ctx;
+
+typedef enum {
+  SSA_OK = 0,
+  SSA_EINVAL = -1,        /* an argument is out of range or inconsistent */
+  SSA_EUNSUPPORTED = -2,  /* valid input this library does not run (see ssa_create) */
+  SSA_ENOMEM = -3,        /* the allocator returned NULL */
+  SSA_ECUDA = -4,         /* a CUDA runtime call failed (no device, launch error, ...) */
+  SSA_ETIMEOUT = -5,      /* a group hit ssa_options.step_budget */
+  SSA_EOVERFLOW = -6,     /* 64 redraws of n in a row, or an internal range check failed */
+  SSA_ESTATE = -7         /* call out of order (e.g. ssa_fetch before ssa_run) */
+} ssa_status;
+
+/* Precision of the waiting-time clock (the integer dynamics are exact in every mode). */
+enum {
+  SSA_P64 = 0,        /* fp64: u = (x + 1) 2^-53 from 53 random bits; the clock keeps
+                         exp(-Lambda t) = prod u as an fp64 mantissa and an integer
+                         exponent, so no logarithm is taken per step */
+  SSA_P32_KAHAN = 1,  /* fp32: u from the top 24 of those bits, tau = -logf(u) / Lambda,
+                         Kahan-compensated fp32 time sum */
+  SSA_P32_D64ACC = 2, /* fp32 tau as above, fp64 time accumulator */
+  SSA_P64_LOGSUM = 3  /* fp64: tau = -log(u) / Lambda and t += tau every step, the
+                         literal form of Eq. equation-tau and Eq. eq-update-time */
+};
+
+/* Simulation engine. */
+enum {
+  SSA_ENGINE_BITSLICED = 0,     /* the method of the paper: 32 runs per word */
+  SSA_ENGINE_THREAD_PER_RUN = 1 /* comparison baseline: one GPU thread per run, direct
+                                   method with integer propensities (Sec. 3, steps 1-7
+                                   without ghosts) and its own per-run Philox stream */
+};
+
+typedef struct {
+  int32_t precision;         /* SSA_P64 (default) | SSA_P32_KAHAN | SSA_P32_D64ACC | SSA_P64_LOGSUM */
+  int32_t engine;            /* SSA_ENGINE_BITSLICED (default) | SSA_ENGINE_THREAD_PER_RUN */
+  int32_t block_size;        /* threads per block, 0 = chosen from occupancy */
+  int32_t blocks_per_sm;     /* resident blocks per SM to launch, 0 = occupancy limit */
+  int32_t thin_bits;         /* q in [1, 64], bits of the thinning threshold (default 32) */
+  int32_t keep_snap_counts;  /* 1: keep per-run counts at each snapshot (SSA_FIELD_SNAP_COUNTS) */
+  int64_t step_budget;       /* group steps before SSA_ETIMEOUT, 0 = unlimited */
+  int64_t first_run;         /* global index of this context's run 0 inside its ensembles
+                                (a multiple of 32); lets several contexts shard one
+                                ensemble with results identical to one context */
+  void* cuda_stream;         /* cudaStream_t to use; NULL = the legacy default stream */
+  int32_t device;            /* CUDA device ordinal, -1 = the current device */
+  int32_t reserved[7];
+} ssa_options;
+
+/* Fields for ssa_fetch.  n_runs = the context's total number of runs (for a batch,
+ * ensembles are concatenated in order); S = n_species, in the caller's species order. */
+enum {
+  SSA_FIELD_FINAL_COUNTS = 0,   /* int32[n_runs][S]: counts when the run stopped (absorbed or
+                                   at t_end) */
+  SSA_FIELD_ABSORB_TIME = 1,    /* double[n_runs]: time of the event after which no reaction
+                                   with k_r > 0 can fire; +inf if that never happened by t_end */
+  SSA_FIELD_ABSORB_OUTCOME = 2, /* int8[n_runs]: -1 not absorbed, else the index of the one
+                                   species left (-2: absorbed with several species left) */
+  SSA_FIELD_EE_HIST = 3,        /* uint64[n_ens][n_snap][65]: enantiomeric-excess histogram of
+                                   (L, D) = (species chiral[0], chiral[1]) at each snapshot:
+                                   bin min(63, floor(64 L / (L + D))), bin 64 = L + D == 0 */
+  SSA_FIELD_SNAP_COUNTS = 4,    /* int32[n_snap][n_runs][S] (needs keep_snap_counts = 1) */
+  SSA_FIELD_COUNTERS = 5,       /* uint64[8]: group steps, lane steps of live runs, real
+                                   reactions, null lane steps, redraw rounds, absorbed runs,
+                                   groups finished, error flags */
+  SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,
+                                   and runs not absorbed, per ensemble */
+};
+#define SSA_N_COUNTERS 8
+
+void ssa_default_options(ssa_options* opt);
+
+/*
+ * Create a context for n_runs runs of one network.
+ *   reactants, products: int32[n_reactions][n_species] multiplicities; every reaction
+ *     has order 1 or 2 and conserves the total count (Sec. 2: the model conserves
+ *     N_tot = N_L + N_R + N_A, which the method relies on, Sec. 3).
+ *   rates: double[n_reactions], k_r >= 0 with max > 0.  Non-unit ratios k_r / k_max
+ *     are applied by thinning: the drawn reaction is kept iff a q-bit uniform U is
+ *     below T_r = floor(k_r / k_max 2^q) (the paper leaves general rates to future
+ *     work, Sec. 6; this is an exact-in-the-limit integer form of it).
+ *   N0: int64[n_species] shared initial counts (n0_per_run = 0) or
+ *     int64[n_runs][n_species] (n0_per_run = 1); every run must have the same total
+ *     (Sec. 3: the copies share N_tot).
+ *   seed: the Philox key.
+ * SSA_EUNSUPPORTED unless the network is Frank's model (Eqs. 1-3) up to a
+ * relabelling of species: three species X, Y, A and, in this order,
+ * A + X -> 2X, A + Y -> 2Y, X + Y -> 2A; and unless N_tot(N_tot - 1)/2 < 2^31
+ * (N_tot <= 65536).  n_runs may be 0.  On success *out owns device memory until
+ * ssa_destroy.
+ */
+int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_species,
+               int32_t n_reactions, const double* rates, const int64_t* N0, int32_t n0_per_run,
+               int64_t n_runs, uint64_t seed, const ssa_options* opt, ssa_ctx** out);
+
+/*
+ * Create a context for n_ens ensembles of the same network run in one launch
+ * sequence.  Ensemble e has its own initial counts N0_ens[e] (int64[n_ens][S]),
+ * rates rates_ens[e] (double[n_ens][R]), run count runs_ens[e] and seed
+ * seed_ens[e]; its runs are numbered from 0 inside the ensemble (stream
+ * groups restart at 0), and appear in the output fields after the runs of
+ * ensembles 0..e-1.  Same restrictions as ssa_create.
+ */
+int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t n_species,
+                     int32_t n_reactions, int32_t n_ens, const int64_t* N0_ens,
+                     const double* rates_ens, const int64_t* runs_ens, const uint64_t* seed_ens,
+                     const ssa_options* opt, ssa_ctx** out);
+
+/*
+ * Simulate every run from its initial state (each call starts again from t = 0,
+ * so repeated calls give identical results) until it is absorbed or its next
+ * event would come after t_end.  snapshot_times: double[n_snap], ascending, each
+ * in [0, t_end]; the snapshot at time t holds the state after every event with
+ * time <= t.  n_snap in [0, 64].  Blocks until the work is done on the stream.
+ */
+int ssa_run(ssa_ctx* ctx, double t_end, const double* snapshot_times, int32_t n_snap);
+
+/* Size in bytes of a field after the last ssa_run (0 for an unknown field). */
+int ssa_field_bytes(const ssa_ctx* ctx, int32_t field, size_t* bytes);
+
+/*
+ * Copy a field into dst (dst_bytes >= ssa_field_bytes).  dst_on_device = 1: dst is
+ * device memory on the context's device, the copy runs on the context's stream
+ * and is complete on return; 0: dst is host memory.
+ */
+int ssa_fetch(ssa_ctx* ctx, int32_t field, void* dst, size_t dst_bytes, int32_t dst_on_device);
+
+/* Free the context and its device memory.  NULL is allowed. */
+int ssa_destroy(ssa_ctx* ctx);
+
+/* Message of the last failed call on ctx, or of the calling thread's last failed
+ * ssa_create / ssa_create_batch / ssa_set_allocator when ctx is NULL.  Owned by
+ * the library; valid until the next call on the same ctx / thread. */
+const char* ssa_last_error(const ssa_ctx* ctx);
+
+/*
+ * Route device allocations through caller functions (e.g. a framework's caching
+ * allocator).  alloc returns device memory of at least `bytes` on `device`
+ * usable on `stream`, or NULL; release frees it.  NULL, NULL restores
+ * cudaMalloc / cudaFree.  Affects contexts created afterwards.
+ */
+typedef void* (*ssa_alloc_fn)(size_t bytes, int device, void* stream, void* user);
+typedef void (*ssa_free_fn)(void* ptr, size_t bytes, int device, void* stream, void* user);
+int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int ssa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,127 @@
+// internal.h -- structures shared by the host runtime and the sm_103a kernels
+// of libbitssa.  Not part of the C ABI.
+#pragma once
+
+#include <cstdint>
+
+namespace bitssa {
+
+constexpr int kMaxSnap = 64;
+constexpr int kHistBins = 65;  // 64 enantiomeric-excess bins + one for L + D == 0
+constexpr int kCounters = 8;
+constexpr int kMaxK = 31;      // random / propensity planes: N_tot (N_tot - 1) / 2 < 2^31
+
+// Clock precision modes (same values as SSA_P64 ... in bitssa.h).
+enum Precision { kP64 = 0, kP32Kahan = 1, kP32D64Acc = 2, kP64LogSum = 3 };
+
+// Indices into the device counter array (uint64).
+enum Counter {
+  kGroupSteps = 0,
+  kLaneSteps = 1,
+  kReactions = 2,
+  kNullLaneSteps = 3,
+  kRedrawRounds = 4,
+  kAbsorbed = 5,
+  kGroupsDone = 6,
+  kErrorFlags = 7
+};
+
+// Error flags (OR-ed into the status word).
+enum ErrorFlag : uint32_t {
+  kErrTimeout = 1u,      // step budget reached
+  kErrRedraw = 2u,       // 64 redraws of n in a row
+  kErrRange = 4u,        // a count or propensity left its range (internal check)
+  kErrQueue = 8u         // work item without a valid ensemble
+};
+
+// Crossing threshold for one time point t of one ensemble, in the forms each
+// clock compares against.
+struct Threshold {
+  double t;        // the time itself (fp64 sum clocks)
+  double m;        // exp(-Lambda t) = m 2^E with m in [1, 2) (product clock)
+  long long E;
+  float t_f;       // the largest float <= t (fp32 Kahan clock: f > t_f <=> (double)f > t)
+  int pad;
+};
+
+// Per-ensemble constants.  Species are in the kernel's canonical Frank order
+// (L, D, A): reactions A+L->2L, A+D->2D, L+D->2A.
+struct Ensemble {
+  unsigned long long seed;
+  long long n_runs;        // runs of this ensemble in this context
+  long long run_offset;    // row of the ensemble's first run in the output fields
+  long long group_base;    // stream group index of the context's first group (first_run / 32)
+  long long thin_T[3];     // thinning thresholds T_r (bit patterns of uint64)
+  double lambda;           // k_max * lambda_int
+  float inv_lambda_f;      // (float)(1 / lambda)
+  unsigned int lambda_int; // N (N - 1) / 2
+  int n_tot;
+  int K;                   // bit length of lambda_int
+  int init[3];             // shared initial counts (canonical order)
+  unsigned int thin_always;  // bit r: k_r == k_max
+  unsigned int active;       // bit r: k_r > 0
+  int thin;                  // any reaction with k_r < k_max
+  int thin_bits;             // q
+  int pad;
+};
+
+// One launch of the bit-sliced kernel for one K.
+struct FrankLaunch {
+  Ensemble ens;                   // used when ens_table == nullptr (one ensemble)
+  const Ensemble* ens_table;      // [n_ens] (batch)
+  const Threshold* thr;           // [n_ens][n_snap + 1]; entry n_snap is t_end
+  const int* item_ens;            // [n_items] ensemble of each work item, or nullptr
+  const int* item_group;          // [n_items] group inside its ensemble, or nullptr
+  long long item_begin, item_end; // work items of this launch
+  const int* init_counts;         // [n_runs_total][3] canonical order, or nullptr (shared init)
+  int n_snap;
+  int precision;
+  long long step_budget;
+  int perm[3];                    // canonical species c is written to column perm[c]
+  int n_species;                  // columns of the count outputs
+  // outputs
+  int* final_counts;              // [n_runs_total][n_species]
+  double* t_abs;                  // [n_runs_total]
+  signed char* outcome;           // [n_runs_total]
+  unsigned long long* hist;       // [n_ens][n_snap][65]
+  unsigned long long* ens_absorbed; // [n_ens][4]
+  int* snap_counts;               // [n_snap][n_runs_total][n_species] or nullptr
+  long long n_runs_total;
+  // scratch
+  unsigned long long* counters;   // [kCounters]
+  unsigned int* status;           // error flags
+  unsigned long long* queue;      // work-item counter of this launch
+};
+
+// One launch of the one-thread-per-run baseline.
+struct ThreadLaunch {
+  Ensemble ens;
+  const Threshold* thr;           // [n_snap + 1]
+  const int* init_counts;         // [n_runs][3] or nullptr
+  int n_snap;
+  int precision;
+  long long step_budget;
+  double rates[3];
+  int unit_rates;                 // all k_r equal: exact integer selection
+  int perm[3];
+  int n_species;
+  int* final_counts;
+  double* t_abs;
+  signed char* outcome;
+  unsigned long long* hist;
+  unsigned long long* ens_absorbed;
+  int* snap_counts;
+  long long n_runs_total;
+  unsigned long long* counters;
+  unsigned int* status;
+};
+
+// Entry points implemented by the kernel translation units.
+using FrankLauncher = int (*)(const FrankLaunch&, int grid, int block, int smem, void* stream);
+FrankLauncher frank_launcher(int K);
+int frank_max_active_blocks(int K, int batch, int block, int smem, int* blocks);
+int frank_registers(int K, int batch);
+int thread_per_run_launch(const ThreadLaunch& p, int grid, int block, int smem, void* stream);
+int thread_per_run_max_active_blocks(int block, int smem, int* blocks);
+
+}  // namespace bitssa

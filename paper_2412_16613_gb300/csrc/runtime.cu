@@ -1,0 +1,735 @@
+// runtime.cu -- host side of libbitssa: the C ABI declared in include/bitssa.h.
+//
+// Validates and copies the inputs, derives the per-ensemble constants of the
+// method (lambda_int = N (N - 1) / 2 of Eq. equation-z, its bit length K, the
+// thinning thresholds), owns the device buffers, and launches the bit-sliced
+// kernel instantiation for each K (or the one-thread-per-run baseline).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/bitssa.h"
+#include "internal.h"
+
+using namespace bitssa;
+
+namespace {
+
+struct Allocator {
+  ssa_alloc_fn alloc = nullptr;
+  ssa_free_fn release = nullptr;
+  void* user = nullptr;
+};
+
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+thread_local std::string t_err;
+
+int bit_len(unsigned long long v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
+}  // namespace
+
+struct ssa_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ssa_options opt{};
+  Allocator alloc;
+  std::string err;
+  int S = 3;
+  int perm[3] = {0, 1, 2};  // canonical species (L, D, A) -> caller's species index
+  bool batch = false;
+  int n_ens = 0;
+  long long n_runs_total = 0;
+  std::vector<Ensemble> ens;
+  std::vector<double> rates;  // [n_ens][3]
+  // batch work items, sorted by K (descending), and the K of each launch range
+  std::vector<int> item_ens, item_group;
+  std::vector<std::pair<int, std::pair<long long, long long>>> ranges;  // K -> [begin, end)
+  struct Buf {
+    void* p;
+    size_t bytes;
+  };
+  std::vector<Buf> bufs;
+  Ensemble* d_ens = nullptr;
+  Threshold* d_thr = nullptr;
+  size_t thr_cap = 0;
+  int* d_item_ens = nullptr;
+  int* d_item_group = nullptr;
+  int* d_init = nullptr;
+  int* d_final = nullptr;
+  double* d_tabs = nullptr;
+  signed char* d_outcome = nullptr;
+  unsigned long long* d_hist = nullptr;
+  size_t hist_cap = 0;
+  unsigned long long* d_ens_abs = nullptr;
+  int* d_snap = nullptr;
+  size_t snap_cap = 0;
+  unsigned long long* d_counters = nullptr;  // [kCounters] then the queues
+  unsigned int* d_status = nullptr;
+  int n_queues = 0;
+  bool ran = false;
+  int n_snap = 0;
+  unsigned long long counters[kCounters] = {0};
+  int sm_count = 0;
+};
+
+namespace {
+
+int fail(ssa_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else t_err = msg;
+  return code;
+}
+
+int cuda_fail(ssa_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SSA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+void* dev_alloc(ssa_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->alloc.alloc) {
+    p = c->alloc.alloc(bytes, c->device, (void*)c->stream, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->bufs.push_back({p, bytes});
+  return p;
+}
+
+void dev_free(ssa_ctx* c, void* p) {
+  for (size_t i = 0; i < c->bufs.size(); ++i) {
+    if (c->bufs[i].p == p) {
+      if (c->alloc.release) c->alloc.release(p, c->bufs[i].bytes, c->device, (void*)c->stream, c->alloc.user);
+      else cudaFree(p);
+      c->bufs.erase(c->bufs.begin() + (long)i);
+      return;
+    }
+  }
+}
+
+void dev_free_all(ssa_ctx* c) {
+  for (auto& b : c->bufs) {
+    if (c->alloc.release) c->alloc.release(b.p, b.bytes, c->device, (void*)c->stream, c->alloc.user);
+    else cudaFree(b.p);
+  }
+  c->bufs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Validation of the network: order 1 or 2, conservation of the total count
+// (Sec. 2), and recognition of Frank's model (Eqs. 1-3) up to relabelling.
+// ---------------------------------------------------------------------------
+int check_network(const int32_t* reac, const int32_t* prod, int S, int R, int perm[3], std::string* why) {
+  if (!reac || !prod) return (*why = "null stoichiometry", SSA_EINVAL);
+  if (S < 1 || R < 1 || S > 64 || R > 64) return (*why = "n_species / n_reactions out of range", SSA_EINVAL);
+  for (int r = 0; r < R; ++r) {
+    int order = 0, made = 0;
+    for (int i = 0; i < S; ++i) {
+      if (reac[r * S + i] < 0 || prod[r * S + i] < 0) return (*why = "negative stoichiometry", SSA_EINVAL);
+      order += reac[r * S + i];
+      made += prod[r * S + i];
+    }
+    if (order < 1 || order > 2)
+      return (*why = "reaction " + std::to_string(r) + " has order " + std::to_string(order) +
+                     " (orders 1 and 2 only)", SSA_EINVAL);
+    if (made != order)
+      return (*why = "reaction " + std::to_string(r) + " does not conserve the total count", SSA_EINVAL);
+  }
+  if (S != 3 || R != 3) return (*why = "only Frank's model (3 species, 3 reactions) is supported", SSA_EUNSUPPORTED);
+  // reaction 2: X + Y -> 2A
+  int A = -1;
+  for (int i = 0; i < 3; ++i)
+    if (prod[2 * 3 + i] == 2) A = i;
+  auto is_auto = [&](int r, int& X) {  // A + X -> 2X
+    X = -1;
+    for (int i = 0; i < 3; ++i)
+      if (i != A && reac[r * 3 + i] == 1 && prod[r * 3 + i] == 2) X = i;
+    return X >= 0 && reac[r * 3 + A] == 1 && prod[r * 3 + A] == 0;
+  };
+  int X = -1, Y = -1;
+  const bool ok = A >= 0 && is_auto(0, X) && is_auto(1, Y) && X != Y && reac[2 * 3 + X] == 1 &&
+                  reac[2 * 3 + Y] == 1 && reac[2 * 3 + A] == 0 && prod[2 * 3 + X] == 0 && prod[2 * 3 + Y] == 0;
+  if (!ok)
+    return (*why = "network is not Frank's model A+X->2X, A+Y->2Y, X+Y->2A (in this reaction order)",
+            SSA_EUNSUPPORTED);
+  perm[0] = X;
+  perm[1] = Y;
+  perm[2] = A;
+  return SSA_OK;
+}
+
+int check_rates(const double* k, std::string* why) {
+  double kmax = 0.0;
+  for (int r = 0; r < 3; ++r) {
+    if (!(k[r] >= 0.0) || std::isinf(k[r])) return (*why = "rates must be finite and >= 0", SSA_EINVAL);
+    kmax = std::max(kmax, k[r]);
+  }
+  if (!(kmax > 0.0)) return (*why = "at least one rate must be > 0", SSA_EINVAL);
+  return SSA_OK;
+}
+
+int check_options(const ssa_options& o, std::string* why) {
+  if (o.precision < 0 || o.precision > 3) return (*why = "unknown precision mode", SSA_EINVAL);
+  if (o.engine < 0 || o.engine > 1) return (*why = "unknown engine", SSA_EINVAL);
+  if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
+  if (o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
+    return (*why = "block_size must be 0 or a multiple of 32 up to 256", SSA_EINVAL);
+  if (o.blocks_per_sm < 0) return (*why = "blocks_per_sm must be >= 0", SSA_EINVAL);
+  if (o.step_budget < 0) return (*why = "step_budget must be >= 0", SSA_EINVAL);
+  if (o.first_run < 0 || (o.first_run % 32) != 0) return (*why = "first_run must be a multiple of 32", SSA_EINVAL);
+  return SSA_OK;
+}
+
+// Per-ensemble constants from their definitions.
+Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], int q, unsigned long long seed,
+                       long long n_runs, long long run_offset, long long group_base) {
+  Ensemble e;
+  std::memset(&e, 0, sizeof e);
+  e.seed = seed;
+  e.n_runs = n_runs;
+  e.run_offset = run_offset;
+  e.group_base = group_base;
+  e.n_tot = (int)n_tot;
+  const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
+  e.lambda_int = (unsigned int)lam;
+  e.K = bit_len(lam);
+  const double kmax = std::max(k[0], std::max(k[1], k[2]));
+  e.lambda = kmax * (double)lam;
+  e.inv_lambda_f = (float)(1.0 / e.lambda);
+  e.thin_bits = q;
+  for (int r = 0; r < 3; ++r) {
+    e.init[r] = init[r];
+    if (k[r] > 0.0) e.active |= 1u << r;
+    if (k[r] == kmax) {
+      e.thin_always |= 1u << r;
+      e.thin_T[r] = 0;
+    } else {
+      e.thin_T[r] = (long long)(unsigned long long)std::floor(std::ldexp(k[r] / kmax, q));
+      e.thin = 1;
+    }
+  }
+  return e;
+}
+
+// The crossing threshold of time t for total rate lambda.
+Threshold make_threshold(double t, double lambda) {
+  Threshold h;
+  std::memset(&h, 0, sizeof h);
+  h.t = t;
+  float f = (float)t;
+  if ((double)f > t) f = std::nextafter(f, -INFINITY);
+  h.t_f = f;
+  if (std::isinf(t) || !(lambda > 0.0)) {
+    h.E = LLONG_MIN;
+    h.m = 1.0;
+    return h;
+  }
+  const double theta = -lambda * t;  // ln exp(-lambda t)
+  long long E = (long long)std::floor(theta / M_LN2);
+  double m = std::exp(theta - (double)E * M_LN2);
+  while (m >= 2.0) {
+    m *= 0.5;
+    ++E;
+  }
+  while (m < 1.0) {
+    m *= 2.0;
+    --E;
+  }
+  h.E = E;
+  h.m = m;
+  return h;
+}
+
+int grow(ssa_ctx* c, void** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return SSA_OK;
+  if (*p) dev_free(c, *p);
+  *p = dev_alloc(c, need);
+  *cap = *p ? need : 0;
+  return *p ? SSA_OK : fail(c, SSA_ENOMEM, "device allocation failed");
+}
+
+int setup_device(ssa_ctx* c) {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(c, SSA_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  if (c->opt.device >= n) return fail(c, SSA_EINVAL, "device ordinal out of range");
+  if (c->opt.device >= 0) c->device = c->opt.device;
+  else if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess)
+    return cuda_fail(c, e, "cudaDeviceGetAttribute");
+  c->stream = (cudaStream_t)c->opt.cuda_stream;
+  return SSA_OK;
+}
+
+int allocate_common(ssa_ctx* c, const std::vector<int>& init_rows) {
+  const long long nr = c->n_runs_total;
+  const int S = c->S;
+  c->d_ens = (Ensemble*)dev_alloc(c, sizeof(Ensemble) * (size_t)c->n_ens);
+  c->d_final = (int*)dev_alloc(c, sizeof(int) * (size_t)nr * S);
+  c->d_tabs = (double*)dev_alloc(c, sizeof(double) * (size_t)nr);
+  c->d_outcome = (signed char*)dev_alloc(c, (size_t)nr);
+  c->d_ens_abs = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * 4 * (size_t)c->n_ens);
+  c->n_queues = 1 + (int)c->ranges.size();
+  c->d_counters = (unsigned long long*)dev_alloc(c, sizeof(unsigned long long) * (kCounters + c->n_queues));
+  c->d_status = (unsigned int*)dev_alloc(c, sizeof(unsigned int) * 4);
+  if (!c->d_ens || !c->d_final || !c->d_tabs || !c->d_outcome || !c->d_ens_abs || !c->d_counters || !c->d_status)
+    return fail(c, SSA_ENOMEM, "device allocation failed");
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->d_ens, c->ens.data(), sizeof(Ensemble) * c->ens.size(), cudaMemcpyHostToDevice,
+                           c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "upload ensembles");
+  if (!init_rows.empty()) {
+    c->d_init = (int*)dev_alloc(c, sizeof(int) * init_rows.size());
+    if (!c->d_init) return fail(c, SSA_ENOMEM, "device allocation failed");
+    if ((e = cudaMemcpyAsync(c->d_init, init_rows.data(), sizeof(int) * init_rows.size(), cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "upload initial counts");
+  }
+  if (!c->item_ens.empty()) {
+    c->d_item_ens = (int*)dev_alloc(c, sizeof(int) * c->item_ens.size());
+    c->d_item_group = (int*)dev_alloc(c, sizeof(int) * c->item_group.size());
+    if (!c->d_item_ens || !c->d_item_group) return fail(c, SSA_ENOMEM, "device allocation failed");
+    cudaMemcpyAsync(c->d_item_ens, c->item_ens.data(), sizeof(int) * c->item_ens.size(), cudaMemcpyHostToDevice,
+                    c->stream);
+    cudaMemcpyAsync(c->d_item_group, c->item_group.data(), sizeof(int) * c->item_group.size(),
+                    cudaMemcpyHostToDevice, c->stream);
+  }
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  return SSA_OK;
+}
+
+int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R, const ssa_options* opt,
+                  ssa_ctx** out, ssa_ctx** made, int perm[3]) {
+  if (!out) return fail(nullptr, SSA_EINVAL, "out is NULL");
+  *out = nullptr;
+  ssa_options o;
+  ssa_default_options(&o);
+  if (opt) o = *opt;
+  std::string why;
+  int st = check_options(o, &why);
+  if (st != SSA_OK) return fail(nullptr, st, why);
+  st = check_network(reac, prod, S, R, perm, &why);
+  if (st != SSA_OK) return fail(nullptr, st, why);
+  ssa_ctx* c = new ssa_ctx();
+  c->opt = o;
+  c->S = S;
+  for (int i = 0; i < 3; ++i) c->perm[i] = perm[i];
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    c->alloc = g_alloc;
+  }
+  *made = c;
+  return SSA_OK;
+}
+
+int launch_runs(ssa_ctx* c) {
+  const int n_snap = c->n_snap;
+  cudaError_t e;
+  FrankLaunch fl;
+  std::memset(&fl, 0, sizeof fl);
+  fl.thr = c->d_thr;
+  fl.init_counts = c->d_init;
+  fl.n_snap = n_snap;
+  fl.precision = c->opt.precision;
+  fl.step_budget = c->opt.step_budget;
+  for (int i = 0; i < 3; ++i) fl.perm[i] = c->perm[i];
+  fl.n_species = c->S;
+  fl.final_counts = c->d_final;
+  fl.t_abs = c->d_tabs;
+  fl.outcome = c->d_outcome;
+  fl.hist = c->d_hist;
+  fl.ens_absorbed = c->d_ens_abs;
+  fl.snap_counts = c->opt.keep_snap_counts ? c->d_snap : nullptr;
+  fl.n_runs_total = c->n_runs_total;
+  fl.counters = c->d_counters;
+  fl.status = c->d_status;
+  const int block = c->opt.block_size ? c->opt.block_size : 64;
+
+  if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN) {
+    if (c->batch) return fail(c, SSA_EUNSUPPORTED, "the thread-per-run engine runs single-ensemble contexts");
+    ThreadLaunch tl;
+    std::memset(&tl, 0, sizeof tl);
+    tl.ens = c->ens[0];
+    tl.thr = c->d_thr;
+    tl.init_counts = c->d_init;
+    tl.n_snap = n_snap;
+    tl.precision = c->opt.precision;
+    tl.step_budget = c->opt.step_budget;
+    for (int r = 0; r < 3; ++r) tl.rates[r] = c->rates[r];
+    tl.unit_rates = c->rates[0] == c->rates[1] && c->rates[1] == c->rates[2];
+    for (int i = 0; i < 3; ++i) tl.perm[i] = c->perm[i];
+    tl.n_species = c->S;
+    tl.final_counts = c->d_final;
+    tl.t_abs = c->d_tabs;
+    tl.outcome = c->d_outcome;
+    tl.hist = c->d_hist;
+    tl.ens_absorbed = c->d_ens_abs;
+    tl.snap_counts = fl.snap_counts;
+    tl.n_runs_total = c->n_runs_total;
+    tl.counters = c->d_counters;
+    tl.status = c->d_status;
+    const int tblock = c->opt.block_size ? c->opt.block_size : 256;
+    const int smem = n_snap * kHistBins * (int)sizeof(unsigned int);
+    int occ = 0;
+    if ((e = (cudaError_t)thread_per_run_max_active_blocks(tblock, smem, &occ)) != cudaSuccess || occ < 1)
+      return fail(c, SSA_ECUDA, "occupancy query failed for the thread-per-run kernel");
+    const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+    const long long need = (c->n_runs_total + tblock - 1) / tblock;
+    const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
+    if ((e = (cudaError_t)thread_per_run_launch(tl, grid, tblock, smem, (void*)c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "thread-per-run launch");
+    return SSA_OK;
+  }
+
+  if (!c->batch) {
+    const Ensemble& en = c->ens[0];
+    const long long groups = (en.n_runs + 31) / 32;
+    const int K = std::max(1, en.K);
+    fl.ens = en;
+    fl.ens_table = nullptr;
+    fl.item_begin = 0;
+    fl.item_end = groups;
+    fl.queue = c->d_counters + kCounters;
+    const int smem = n_snap * kHistBins * (int)sizeof(unsigned int);
+    int occ = 0;
+    if (frank_max_active_blocks(K, 0, block, smem, &occ) != 0 || occ < 1)
+      return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
+    const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+    const long long need = (groups + block - 1) / block;
+    const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
+    if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, smem, (void*)c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "bit-sliced kernel launch");
+    return SSA_OK;
+  }
+
+  fl.ens_table = c->d_ens;
+  fl.item_ens = c->d_item_ens;
+  fl.item_group = c->d_item_group;
+  for (size_t r = 0; r < c->ranges.size(); ++r) {
+    const int K = std::max(1, c->ranges[r].first);
+    fl.item_begin = c->ranges[r].second.first;
+    fl.item_end = c->ranges[r].second.second;
+    fl.queue = c->d_counters + kCounters + 1 + r;
+    int occ = 0;
+    if (frank_max_active_blocks(K, 1, block, 0, &occ) != 0 || occ < 1)
+      return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
+    const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+    const long long need = (fl.item_end - fl.item_begin + block - 1) / block;
+    const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
+    if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, 0, (void*)c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "bit-sliced kernel launch");
+  }
+  return SSA_OK;
+}
+
+size_t field_bytes(const ssa_ctx* c, int field) {
+  const size_t nr = (size_t)c->n_runs_total, S = (size_t)c->S;
+  switch (field) {
+    case SSA_FIELD_FINAL_COUNTS: return nr * S * sizeof(int32_t);
+    case SSA_FIELD_ABSORB_TIME: return nr * sizeof(double);
+    case SSA_FIELD_ABSORB_OUTCOME: return nr;
+    case SSA_FIELD_EE_HIST: return (size_t)c->n_ens * (size_t)c->n_snap * kHistBins * sizeof(uint64_t);
+    case SSA_FIELD_SNAP_COUNTS: return c->opt.keep_snap_counts ? (size_t)c->n_snap * nr * S * sizeof(int32_t) : 0;
+    case SSA_FIELD_COUNTERS: return kCounters * sizeof(uint64_t);
+    case SSA_FIELD_ENS_ABSORBED: return (size_t)c->n_ens * 4 * sizeof(uint64_t);
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void ssa_default_options(ssa_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->precision = SSA_P64;
+  opt->engine = SSA_ENGINE_BITSLICED;
+  opt->thin_bits = 32;
+  opt->device = -1;
+}
+
+int ssa_version(void) { return 100; }
+
+int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_species, int32_t n_reactions,
+               const double* rates, const int64_t* N0, int32_t n0_per_run, int64_t n_runs, uint64_t seed,
+               const ssa_options* opt, ssa_ctx** out) {
+  ssa_ctx* c = nullptr;
+  int perm[3];
+  int st = create_common(reactants, products, n_species, n_reactions, opt, out, &c, perm);
+  if (st != SSA_OK) return st;
+  std::string why;
+  auto bail = [&](int code, std::string msg) {  // by value: msg may live in *c
+    delete c;
+    return fail(nullptr, code, msg);
+  };
+  if (!rates) return bail(SSA_EINVAL, "rates is NULL");
+  if ((st = check_rates(rates, &why)) != SSA_OK) return bail(st, why);
+  if (!N0) return bail(SSA_EINVAL, "N0 is NULL");
+  if (n_runs < 0) return bail(SSA_EINVAL, "n_runs must be >= 0");
+  if (n0_per_run != 0 && n0_per_run != 1) return bail(SSA_EINVAL, "n0_per_run must be 0 or 1");
+  if (c->opt.first_run + n_runs > (1ll << 37)) return bail(SSA_EINVAL, "run index beyond 2^37");
+  // total count, identical for every run (Sec. 3)
+  long long n_tot = -1;
+  std::vector<int> rows;
+  const long long nrows = n0_per_run ? n_runs : 1;
+  if (n0_per_run) rows.resize((size_t)n_runs * 3);
+  int shared[3] = {0, 0, 0};
+  for (long long j = 0; j < nrows; ++j) {
+    long long tot = 0;
+    int canon[3];
+    for (int ci = 0; ci < 3; ++ci) {
+      const long long v = N0[j * 3 + perm[ci]];
+      if (v < 0) return bail(SSA_EINVAL, "initial counts must be >= 0");
+      if (v > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
+      canon[ci] = (int)v;
+      tot += v;
+    }
+    if (n_tot < 0) n_tot = tot;
+    if (tot != n_tot) return bail(SSA_EINVAL, "every run must have the same total count");
+    if (n0_per_run) std::memcpy(&rows[(size_t)j * 3], canon, sizeof canon);
+    else std::memcpy(shared, canon, sizeof canon);
+  }
+  if (nrows == 0) n_tot = 1;
+  if (n_tot < 1) return bail(SSA_EINVAL, "the total count must be >= 1");
+  if (n_tot > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536 (lambda_int must stay below 2^31)");
+  const double canon_rates[3] = {rates[0], rates[1], rates[2]};
+  c->rates.assign(canon_rates, canon_rates + 3);
+  c->n_ens = 1;
+  c->n_runs_total = n_runs;
+  c->ens.push_back(make_ensemble(n_tot, shared, canon_rates, c->opt.thin_bits, seed, n_runs, 0,
+                                 c->opt.first_run / 32));
+  DeviceGuard guard(c->opt.device);
+  if ((st = setup_device(c)) != SSA_OK) return bail(st, c->err);
+  if ((st = allocate_common(c, rows)) != SSA_OK) {
+    std::string msg = c->err;
+    dev_free_all(c);
+    return bail(st, msg);
+  }
+  *out = c;
+  return SSA_OK;
+}
+
+int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t n_species, int32_t n_reactions,
+                     int32_t n_ens, const int64_t* N0_ens, const double* rates_ens, const int64_t* runs_ens,
+                     const uint64_t* seed_ens, const ssa_options* opt, ssa_ctx** out) {
+  ssa_ctx* c = nullptr;
+  int perm[3];
+  int st = create_common(reactants, products, n_species, n_reactions, opt, out, &c, perm);
+  if (st != SSA_OK) return st;
+  std::string why;
+  auto bail = [&](int code, std::string msg) {  // by value: msg may live in *c
+    delete c;
+    return fail(nullptr, code, msg);
+  };
+  if (n_ens < 1) return bail(SSA_EINVAL, "n_ens must be >= 1");
+  if (!N0_ens || !rates_ens || !runs_ens || !seed_ens) return bail(SSA_EINVAL, "null batch array");
+  if (c->opt.first_run != 0) return bail(SSA_EINVAL, "first_run must be 0 for a batch");
+  if (c->opt.engine != SSA_ENGINE_BITSLICED) return bail(SSA_EUNSUPPORTED, "batches run on the bit-sliced engine");
+  c->batch = true;
+  c->n_ens = n_ens;
+  long long offset = 0;
+  std::vector<std::pair<int, int>> order;  // (K, e)
+  for (int e = 0; e < n_ens; ++e) {
+    if ((st = check_rates(rates_ens + 3 * e, &why)) != SSA_OK) return bail(st, why);
+    if (runs_ens[e] < 0) return bail(SSA_EINVAL, "runs_ens must be >= 0");
+    int canon[3];
+    long long tot = 0;
+    for (int ci = 0; ci < 3; ++ci) {
+      const long long v = N0_ens[e * 3 + perm[ci]];
+      if (v < 0) return bail(SSA_EINVAL, "initial counts must be >= 0");
+      if (v > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
+      canon[ci] = (int)v;
+      tot += v;
+    }
+    if (tot < 1) return bail(SSA_EINVAL, "the total count must be >= 1");
+    if (tot > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
+    const double* k = rates_ens + 3 * e;
+    c->ens.push_back(make_ensemble(tot, canon, k, c->opt.thin_bits, seed_ens[e], runs_ens[e], offset, 0));
+    c->rates.insert(c->rates.end(), k, k + 3);
+    offset += runs_ens[e];
+    order.push_back({std::max(1, c->ens.back().K), e});
+  }
+  c->n_runs_total = offset;
+  // work items sorted by K, largest first (the longest runs start first)
+  std::stable_sort(order.begin(), order.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+    return a.first > b.first;
+  });
+  for (size_t i = 0; i < order.size();) {
+    const int K = order[i].first;
+    const long long begin = (long long)c->item_ens.size();
+    for (; i < order.size() && order[i].first == K; ++i) {
+      const int e = order[i].second;
+      const long long groups = (c->ens[e].n_runs + 31) / 32;
+      for (long long g = 0; g < groups; ++g) {
+        c->item_ens.push_back(e);
+        c->item_group.push_back((int)g);
+      }
+    }
+    const long long end = (long long)c->item_ens.size();
+    if (end > begin) c->ranges.push_back({K, {begin, end}});
+  }
+  DeviceGuard guard(c->opt.device);
+  if ((st = setup_device(c)) != SSA_OK) return bail(st, c->err);
+  if ((st = allocate_common(c, {})) != SSA_OK) {
+    std::string msg = c->err;
+    dev_free_all(c);
+    return bail(st, msg);
+  }
+  *out = c;
+  return SSA_OK;
+}
+
+int ssa_run(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_snap) {
+  if (!c) return fail(nullptr, SSA_EINVAL, "ctx is NULL");
+  if (!(t_end >= 0.0)) return fail(c, SSA_EINVAL, "t_end must be >= 0");
+  if (n_snap < 0 || n_snap > kMaxSnap) return fail(c, SSA_EINVAL, "n_snap must be in [0, 64]");
+  if (n_snap > 0 && !snapshot_times) return fail(c, SSA_EINVAL, "snapshot_times is NULL");
+  for (int s = 0; s < n_snap; ++s) {
+    if (!(snapshot_times[s] >= 0.0) || snapshot_times[s] > t_end)
+      return fail(c, SSA_EINVAL, "snapshot times must lie in [0, t_end]");
+    if (s > 0 && snapshot_times[s] < snapshot_times[s - 1])
+      return fail(c, SSA_EINVAL, "snapshot times must be ascending");
+  }
+  DeviceGuard guard(c->device);
+  cudaError_t e;
+  c->ran = false;
+  c->n_snap = n_snap;
+  // thresholds [n_ens][n_snap + 1], the last one t_end
+  std::vector<Threshold> thr((size_t)c->n_ens * (n_snap + 1));
+  for (int ei = 0; ei < c->n_ens; ++ei) {
+    for (int s = 0; s < n_snap; ++s) thr[(size_t)ei * (n_snap + 1) + s] = make_threshold(snapshot_times[s], c->ens[ei].lambda);
+    thr[(size_t)ei * (n_snap + 1) + n_snap] = make_threshold(t_end, c->ens[ei].lambda);
+  }
+  int st;
+  if ((st = grow(c, (void**)&c->d_thr, &c->thr_cap, sizeof(Threshold) * thr.size())) != SSA_OK) return st;
+  const size_t hist_bytes = std::max<size_t>(8, (size_t)c->n_ens * n_snap * kHistBins * sizeof(unsigned long long));
+  if ((st = grow(c, (void**)&c->d_hist, &c->hist_cap, hist_bytes)) != SSA_OK) return st;
+  if (c->opt.keep_snap_counts) {
+    const size_t snap_bytes = std::max<size_t>(16, (size_t)n_snap * (size_t)c->n_runs_total * c->S * sizeof(int));
+    if ((st = grow(c, (void**)&c->d_snap, &c->snap_cap, snap_bytes)) != SSA_OK) return st;
+  }
+  if ((e = cudaMemcpyAsync(c->d_thr, thr.data(), sizeof(Threshold) * thr.size(), cudaMemcpyHostToDevice,
+                           c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "upload thresholds");
+  cudaMemsetAsync(c->d_hist, 0, hist_bytes, c->stream);
+  cudaMemsetAsync(c->d_ens_abs, 0, sizeof(unsigned long long) * 4 * c->n_ens, c->stream);
+  cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * (kCounters + c->n_queues), c->stream);
+  cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int) * 4, c->stream);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "clear outputs");
+  if (c->n_runs_total > 0 && (st = launch_runs(c)) != SSA_OK) return st;
+  unsigned int status = 0;
+  if ((e = cudaMemcpyAsync(c->counters, c->d_counters, sizeof(unsigned long long) * kCounters,
+                           cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "read counters");
+  if ((e = cudaMemcpyAsync(&status, c->d_status, sizeof status, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "read status");
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "simulation");
+  c->counters[kErrorFlags] = status;
+  c->ran = true;
+  if (status & kErrRedraw) return fail(c, SSA_EOVERFLOW, "64 redraws of n in a row");
+  if (status & kErrRange) return fail(c, SSA_EOVERFLOW, "internal range check failed");
+  if (status & kErrTimeout) return fail(c, SSA_ETIMEOUT, "a group reached the step budget");
+  return SSA_OK;
+}
+
+int ssa_field_bytes(const ssa_ctx* c, int32_t field, size_t* bytes) {
+  if (!c || !bytes) return fail(const_cast<ssa_ctx*>(c), SSA_EINVAL, "null argument");
+  *bytes = field_bytes(c, field);
+  return SSA_OK;
+}
+
+int ssa_fetch(ssa_ctx* c, int32_t field, void* dst, size_t dst_bytes, int32_t dst_on_device) {
+  if (!c) return fail(nullptr, SSA_EINVAL, "ctx is NULL");
+  if (!c->ran) return fail(c, SSA_ESTATE, "ssa_fetch before a successful ssa_run");
+  if (field < 0 || field > SSA_FIELD_ENS_ABSORBED) return fail(c, SSA_EINVAL, "unknown field");
+  const size_t bytes = field_bytes(c, field);
+  if (field == SSA_FIELD_SNAP_COUNTS && !c->opt.keep_snap_counts)
+    return fail(c, SSA_ESTATE, "snapshot counts were not kept (keep_snap_counts = 0)");
+  if (dst_bytes < bytes) return fail(c, SSA_EINVAL, "destination too small");
+  if (bytes == 0) return SSA_OK;
+  if (!dst) return fail(c, SSA_EINVAL, "dst is NULL");
+  DeviceGuard guard(c->device);
+  const void* src = nullptr;
+  switch (field) {
+    case SSA_FIELD_FINAL_COUNTS: src = c->d_final; break;
+    case SSA_FIELD_ABSORB_TIME: src = c->d_tabs; break;
+    case SSA_FIELD_ABSORB_OUTCOME: src = c->d_outcome; break;
+    case SSA_FIELD_EE_HIST: src = c->d_hist; break;
+    case SSA_FIELD_SNAP_COUNTS: src = c->d_snap; break;
+    case SSA_FIELD_ENS_ABSORBED: src = c->d_ens_abs; break;
+    case SSA_FIELD_COUNTERS:
+      if (!dst_on_device) {
+        std::memcpy(dst, c->counters, bytes);
+        return SSA_OK;
+      }
+      src = nullptr;
+      break;
+  }
+  cudaError_t e;
+  if (field == SSA_FIELD_COUNTERS)
+    e = cudaMemcpyAsync(dst, c->counters, bytes, cudaMemcpyHostToDevice, c->stream);
+  else
+    e = cudaMemcpyAsync(dst, src, bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fetch copy");
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "fetch synchronize");
+  return SSA_OK;
+}
+
+int ssa_destroy(ssa_ctx* c) {
+  if (!c) return SSA_OK;
+  {
+    DeviceGuard guard(c->device);
+    if (c->stream || !c->bufs.empty()) cudaStreamSynchronize(c->stream);
+    dev_free_all(c);
+  }
+  delete c;
+  return SSA_OK;
+}
+
+const char* ssa_last_error(const ssa_ctx* c) { return c ? c->err.c_str() : t_err.c_str(); }
+
+int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user) {
+  if ((alloc == nullptr) != (release == nullptr)) return fail(nullptr, SSA_EINVAL, "alloc and release go together");
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.release = release;
+  g_alloc.user = user;
+  return SSA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+"""The C-ABI library: it builds, loads, exports every declared symbol, and
+validates its arguments before touching the GPU (runs on CPU)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2412_16613_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg.build()
+    return pkg.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w[\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M):
+            name = m.group(1)
+            if name not in ("typedef",) and not text[m.start():m.end()].lstrip().startswith("typedef"):
+                names.add(name)
+    return names
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for n in ["ssa_create", "ssa_create_batch", "ssa_run", "ssa_fetch", "ssa_destroy", "ssa_last_error",
+              "ssa_set_allocator", "ssa_default_options", "ssa_field_bytes", "ssa_version",
+              "bitssa_test_philox", "bitssa_test_bitslice", "bitssa_bench_alu"]:
+        assert n in names, n
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = declared_functions() - exported
+    assert not missing, missing
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+
+
+def test_default_options(lib):
+    o = pkg.ssa_default_options()
+    assert o.precision == pkg.SSA_P64 and o.engine == pkg.SSA_ENGINE_BITSLICED
+    assert o.thin_bits == 32 and o.device == -1 and o.step_budget == 0 and o.first_run == 0
+    assert C.sizeof(pkg.ssa_options) == 80
+
+
+def _create(reac, prod, rates=(1.0, 1.0, 1.0), N0=(16, 16, 32), n_runs=64, **opt):
+    return pkg.ssa_create(reac, prod, rates, N0, n_runs, 0, pkg.ssa_default_options(**opt))
+
+
+F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(reac=[[1, 1, 1], [0, 1, 1], [1, 1, 0]], prod=F_P), pkg.SSA_EINVAL),      # order 3
+    (dict(reac=F_R, prod=[[2, 0, 1], [0, 2, 0], [0, 0, 2]]), pkg.SSA_EINVAL),      # not conserving
+    (dict(reac=F_R, prod=F_P, rates=(1.0, -1.0, 1.0)), pkg.SSA_EINVAL),            # negative rate
+    (dict(reac=F_R, prod=F_P, rates=(0.0, 0.0, 0.0)), pkg.SSA_EINVAL),             # no positive rate
+    (dict(reac=F_R, prod=F_P, rates=(1.0, float("nan"), 1.0)), pkg.SSA_EINVAL),    # nan rate
+    (dict(reac=F_R, prod=F_P, N0=(0, 0, 0)), pkg.SSA_EINVAL),                      # empty system
+    (dict(reac=F_R, prod=F_P, N0=(-1, 1, 1)), pkg.SSA_EINVAL),                     # negative count
+    (dict(reac=F_R, prod=F_P, N0=(30000, 30000, 6000)), pkg.SSA_EUNSUPPORTED),     # N_tot > 65536
+    (dict(reac=F_R, prod=F_P, n_runs=-1), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, thin_bits=0), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, thin_bits=65), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, precision=7), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, block_size=48), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, first_run=16), pkg.SSA_EINVAL),
+    (dict(reac=[[1, 0, 1], [0, 1, 1]], prod=[[2, 0, 0], [0, 2, 0]]), pkg.SSA_EUNSUPPORTED),  # not Frank
+    (dict(reac=[[1, 1, 0], [0, 1, 1], [1, 0, 1]], prod=[[0, 0, 2], [0, 2, 0], [2, 0, 0]]),
+     pkg.SSA_EUNSUPPORTED),                                                           # Frank, wrong order
+])
+def test_validation_before_any_cuda_call(lib, kw, status):
+    with pytest.raises(pkg.SSAError) as ei:
+        _create(**kw)
+    assert ei.value.status == status
+    assert pkg.ssa_last_error()
+
+
+def test_per_run_totals_must_agree(lib):
+    N0 = np.array([[16, 16, 32], [16, 16, 31]])
+    with pytest.raises(pkg.SSAError) as ei:
+        pkg.ssa_create(F_R, F_P, [1, 1, 1], N0, 2, 0)
+    assert ei.value.status == pkg.SSA_EINVAL
+
+
+def test_null_and_order_errors(lib):
+    L = lib
+    assert L.ssa_run(None, 1.0, None, 0) == pkg.SSA_EINVAL
+    assert L.ssa_fetch(None, 0, None, 0, 0) == pkg.SSA_EINVAL
+    assert L.ssa_destroy(None) == pkg.SSA_OK
+    ctx = C.c_void_p()
+    assert L.ssa_create(None, None, 3, 3, None, None, 0, 1, 0, None, C.byref(ctx)) == pkg.SSA_EINVAL
+    assert not ctx.value
+
+
+def test_frank_relabelled_passes_validation(lib):
+    """Species order (A, L, D): validation accepts it; without a GPU the call stops at the device."""
+    reac = [[1, 1, 0], [1, 0, 1], [0, 1, 1]]
+    prod = [[0, 2, 0], [0, 0, 2], [2, 0, 0]]
+    try:
+        ctx = _create(reac, prod, N0=(32, 16, 16))
+    except pkg.SSAError as e:
+        assert e.status == pkg.SSA_ECUDA  # no device here
+    else:
+        pkg.ssa_destroy(ctx)
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package never imports the oracle and has no host implementation of the step."""
+    src_dir = os.path.join(ROOT, "paper_2412_16613_gb300")
+    for name in os.listdir(src_dir):
+        if name.endswith(".py"):
+            text = open(os.path.join(src_dir, name)).read()
+            assert "import oracle" not in text and "from oracle" not in text, name

@@ -1,0 +1,280 @@
+"""GPU parity: libbitssa through its C ABI against the CPU oracle on the same
+seeded inputs.  Counts, outcomes and histograms bit-exact; fp64 event times
+within 1e-12 relative; fp32 clocks within their own tolerance."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2412_16613_gb300 as pkg
+from tests._gpu import FRANK_P, FRANK_R, assert_parity, gpu_run, log_snapshots
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    pkg.use_torch_allocator()
+    yield
+    torch.cuda.synchronize()
+
+
+# --------------------------------------------------------------------------
+# Pieces of the hot path
+# --------------------------------------------------------------------------
+def test_philox_device_matches_oracle_and_curand():
+    rng = np.random.default_rng(1)
+    n = 4096
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    ours = pkg.bitssa_test_philox(ctr, key, which=0)
+    curand = pkg.bitssa_test_philox(ctr, key, which=1)
+    assert np.array_equal(ours, curand)
+    for i in range(0, n, 97):
+        assert oracle.philox4x32_10(ctr[i], key[i]) == curand[i].tolist()
+
+
+@pytest.mark.parametrize("op", [0, 1, 2, 3, 4])
+def test_bitslice_primitives_exhaustive(op):
+    x, y = np.meshgrid(np.arange(256), np.arange(256), indexing="ij")
+    x, y = x.ravel(), y.ravel()
+    out = pkg.bitssa_test_bitslice(op, x, y)
+    if op == 0:
+        want = x + y
+    elif op == 1:
+        want = x - y
+    elif op == 2:
+        want = (x < y).astype(np.int64)
+    elif op == 3:
+        want = x * y
+    else:
+        want = x + np.select([y == 1, y == 2, y == 3], [3, -2, 5], 0)
+    assert np.array_equal(out, want)
+
+
+def test_paper_fig1_sum():
+    """Fig. 1: augend 1 plus addend 1 gives 2 (tests/golden/paper_bitwise_examples.txt)."""
+    x = np.ones(32, dtype=np.int64)
+    assert np.all(pkg.bitssa_test_bitslice(0, x, x) == 2)
+
+
+# --------------------------------------------------------------------------
+# Whole runs against the oracle
+# --------------------------------------------------------------------------
+def test_parity_n64_all_runs():
+    """N_tot = 64, (16, 16, 32), 64 runs in two groups, seed 0, t_end 10."""
+    snaps = [0.01, 0.05, 0.1, 0.5, 10.0]
+    g = gpu_run((16, 16, 32), 64, seed=0, t_end=10.0, snaps=snaps)
+    r = oracle.run(oracle.frank(), (16, 16, 32), 64, seed=0, t_end=10.0, snap_times=snaps)
+    ok = assert_parity(g, r)
+    assert ok.all()
+    assert g["counters"]["reactions"] == r["reactions"].sum()
+    assert g["counters"]["lane_steps"] == r["steps"].sum()
+    assert np.array_equal(g["ee_hist"], oracle.ee_histogram(r["snap_counts"]))
+
+
+def test_parity_n1024_subset_ragged():
+    """N_tot = 1024, (256, 256, 512), 4113 runs (129 groups, ragged last group), 10 log-spaced
+    snapshots, t_end = 50: every run, every snapshot, the histograms and the counters."""
+    n = 4096 + 17
+    snaps = log_snapshots(50.0, 10)
+    g = gpu_run((256, 256, 512), n, seed=0, t_end=50.0, snaps=snaps)
+    r = oracle.run(oracle.frank(), (256, 256, 512), n, seed=0, t_end=50.0, snap_times=snaps,
+                   threads=THREADS)
+    ok = assert_parity(g, r)
+    if ok.all():
+        assert np.array_equal(g["ee_hist"], oracle.ee_histogram(r["snap_counts"]))
+        assert g["counters"]["reactions"] == r["reactions"].sum()
+        assert g["counters"]["lane_steps"] == r["steps"].sum()
+    assert np.all(g["ee_hist"].sum(1) == n)
+    assert np.all(g["final_counts"].sum(1) == 1024)
+
+
+def test_parity_n1024_full_size_sampled():
+    """The benchmark workload itself: 2^20 runs at N_tot = 1024; the oracle recomputes a
+    sample of runs one by one, and every run satisfies the invariants."""
+    n = 1 << 20
+    snaps = log_snapshots(50.0, 10)
+    g = gpu_run((256, 256, 512), n, seed=0, t_end=50.0, snaps=snaps, keep_snaps=False)
+    rng = np.random.default_rng(2024)
+    ids = np.unique(np.concatenate([[0, 31, 32, n - 1], rng.integers(0, n, 60)]))
+    r = oracle.run(oracle.frank(), (256, 256, 512), run_ids=ids, seed=0, t_end=50.0, snap_times=snaps,
+                   threads=THREADS)
+    sub = {k: g[k][ids] for k in ("final_counts", "outcome", "t_abs")}
+    assert_parity(sub, r, snaps=False, min_ok=0.95)
+    fc = g["final_counts"]
+    assert np.all(fc.sum(1) == 1024)
+    absorbed = g["outcome"] >= 0
+    assert np.all((fc[absorbed] > 0).sum(1) == 1)
+    assert np.all(g["ee_hist"].sum(1) == n)
+    assert g["counters"]["absorbed"] == absorbed.sum()
+    pL, pD = np.mean(g["outcome"] == 0), np.mean(g["outcome"] == 1)
+    assert abs(pL - pD) < 5 * math.sqrt((pL + pD) / n)
+
+
+@pytest.mark.parametrize("mode,omode,rtol,tie", [
+    (pkg.SSA_P64_LOGSUM, oracle.P64, 1e-12, 1e-12),
+    (pkg.SSA_P32_KAHAN, oracle.P32_KAHAN, 2e-5, 5e-6),
+    (pkg.SSA_P32_D64ACC, oracle.P32_D64ACC, 2e-5, 5e-6),
+])
+def test_parity_precision_modes(mode, omode, rtol, tie):
+    snaps = log_snapshots(50.0, 10)
+    n = 1024 + 5
+    g = gpu_run((256, 256, 512), n, seed=3, t_end=50.0, snaps=snaps, precision=mode)
+    r = oracle.run(oracle.frank(), (256, 256, 512), n, seed=3, t_end=50.0, snap_times=snaps,
+                   precision=omode, threads=THREADS)
+    assert_parity(g, r, rtol=rtol, tie=tie, min_ok=0.97)
+
+
+def test_results_do_not_depend_on_launch_shape():
+    snaps = [0.005, 0.02]
+    base = gpu_run((256, 256, 512), 3000, seed=5, t_end=0.05, snaps=snaps)
+    for block, bpsm in [(32, 1), (128, 0), (256, 1)]:
+        g = gpu_run((256, 256, 512), 3000, seed=5, t_end=0.05, snaps=snaps, block_size=block,
+                    blocks_per_sm=bpsm)
+        for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
+            assert np.array_equal(g[k], base[k]), k
+        assert g["counters"] == base["counters"]
+
+
+def test_sharded_contexts_equal_one_context():
+    """Two contexts holding runs [0, 2048) and [2048, 4096) (first_run) give the runs of one
+    context of 4096: the stream is keyed by the global group index."""
+    snaps = [0.01, 0.03]
+    whole = gpu_run((256, 256, 512), 4096, seed=9, t_end=0.1, snaps=snaps)
+    a = gpu_run((256, 256, 512), 2048, seed=9, t_end=0.1, snaps=snaps, first_run=0)
+    b = gpu_run((256, 256, 512), 2048, seed=9, t_end=0.1, snaps=snaps, first_run=2048)
+    for k in ("final_counts", "outcome", "t_abs"):
+        assert np.array_equal(np.concatenate([a[k], b[k]]), whole[k]), k
+    assert np.array_equal(a["ee_hist"] + b["ee_hist"], whole["ee_hist"])
+
+
+def test_parity_per_run_initial_states():
+    """Independent multinomial initial states around the racemic point (Sec. 5, Fig. 4)."""
+    rng = np.random.default_rng(77)
+    n = 2000
+    init = rng.multinomial(256, [0.25, 0.25, 0.5], size=n)
+    snaps = [0.01, 0.05]
+    g = gpu_run(init, n, seed=4, t_end=1.0, snaps=snaps)
+    r = oracle.run(oracle.frank(), init, seed=4, t_end=1.0, snap_times=snaps, threads=THREADS)
+    assert_parity(g, r)
+
+
+def test_relabelled_species_give_the_same_runs():
+    """Species order (A, L, D) with the reactions in Frank's order: the same trajectories,
+    reported in the caller's species order."""
+    reac = [[1, 1, 0], [1, 0, 1], [0, 1, 1]]
+    prod = [[0, 2, 0], [0, 0, 2], [2, 0, 0]]
+    snaps = [0.02]
+    base = gpu_run((16, 16, 32), 256, seed=6, t_end=1.0, snaps=snaps)
+    g = gpu_run((32, 16, 16), 256, seed=6, t_end=1.0, snaps=snaps, reac=reac, prod=prod)
+    assert np.array_equal(g["final_counts"][:, [1, 2, 0]], base["final_counts"])
+    assert np.array_equal(g["snap_counts"][:, :, [1, 2, 0]], base["snap_counts"])
+    remap = np.array([-2, -1, 2, 0, 1])  # caller's outcome -2..2 (A=0, L=1, D=2) -> (L=0, D=1, A=2)
+    assert np.array_equal(remap[g["outcome"] + 2], base["outcome"])
+
+
+@pytest.mark.parametrize("rates,q", [((1.0, 0.5, 0.25), 32), ((0.7, 2.0, 1.3), 64), ((0.0, 0.0, 1.0), 32),
+                                     ((1.0, 1.0, 0.5), 5)])
+def test_parity_thinning(rates, q):
+    snaps = [0.01, 0.1]
+    n = 1024 + 3
+    g = gpu_run((64, 64, 128), n, seed=12, t_end=2.0, snaps=snaps, rates=rates, thin_bits=q)
+    r = oracle.run(oracle.frank(*rates), (64, 64, 128), n, seed=12, t_end=2.0, snap_times=snaps,
+                   thin_bits=q, threads=THREADS)
+    assert_parity(g, r)
+
+
+# --------------------------------------------------------------------------
+# Edge cases
+# --------------------------------------------------------------------------
+def test_empty_context():
+    g = gpu_run((16, 16, 32), 0, t_end=1.0, snaps=[0.5])
+    assert g["final_counts"].size == 0 and g["ee_hist"].sum() == 0
+
+
+@pytest.mark.parametrize("init", [(1, 0, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 0, 50), (25, 0, 0),
+                                  (2, 1, 0)])
+def test_small_and_absorbed_systems(init):
+    n = 70
+    snaps = [0.0, 0.5, 3.0]
+    g = gpu_run(init, n, seed=2, t_end=3.0, snaps=snaps)
+    r = oracle.run(oracle.frank(), init, n, seed=2, t_end=3.0, snap_times=snaps)
+    assert_parity(g, r)
+
+
+def test_t_end_zero_and_snapshot_at_t_end():
+    g = gpu_run((10, 10, 10), 40, seed=1, t_end=0.0, snaps=[0.0])
+    assert np.all(g["final_counts"] == [10, 10, 10]) and np.all(g["outcome"] == -1)
+    assert np.all(np.isinf(g["t_abs"])) and np.all(g["snap_counts"] == [10, 10, 10])
+    snaps = [0.02, 0.04]
+    g = gpu_run((16, 16, 32), 96, seed=1, t_end=0.04, snaps=snaps)
+    r = oracle.run(oracle.frank(), (16, 16, 32), 96, seed=1, t_end=0.04, snap_times=snaps)
+    assert_parity(g, r)
+    assert np.array_equal(g["snap_counts"][1], g["final_counts"])
+
+
+def test_step_budget_reports_timeout():
+    g = gpu_run((256, 256, 512), 64, seed=1, t_end=50.0, step_budget=100, expect_status=pkg.SSA_ETIMEOUT)
+    assert g["counters"]["group_steps"] == 2 * 100
+    r = oracle.run(oracle.frank(), (256, 256, 512), 64, seed=1, t_end=50.0, step_budget=100, check=False)
+    assert np.array_equal(g["final_counts"], r["final_counts"])
+
+
+def test_fetch_before_run_is_a_state_error():
+    ctx = pkg.ssa_create(FRANK_R, FRANK_P, [1, 1, 1], (16, 16, 32), 32, 0)
+    try:
+        with pytest.raises(pkg.SSAError) as ei:
+            pkg.ssa_fetch(ctx, pkg.SSA_FIELD_FINAL_COUNTS)
+        assert ei.value.status == pkg.SSA_ESTATE
+    finally:
+        pkg.ssa_destroy(ctx)
+
+
+def test_repeated_runs_are_identical():
+    import torch
+    o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream())
+    ctx = pkg.ssa_create(FRANK_R, FRANK_P, [1, 1, 1], (64, 64, 128), 5000, 3, o)
+    try:
+        pkg.ssa_run(ctx, 1.0, [0.01])
+        a = pkg.fetch_all(ctx)
+        pkg.ssa_run(ctx, 1.0, [0.01])
+        b = pkg.fetch_all(ctx)
+        dev = torch.empty(5000 * 3, dtype=torch.int32, device="cuda")
+        pkg.ssa_fetch(ctx, pkg.SSA_FIELD_FINAL_COUNTS, dev)
+    finally:
+        pkg.ssa_destroy(ctx)
+    for k in ("final_counts", "t_abs", "outcome", "ee_hist"):
+        assert np.array_equal(a[k], b[k])
+    assert a["counters"] == b["counters"]
+    assert np.array_equal(dev.cpu().numpy().reshape(-1, 3), a["final_counts"])
+
+
+# --------------------------------------------------------------------------
+# The one-thread-per-run baseline samples the same process
+# --------------------------------------------------------------------------
+def test_thread_per_run_baseline_distribution():
+    n = 200_000
+    g = gpu_run((16, 16, 32), n, seed=8, t_end=np.inf, engine=pkg.SSA_ENGINE_THREAD_PER_RUN)
+    r = oracle.run(oracle.frank(), (16, 16, 32), run_ids=np.arange(20_000) * 32, seed=8, t_end=np.inf,
+                   threads=THREADS)
+    assert np.all(g["outcome"] >= 0)
+    assert np.all(g["final_counts"].sum(1) == 64)
+    pL = np.mean(g["outcome"] == 0)
+    pL_ref = np.mean(r["outcome"] == 0)
+    assert abs(pL - pL_ref) < 5 * math.sqrt(0.25 / n + 0.25 / len(r["outcome"]))
+    se = math.sqrt(g["t_abs"].var() / n + r["t_abs"].var() / len(r["t_abs"]))
+    assert abs(g["t_abs"].mean() - r["t_abs"].mean()) < 5 * se
+    assert g["counters"]["reactions"] > 0
