@@ -167,6 +167,7 @@ def workload_config(world):
 
 
 def main():
+    global RUNS_PER_GPU
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -177,8 +178,11 @@ def main():
     ap.add_argument("--no-baselines", action="store_true", help="skip the K7 and CPU legs")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--runs", type=int, default=RUNS_PER_GPU,
+                    help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
     args = ap.parse_args()
     rank, world, local = env_rank()
+    RUNS_PER_GPU = args.runs
 
     if args.impl == "reference":
         if world > 1:

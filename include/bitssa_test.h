@@ -33,7 +33,8 @@ int bitssa_test_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, 
  *   op 1: x - y (two's complement on 9 planes, read back as a signed value)
  *   op 2: [x < y] (borrow chain)
  *   op 3: x * y (schoolbook product, 16 planes)
- *   op 4: x + c with c = +3 where y == 1, -2 where y == 2, +5 where y == 3, else 0
+ *   op 4: x + c with c = +3 where y % 4 == 1, -2 where y % 4 == 2, +5 where y % 4 == 3,
+ *         else 0
  *         (the masked constant update of Eq. equation-v, on 10 signed planes)
  */
 int bitssa_test_bitslice(int32_t op, const int64_t* x, const int64_t* y, int64_t* out, int64_t n);

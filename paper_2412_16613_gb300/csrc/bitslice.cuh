@@ -128,6 +128,23 @@ __device__ __forceinline__ void multiply(uint32_t (&out)[RW], const uint32_t (&x
   }
 }
 
+// acc += x * y (unsigned), modulo 2^RW: each row of the schoolbook product is rippled into acc.
+template <int RW, int XW, int YW>
+__device__ __forceinline__ void multiply_add(uint32_t (&acc)[RW], const uint32_t (&x)[XW],
+                                             const uint32_t (&y)[YW]) {
+#pragma unroll
+  for (int j = 0; j < YW; ++j) {
+    uint32_t carry = 0u;
+#pragma unroll
+    for (int i = j; i < RW; ++i) {
+      const uint32_t t = (i - j < XW) ? (x[i - j] & y[j]) : 0u;
+      const uint32_t s = xor3(acc[i], t, carry);
+      carry = maj(acc[i], t, carry);
+      acc[i] = s;
+    }
+  }
+}
+
 // Value of one lane, sign-extended from W planes when SIGNED.
 template <bool SIGNED, int W>
 __device__ __forceinline__ long long lane_value(const uint32_t (&x)[W], int lane) {

@@ -96,31 +96,91 @@ __device__ __forceinline__ int ee_bin(int l, int d) {
   return b > 63 ? 63 : b;
 }
 
-template <int K>
-__device__ __forceinline__ void run_group(const FrankLaunch& p, const Ensemble& e, const Threshold* thr,
-                                          long long group_local, int ens_index, unsigned int* s_hist,
-                                          FrankCounters& cnt, unsigned int& errors) {
-  using Sh = FrankShape<K>;
-  constexpr int B = Sh::B, WP = Sh::WP, WU3 = Sh::WU3, WR1 = Sh::WR1, WR3 = Sh::WR3;
-  constexpr int NC0 = Sh::NC0, NCR = Sh::NCR;
 
+// Everything one thread keeps about its group between steps (all in registers).
+template <int K>
+struct GroupState {
+  uint32_t S1[K], S2[K], S3[K];
+  uint32_t L[FrankShape<K>::B], P[FrankShape<K>::WP], U[FrankShape<K>::WP];
+  uint32_t R1[FrankShape<K>::WR1], R3[FrankShape<K>::WR3];
+  uint32_t live;       // lanes that can still react
+  uint32_t valid;      // lanes that hold a run (the last group may be partial)
+  uint32_t sgroup;     // stream group index
+  int nvalid;
+  int ens;             // ensemble index
+  int snap;            // next snapshot
+  long long row0;      // output row of lane 0
+  unsigned long long step;
+  double m;            // product clock: exp(-Lambda t) = m 2^E
+  long long E;
+  double t;            // fp64 sum clocks
+  float t_f, c_f;      // Kahan clock and compensation
+  Threshold cur;       // next time point to cross (snapshot or t_end)
+  unsigned long long reactions, lane_steps, redraws;
+  bool done;
+};
+
+template <int K>
+__device__ __forceinline__ uint32_t live_lanes(const GroupState<K>& s, const Ensemble& e) {
+  if (e.active == 7u) return bs::nonzero(s.S3);
+  uint32_t m = 0u;
+  if (e.active & 1u) m |= bs::nonzero(s.S1);
+  if (e.active & 2u) m |= bs::differ(s.S2, s.S1);
+  if (e.active & 4u) m |= bs::differ(s.S3, s.S2);
+  return m;
+}
+
+// The current state of every valid lane into snapshot `snap`: histogram and per-run counts.
+template <int K>
+__device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K>& s, const Ensemble& e, int snap,
+                                     unsigned int* s_hist) {
+  using Sh = FrankShape<K>;
+  for (int l = 0; l < s.nvalid; ++l) {
+    int cl, cd, ca;
+    lane_counts<Sh::B, Sh::WP>(s.L, s.U, e.n_tot, l, cl, cd, ca);
+    if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(cl, cd)], 1u);
+    else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + ee_bin(cl, cd)], 1ull);
+    if (p.snap_counts) {
+      int* o = p.snap_counts + ((long long)snap * p.n_runs_total + s.row0 + l) * p.n_species;
+      o[p.perm[0]] = cl;
+      o[p.perm[1]] = cd;
+      o[p.perm[2]] = ca;
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ double group_time(const GroupState<K>& s, const Ensemble& e, int precision) {
+  if (precision == kP64) return -(log(s.m) + (double)s.E * kLn2) / e.lambda;
+  if (precision == kP32Kahan) return (double)s.t_f;
+  return s.t;
+}
+
+// Set up group `group_local` of ensemble `e`: initial planes, cumulative propensities by
+// bit-sliced products, the linear forms, the runs that start absorbed.
+template <int K>
+__device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K>& s, const Ensemble& e,
+                                           const Threshold* thr, long long group_local, int ens_index,
+                                           unsigned int* s_hist) {
+  using Sh = FrankShape<K>;
+  constexpr int B = Sh::B, WP = Sh::WP, WR1 = Sh::WR1, WR3 = Sh::WR3;
   const long long run0 = group_local * 32;
   const long long left = e.n_runs - run0;
-  const int nvalid = left >= 32 ? 32 : (int)left;
-  const uint32_t valid = nvalid >= 32 ? 0xFFFFFFFFu : ((1u << nvalid) - 1u);
-  const uint32_t sgroup = (uint32_t)(e.group_base + group_local);
-  const PhiloxKey key{(uint32_t)e.seed, (uint32_t)(e.seed >> 32)};
-  const long long row0 = e.run_offset + run0;
+  s.nvalid = left >= 32 ? 32 : (int)left;
+  s.valid = s.nvalid >= 32 ? 0xFFFFFFFFu : ((1u << s.nvalid) - 1u);
+  s.sgroup = (uint32_t)(e.group_base + group_local);
+  s.row0 = e.run_offset + run0;
+  s.ens = ens_index;
   const int n_tot = e.n_tot;
 
-  // ---- initial planes (padding lanes hold (0, 0, N): absorbed, never counted)
+  // initial planes (padding lanes hold (0, 0, N): absorbed, never counted)
   uint32_t Lp[B], Dp[B], Ap[B];
   if (p.init_counts) {
     bs::broadcast(Lp, 0);
     bs::broadcast(Dp, 0);
     bs::broadcast(Ap, n_tot);
-    for (int l = 0; l < nvalid; ++l) {
-      const int* c = p.init_counts + (row0 + l) * 3;
+    for (int l = 0; l < s.nvalid; ++l) {
+      const int* c = p.init_counts + (s.row0 + l) * 3;
       bs::set_lane(Lp, l, c[0]);
       bs::set_lane(Dp, l, c[1]);
       bs::set_lane(Ap, l, c[2]);
@@ -131,161 +191,122 @@ __device__ __forceinline__ void run_group(const FrankLaunch& p, const Ensemble& 
     bs::broadcast(Ap, e.init[2]);
 #pragma unroll
     for (int i = 0; i < B; ++i) {
-      Lp[i] &= valid;
-      Dp[i] &= valid;
-      Ap[i] = (Ap[i] & valid) | (((n_tot >> i) & 1) ? ~valid : 0u);
+      Lp[i] &= s.valid;
+      Dp[i] &= s.valid;
+      Ap[i] = (Ap[i] & s.valid) | (((n_tot >> i) & 1) ? ~s.valid : 0u);
     }
   }
-
-  // ---- cumulative propensities by bit-sliced products (Eq. equation-as)
-  uint32_t S1[K], S2[K], S3[K];
-  {
-    uint32_t h[K];
-    bs::multiply(S1, Ap, Lp);
-    bs::multiply(h, Ap, Dp);
+  // cumulative propensities (Eq. equation-as)
+  bs::multiply(s.S1, Ap, Lp);
+  bs::multiply(s.S2, Ap, Dp);
+  bs::multiply_add(s.S2, Ap, Lp);  // A D + A L
 #pragma unroll
-    for (int i = 0; i < K; ++i) S2[i] = S1[i];
-    bs::add_signed(S2, h, 0u);
-    bs::multiply(h, Lp, Dp);
+  for (int i = 0; i < K; ++i) s.S3[i] = s.S2[i];
+  bs::multiply_add(s.S3, Lp, Dp);  // + L D
+  // the linear forms, by ripple adds of (shifted, complemented) count planes
 #pragma unroll
-    for (int i = 0; i < K; ++i) S3[i] = S2[i];
-    bs::add_signed(S3, h, 0u);
+  for (int i = 0; i < B; ++i) s.L[i] = Lp[i];
+  uint32_t c = 0u;  // P = A + ~L = A - L - 1
+#pragma unroll
+  for (int i = 0; i < WP; ++i) {
+    const uint32_t a = bs::plane<false>(Ap, i), b = ~bs::plane<false>(Lp, i);
+    s.P[i] = bs::xor3(a, b, c);
+    c = bs::maj(a, b, c);
   }
-
-  // ---- the linear forms, by ripple adds of (shifted, complemented) count planes
-  uint32_t Lm[B], P[WP], U[WP], R1[WR1], R3[WR3];
+  c = 0xFFFFFFFFu;  // U = P + ~D + 1 = A - L - D - 1
 #pragma unroll
-  for (int i = 0; i < B; ++i) Lm[i] = Lp[i];
-  {
-    uint32_t c = 0u;  // P = A + ~L = A - L - 1
-#pragma unroll
-    for (int i = 0; i < WP; ++i) {
-      const uint32_t a = bs::plane<false>(Ap, i), b = ~bs::plane<false>(Lp, i);
-      P[i] = bs::xor3(a, b, c);
-      c = bs::maj(a, b, c);
-    }
-    c = 0xFFFFFFFFu;  // U = P + ~D + 1 = A - L - D - 1
-#pragma unroll
-    for (int i = 0; i < WP; ++i) {
-      const uint32_t a = P[i], b = ~bs::plane<false>(Dp, i);
-      U[i] = bs::xor3(a, b, c);
-      c = bs::maj(a, b, c);
-    }
-    // R1 = (L << 1) + ~A - 1 = 2L - A - 2
-    c = 0u;
-#pragma unroll
-    for (int i = 0; i < WR1; ++i) {
-      const uint32_t a = i == 0 ? 0u : bs::plane<false>(Lp, i - 1), b = ~bs::plane<false>(Ap, i);
-      R1[i] = bs::xor3(a, b, c);
-      c = bs::maj(a, b, c);
-    }
-    bs::add_select3<-1, -1, -1>(R1, 0xFFFFFFFFu, 0u, 0u);
-    // R3 = L + D + (~A << 1) - 1 = L + D - 2A - 3
-    c = 0u;
-#pragma unroll
-    for (int i = 0; i < WR3; ++i) {
-      const uint32_t a = bs::plane<false>(Lp, i), b = bs::plane<false>(Dp, i);
-      R3[i] = bs::xor3(a, b, c);
-      c = bs::maj(a, b, c);
-    }
-    c = 0u;
-#pragma unroll
-    for (int i = 0; i < WR3; ++i) {
-      const uint32_t a = R3[i], b = i == 0 ? 0u : ~bs::plane<false>(Ap, i - 1);
-      R3[i] = bs::xor3(a, b, c);
-      c = bs::maj(a, b, c);
-    }
-    bs::add_select3<-1, -1, -1>(R3, 0xFFFFFFFFu, 0u, 0u);
+  for (int i = 0; i < WP; ++i) {
+    const uint32_t a = s.P[i], b = ~bs::plane<false>(Dp, i);
+    s.U[i] = bs::xor3(a, b, c);
+    c = bs::maj(a, b, c);
   }
-
-  // ---- which lanes can still react: some reaction with k_r > 0 has h_r > 0
-  const bool all_active = e.active == 7u;
-  auto live_lanes = [&]() -> uint32_t {
-    if (all_active) return bs::nonzero(S3);
-    uint32_t m = 0u;
-    if (e.active & 1u) m |= bs::nonzero(S1);
-    if (e.active & 2u) m |= bs::differ(S2, S1);
-    if (e.active & 4u) m |= bs::differ(S3, S2);
-    return m;
-  };
-  uint32_t live = live_lanes() & valid;
-  // runs that start absorbed are absorbed at t = 0
-  {
-    uint32_t at0 = valid & ~live;
-    while (at0) {
-      const int l = __ffs(at0) - 1;
-      at0 &= at0 - 1;
-      p.t_abs[row0 + l] = 0.0;
-    }
+  c = 0u;  // R1 = (L << 1) + ~A - 1 = 2L - A - 2
+#pragma unroll
+  for (int i = 0; i < WR1; ++i) {
+    const uint32_t a = i == 0 ? 0u : bs::plane<false>(Lp, i - 1), b = ~bs::plane<false>(Ap, i);
+    s.R1[i] = bs::xor3(a, b, c);
+    c = bs::maj(a, b, c);
   }
+  bs::add_select3<-1, -1, -1>(s.R1, 0xFFFFFFFFu, 0u, 0u);
+  c = 0u;  // R3 = L + D + (~A << 1) - 1 = L + D - 2A - 3
+#pragma unroll
+  for (int i = 0; i < WR3; ++i) {
+    const uint32_t a = bs::plane<false>(Lp, i), b = bs::plane<false>(Dp, i);
+    s.R3[i] = bs::xor3(a, b, c);
+    c = bs::maj(a, b, c);
+  }
+  c = 0u;
+#pragma unroll
+  for (int i = 0; i < WR3; ++i) {
+    const uint32_t a = s.R3[i], b = i == 0 ? 0u : ~bs::plane<false>(Ap, i - 1);
+    s.R3[i] = bs::xor3(a, b, c);
+    c = bs::maj(a, b, c);
+  }
+  bs::add_select3<-1, -1, -1>(s.R3, 0xFFFFFFFFu, 0u, 0u);
 
-  // ---- snapshot capture: the current state of every valid lane
-  const int n_snap = p.n_snap;
-  auto capture = [&](int snap) {
-    for (int l = 0; l < nvalid; ++l) {
-      int cl, cd, ca;
-      lane_counts<B, WP>(Lm, U, n_tot, l, cl, cd, ca);
-      if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(cl, cd)], 1u);
-      else atomicAdd(&p.hist[((long long)ens_index * n_snap + snap) * kHistBins + ee_bin(cl, cd)], 1ull);
-      if (p.snap_counts) {
-        int* o = p.snap_counts + ((long long)snap * p.n_runs_total + row0 + l) * p.n_species;
-        o[p.perm[0]] = cl;
-        o[p.perm[1]] = cd;
-        o[p.perm[2]] = ca;
-      }
-    }
-  };
+  s.live = live_lanes(s, e) & s.valid;
+  uint32_t at0 = s.valid & ~s.live;  // runs that start absorbed are absorbed at t = 0
+  while (at0) {
+    const int l = __ffs(at0) - 1;
+    at0 &= at0 - 1;
+    p.t_abs[s.row0 + l] = 0.0;
+  }
+  s.step = 0;
+  s.m = 1.0;
+  s.E = 0;
+  s.t = 0.0;
+  s.t_f = 0.0f;
+  s.c_f = 0.0f;
+  s.snap = 0;
+  s.cur = thr[0];
+  s.reactions = s.lane_steps = s.redraws = 0;
+  s.done = s.live == 0u;
+  if (s.done)
+    for (; s.snap < p.n_snap; ++s.snap) capture<K>(p, s, e, s.snap, s_hist);
+}
 
-  // ---- clock state
+// One group step (see the file header).  Never leaves the caller's loop: a group that
+// stops sets s.done.
+template <int K>
+__device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K>& s, const Ensemble& e,
+                                           const Threshold* thr, unsigned int* s_hist, unsigned int& errors) {
+  using Sh = FrankShape<K>;
+  constexpr int WP = Sh::WP, WU3 = Sh::WU3, WR1 = Sh::WR1, WR3 = Sh::WR3;
+  constexpr int NC0 = Sh::NC0, NCR = Sh::NCR;
+  const PhiloxKey key{(uint32_t)e.seed, (uint32_t)(e.seed >> 32)};
   const int precision = p.precision;
-  double m = 1.0;        // product clock: exp(-Lambda t) = m 2^E
-  long long E = 0;
-  double t = 0.0;        // fp64 sum clocks
-  float t_f = 0.0f, c_f = 0.0f;  // Kahan clock
-  int snap = 0;
-  Threshold cur = thr[0];
-  auto group_time = [&]() -> double {
-    if (precision == kP64) return -(log(m) + (double)E * kLn2) / e.lambda;
-    if (precision == kP32Kahan) return (double)t_f;
-    return t;
-  };
 
-  unsigned long long step = 0;
-  unsigned long long reactions = 0, lane_steps = 0, redraws = 0;
-  bool done = live == 0u;
-  if (done)
-    for (; snap < n_snap; ++snap) capture(snap);
-
-  while (!done) {
-    if (p.step_budget > 0 && (long long)step >= p.step_budget) {
-      errors |= kErrTimeout;
-      break;
-    }
-    // (1) the random words of attempt 0
-    uint32_t w[4 * NC0];
+  if (p.step_budget > 0 && (long long)s.step >= p.step_budget) {
+    errors |= kErrTimeout;
+    s.done = true;
+    return;
+  }
+  // (1) the random words of attempt 0
+  uint32_t w[4 * NC0];
 #pragma unroll
-    for (int c = 0; c < NC0; ++c) {
-      const uint4 r = philox4x32_10(stream_counter(sgroup, step, 0u, 0u, (uint32_t)c), key);
-      w[4 * c + 0] = r.x;
-      w[4 * c + 1] = r.y;
-      w[4 * c + 2] = r.z;
-      w[4 * c + 3] = r.w;
-    }
-    uint32_t n[K];
+  for (int c = 0; c < NC0; ++c) {
+    const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, (uint32_t)c), key);
+    w[4 * c + 0] = r.x;
+    w[4 * c + 1] = r.y;
+    w[4 * c + 2] = r.z;
+    w[4 * c + 3] = r.w;
+  }
+  uint32_t n[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i) n[i] = w[i];
-    uint32_t need = ~bs::less_than_const(n, e.lambda_int) & live;
-    uint32_t attempt = 0u;
-    while (need) {
-      if (++attempt >= 64u) {
+  for (int i = 0; i < K; ++i) n[i] = w[i];
+  uint32_t need = ~bs::less_than_const(n, e.lambda_int) & s.live;
+  if (need) {
+    for (uint32_t attempt = 1u; need; ++attempt) {
+      if (attempt >= 64u) {
         errors |= kErrRedraw;
-        break;
+        s.done = true;
+        return;
       }
-      ++redraws;
+      ++s.redraws;
       uint32_t wr[4 * NCR];
 #pragma unroll
       for (int c = 0; c < NCR; ++c) {
-        const uint4 r = philox4x32_10(stream_counter(sgroup, step, attempt, 0u, (uint32_t)c), key);
+        const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, attempt, 0u, (uint32_t)c), key);
         wr[4 * c + 0] = r.x;
         wr[4 * c + 1] = r.y;
         wr[4 * c + 2] = r.z;
@@ -295,227 +316,248 @@ __device__ __forceinline__ void run_group(const FrankLaunch& p, const Ensemble& 
       for (int i = 0; i < K; ++i) n[i] = (n[i] & ~need) | (wr[i] & need);
       need &= ~bs::less_than_const(n, e.lambda_int);
     }
-    if (need) break;
-
-    // (2) the clock: the candidate time of this step's event
-    double m_new = m, t_new = t;
-    long long E_new = E;
-    float tf_new = t_f, cf_new = c_f;
-    bool crossed;
-    if (precision == kP64) {
-      const unsigned long long x = ((unsigned long long)w[K + 1] << 21) | (w[K] >> 11);
-      const double u = (double)(x + 1ull) * 0x1p-53;
-      const double mm = m * u;
-      const int hi = __double2hiint(mm), lo = __double2loint(mm);
-      E_new = E + (long long)(((hi >> 20) & 0x7FF) - 1023);
-      m_new = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, lo);
-      crossed = E_new < cur.E || (E_new == cur.E && m_new < cur.m);
-    } else if (precision == kP64LogSum) {
-      const unsigned long long x = ((unsigned long long)w[K + 1] << 21) | (w[K] >> 11);
-      const double u = (double)(x + 1ull) * 0x1p-53;
-      t_new = t + (-log(u) / e.lambda);
-      crossed = t_new > cur.t;
-    } else {
-      const float u = (float)((w[K + 1] >> 8) + 1u) * 0x1p-24f;
-      const float tau = -logf(u) * e.inv_lambda_f;
-      if (precision == kP32Kahan) {
-        const float y = tau - c_f;
-        const float s = t_f + y;
-        cf_new = (s - t_f) - y;
-        tf_new = s;
-        crossed = s > cur.t_f;
-      } else {
-        t_new = t + (double)tau;
-        crossed = t_new > cur.t;
-      }
-    }
-    if (crossed) {
-      bool stop = false;
-      for (;;) {
-        if (snap >= n_snap) {
-          stop = true;  // t_end passed: the event is not applied
-          break;
-        }
-        capture(snap);
-        ++snap;
-        cur = thr[snap];
-        if (precision == kP64) crossed = E_new < cur.E || (E_new == cur.E && m_new < cur.m);
-        else if (precision == kP32Kahan) crossed = tf_new > cur.t_f;
-        else crossed = t_new > cur.t;
-        if (!crossed) break;
-      }
-      if (stop) break;
-    }
-    m = m_new;
-    E = E_new;
-    t = t_new;
-    t_f = tf_new;
-    c_f = cf_new;
-
-    // (3) comparators and changer words
-    const uint32_t lt1 = bs::less_than(n, S1);
-    const uint32_t lt2 = bs::less_than(n, S2);
-    const uint32_t lt3 = bs::less_than(n, S3);
-    uint32_t x1 = lt1 & live, x2 = lt2 & ~lt1 & live, x3 = lt3 & ~lt2 & live;
-
-    // (4) thinning for k_r < k_max: keep iff U < T_r, U read most significant bit first
-    if (e.thin) {
-      const uint32_t alw1 = (e.thin_always & 1u) ? ~0u : 0u;
-      const uint32_t alw2 = (e.thin_always & 2u) ? ~0u : 0u;
-      const uint32_t alw3 = (e.thin_always & 4u) ? ~0u : 0u;
-      uint32_t und = (x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3);
-      uint32_t rej = 0u;
-      const int q = e.thin_bits;
-      int i = 0;
-      auto thin_bit = [&](uint32_t word) {
-        const int pos = q - 1 - i;
-        const uint32_t b1 = 0u - (uint32_t)(((unsigned long long)e.thin_T[0] >> pos) & 1ull);
-        const uint32_t b2 = 0u - (uint32_t)(((unsigned long long)e.thin_T[1] >> pos) & 1ull);
-        const uint32_t b3 = 0u - (uint32_t)(((unsigned long long)e.thin_T[2] >> pos) & 1ull);
-        const uint32_t tb = (x1 & b1) | (x2 & b2) | (x3 & b3);
-        const uint32_t lower = und & ~word & tb;   // U < T decided
-        const uint32_t higher = und & word & ~tb;  // U > T decided
-        rej |= higher;
-        und &= ~(lower | higher);
-        ++i;
-      };
-#pragma unroll
-      for (int k = K + 2; k < 4 * NC0; ++k)
-        if (i < q) thin_bit(w[k]);
-      for (uint32_t c = NC0; und != 0u && i < q; ++c) {
-        const uint4 r = philox4x32_10(stream_counter(sgroup, step, 0u, 0u, c), key);
-        if (i < q) thin_bit(r.x);
-        if (i < q) thin_bit(r.y);
-        if (i < q) thin_bit(r.z);
-        if (i < q) thin_bit(r.w);
-      }
-      rej |= und;  // U == T: not below
-      x1 &= ~rej;
-      x2 &= ~rej;
-      x3 &= ~rej;
-    }
-
-    // (5) updates from the counts before the reaction (App. B)
-    const uint32_t x12 = x1 | x2;
-    {
-      uint32_t T[WR1];
-#pragma unroll
-      for (int i = 0; i < WR1; ++i)
-        T[i] = (x1 & bs::plane<true>(P, i)) | (x2 & ~bs::plane<false>(Lm, i)) | (x3 & R1[i]);
-      bs::add_signed(S1, T, x2);  // -L = ~L + 1
-    }
-    {
-      uint32_t U3[WU3];  // -U - 3 = ~U - 2
-#pragma unroll
-      for (int i = 0; i < WU3; ++i) U3[i] = ~bs::plane<true>(U, i);
-      bs::add_select3<-2, -2, -2>(U3, 0xFFFFFFFFu, 0u, 0u);
-      uint32_t T[WU3 + 1];
-#pragma unroll
-      for (int i = 0; i < WU3 + 1; ++i)
-        T[i] = (x12 & bs::plane<true>(U, i)) | (x3 & (i == 0 ? 0u : U3[i - 1]));
-      bs::add_signed(S2, T, 0u);
-    }
-    {
-      uint32_t Q[WP];  // A - D - 1 = U + L
-      uint32_t c = 0u;
-#pragma unroll
-      for (int i = 0; i < WP; ++i) {
-        const uint32_t a = U[i], b = bs::plane<false>(Lm, i);
-        Q[i] = bs::xor3(a, b, c);
-        c = bs::maj(a, b, c);
-      }
-      uint32_t T[WR3];
-#pragma unroll
-      for (int i = 0; i < WR3; ++i)
-        T[i] = (x1 & bs::plane<true>(P, i)) | (x2 & bs::plane<true>(Q, i)) | (x3 & R3[i]);
-      bs::add_signed(S3, T, 0u);
-    }
-    bs::add_select3<1, 0, -1>(Lm, x1, x2, x3);
-    bs::add_select3<-2, -1, 3>(P, x1, x2, x3);
-    bs::add_select3<-2, -2, 4>(U, x1, x2, x3);
-    bs::add_select3<3, 1, -4>(R1, x1, x2, x3);
-    bs::add_select3<3, 3, -6>(R3, x1, x2, x3);
-    const uint32_t fired = x12 | x3;
-    reactions += (unsigned)__popc(fired);
-    lane_steps += (unsigned)__popc(live);
-    ++step;
-
-    // (6) absorption
-    const uint32_t now_live = live_lanes() & live;
-    uint32_t newly = live & ~now_live;
-    if (newly) {
-      const double tn = group_time();
-      while (newly) {
-        const int l = __ffs(newly) - 1;
-        newly &= newly - 1;
-        p.t_abs[row0 + l] = tn;
-      }
-      live = now_live;
-      if (!live) {
-        done = true;
-        for (; snap < n_snap; ++snap) capture(snap);
-      }
-    }
   }
 
-  // ---- outputs of the group
+  // (2) the clock: the candidate time of this step's event
+  double m_new = s.m, t_new = s.t;
+  long long E_new = s.E;
+  float tf_new = s.t_f, cf_new = s.c_f;
+  bool crossed;
+  if (precision == kP64) {
+    const unsigned long long x = ((unsigned long long)w[K + 1] << 21) | (w[K] >> 11);
+    const double u = (double)(x + 1ull) * 0x1p-53;
+    const double mm = s.m * u;
+    const int hi = __double2hiint(mm), lo = __double2loint(mm);
+    E_new = s.E + (long long)(((hi >> 20) & 0x7FF) - 1023);
+    m_new = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, lo);
+    crossed = E_new < s.cur.E || (E_new == s.cur.E && m_new < s.cur.m);
+  } else if (precision == kP64LogSum) {
+    const unsigned long long x = ((unsigned long long)w[K + 1] << 21) | (w[K] >> 11);
+    const double u = (double)(x + 1ull) * 0x1p-53;
+    t_new = s.t + (-log(u) / e.lambda);
+    crossed = t_new > s.cur.t;
+  } else {
+    const float u = (float)((w[K + 1] >> 8) + 1u) * 0x1p-24f;
+    const float tau = -logf(u) * e.inv_lambda_f;
+    if (precision == kP32Kahan) {
+      const float y = tau - s.c_f;
+      const float sum = s.t_f + y;
+      cf_new = (sum - s.t_f) - y;
+      tf_new = sum;
+      crossed = sum > s.cur.t_f;
+    } else {
+      t_new = s.t + (double)tau;
+      crossed = t_new > s.cur.t;
+    }
+  }
+  while (crossed) {
+    if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
+      s.done = true;
+      return;
+    }
+    capture<K>(p, s, e, s.snap, s_hist);
+    ++s.snap;
+    s.cur = thr[s.snap];
+    if (precision == kP64) crossed = E_new < s.cur.E || (E_new == s.cur.E && m_new < s.cur.m);
+    else if (precision == kP32Kahan) crossed = tf_new > s.cur.t_f;
+    else crossed = t_new > s.cur.t;
+  }
+  s.m = m_new;
+  s.E = E_new;
+  s.t = t_new;
+  s.t_f = tf_new;
+  s.c_f = cf_new;
+
+  // (3) comparators and changer words
+  const uint32_t lt1 = bs::less_than(n, s.S1);
+  const uint32_t lt2 = bs::less_than(n, s.S2);
+  const uint32_t lt3 = bs::less_than(n, s.S3);
+  uint32_t x1 = lt1 & s.live, x2 = lt2 & ~lt1 & s.live, x3 = lt3 & ~lt2 & s.live;
+
+  // (4) thinning for k_r < k_max: keep iff U < T_r, U read most significant bit first
+  if (e.thin) {
+    const uint32_t alw1 = (e.thin_always & 1u) ? ~0u : 0u;
+    const uint32_t alw2 = (e.thin_always & 2u) ? ~0u : 0u;
+    const uint32_t alw3 = (e.thin_always & 4u) ? ~0u : 0u;
+    uint32_t und = (x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3);
+    uint32_t rej = 0u;
+    const int q = e.thin_bits;
+    int i = 0;
+    auto thin_bit = [&](uint32_t word) {
+      const int pos = q - 1 - i;
+      const uint32_t b1 = 0u - (uint32_t)(((unsigned long long)e.thin_T[0] >> pos) & 1ull);
+      const uint32_t b2 = 0u - (uint32_t)(((unsigned long long)e.thin_T[1] >> pos) & 1ull);
+      const uint32_t b3 = 0u - (uint32_t)(((unsigned long long)e.thin_T[2] >> pos) & 1ull);
+      const uint32_t tb = (x1 & b1) | (x2 & b2) | (x3 & b3);
+      const uint32_t lower = und & ~word & tb;   // U < T decided
+      const uint32_t higher = und & word & ~tb;  // U > T decided
+      rej |= higher;
+      und &= ~(lower | higher);
+      ++i;
+    };
+#pragma unroll
+    for (int k = K + 2; k < 4 * NC0; ++k)
+      if (i < q) thin_bit(w[k]);
+    for (uint32_t c = NC0; und != 0u && i < q; ++c) {
+      const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, c), key);
+      if (i < q) thin_bit(r.x);
+      if (i < q) thin_bit(r.y);
+      if (i < q) thin_bit(r.z);
+      if (i < q) thin_bit(r.w);
+    }
+    rej |= und;  // U == T: not below
+    x1 &= ~rej;
+    x2 &= ~rej;
+    x3 &= ~rej;
+  }
+
+  // (5) updates from the counts before the reaction (App. B)
+  const uint32_t x12 = x1 | x2;
+  {
+    uint32_t T[WR1];
+#pragma unroll
+    for (int i = 0; i < WR1; ++i)
+      T[i] = (x1 & bs::plane<true>(s.P, i)) | (x2 & ~bs::plane<false>(s.L, i)) | (x3 & s.R1[i]);
+    bs::add_signed(s.S1, T, x2);  // -L = ~L + 1
+  }
+  {
+    uint32_t U3[WU3];  // -U - 3 = ~U - 2
+#pragma unroll
+    for (int i = 0; i < WU3; ++i) U3[i] = ~bs::plane<true>(s.U, i);
+    bs::add_select3<-2, -2, -2>(U3, 0xFFFFFFFFu, 0u, 0u);
+    uint32_t T[WU3 + 1];
+#pragma unroll
+    for (int i = 0; i < WU3 + 1; ++i)
+      T[i] = (x12 & bs::plane<true>(s.U, i)) | (x3 & (i == 0 ? 0u : U3[i - 1]));
+    bs::add_signed(s.S2, T, 0u);
+  }
+  {
+    uint32_t Q[WP];  // A - D - 1 = U + L
+    uint32_t c = 0u;
+#pragma unroll
+    for (int i = 0; i < WP; ++i) {
+      const uint32_t a = s.U[i], b = bs::plane<false>(s.L, i);
+      Q[i] = bs::xor3(a, b, c);
+      c = bs::maj(a, b, c);
+    }
+    uint32_t T[WR3];
+#pragma unroll
+    for (int i = 0; i < WR3; ++i)
+      T[i] = (x1 & bs::plane<true>(s.P, i)) | (x2 & bs::plane<true>(Q, i)) | (x3 & s.R3[i]);
+    bs::add_signed(s.S3, T, 0u);
+  }
+  bs::add_select3<1, 0, -1>(s.L, x1, x2, x3);
+  bs::add_select3<-2, -1, 3>(s.P, x1, x2, x3);
+  bs::add_select3<-2, -2, 4>(s.U, x1, x2, x3);
+  bs::add_select3<3, 1, -4>(s.R1, x1, x2, x3);
+  bs::add_select3<3, 3, -6>(s.R3, x1, x2, x3);
+  s.reactions += (unsigned)__popc(x12 | x3);
+  s.lane_steps += (unsigned)__popc(s.live);
+  ++s.step;
+
+  // (6) absorption
+  const uint32_t now_live = live_lanes(s, e) & s.live;
+  uint32_t newly = s.live & ~now_live;
+  if (newly) {
+    const double tn = group_time(s, e, precision);
+    while (newly) {
+      const int l = __ffs(newly) - 1;
+      newly &= newly - 1;
+      p.t_abs[s.row0 + l] = tn;
+    }
+    s.live = now_live;
+    if (!s.live) {
+      s.done = true;
+      for (; s.snap < p.n_snap; ++s.snap) capture<K>(p, s, e, s.snap, s_hist);
+    }
+  }
+}
+
+// Outputs of a finished group: final counts, outcomes, per-ensemble tallies, counters.
+template <int K>
+__device__ __forceinline__ void group_finish(const FrankLaunch& p, const GroupState<K>& s, const Ensemble& e,
+                                          FrankCounters& cnt) {
+  using Sh = FrankShape<K>;
   unsigned long long outc[4] = {0, 0, 0, 0};
-  for (int l = 0; l < nvalid; ++l) {
+  for (int l = 0; l < s.nvalid; ++l) {
     int cl, cd, ca;
-    lane_counts<B, WP>(Lm, U, n_tot, l, cl, cd, ca);
-    int* o = p.final_counts + (row0 + l) * p.n_species;
+    lane_counts<Sh::B, Sh::WP>(s.L, s.U, e.n_tot, l, cl, cd, ca);
+    int* o = p.final_counts + (s.row0 + l) * p.n_species;
     o[p.perm[0]] = cl;
     o[p.perm[1]] = cd;
     o[p.perm[2]] = ca;
     signed char oc = -1;
-    if (!((live >> l) & 1u)) {
+    if (!((s.live >> l) & 1u)) {
       const int nz = (cl != 0) + (cd != 0) + (ca != 0);
       oc = nz == 1 ? (signed char)(cl ? p.perm[0] : (cd ? p.perm[1] : p.perm[2])) : (signed char)-2;
       outc[nz == 1 ? (int)oc : 3] += 1;  // [3] also counts absorbed-with-several
     } else {
-      p.t_abs[row0 + l] = __longlong_as_double(0x7FF0000000000000ll);
+      p.t_abs[s.row0 + l] = __longlong_as_double(0x7FF0000000000000ll);
       outc[3] += 1;
     }
-    p.outcome[row0 + l] = oc;
+    p.outcome[s.row0 + l] = oc;
   }
   if (p.ens_absorbed) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (outc[k]) atomicAdd(&p.ens_absorbed[(long long)ens_index * 4 + k], outc[k]);
+      if (outc[k]) atomicAdd(&p.ens_absorbed[(long long)s.ens * 4 + k], outc[k]);
   }
-  cnt.group_steps += step;
-  cnt.lane_steps += lane_steps;
-  cnt.reactions += reactions;
-  cnt.null_steps += lane_steps - reactions;
-  cnt.redraws += redraws;
-  cnt.absorbed += (unsigned long long)__popc(valid & ~live);
+  cnt.group_steps += s.step;
+  cnt.lane_steps += s.lane_steps;
+  cnt.reactions += s.reactions;
+  cnt.null_steps += s.lane_steps - s.reactions;
+  cnt.redraws += s.redraws;
+  cnt.absorbed += (unsigned long long)__popc(s.valid & ~s.live);
   cnt.groups += 1;
 }
 
-// The persistent kernel: every thread takes work items (groups) from a queue
-// until none is left; single-ensemble launches read the ensemble from the
-// kernel parameters (warp-uniform), batches from a table.
+// The persistent kernel.  Every thread owns one group at a time and takes the next
+// work item from a queue when its group finishes.  The loop is warp-synchronous: all
+// 32 threads stay in it until the whole warp has run out of work, and the warp
+// reconverges after every group step, so the rare divergent paths (redraws,
+// snapshots, absorptions, a new group) cost one pass each instead of leaving the warp
+// split for the rest of the run.  Single-ensemble launches read the ensemble from the
+// kernel parameters (warp-uniform); batches from a table.
 template <int K, bool BATCH>
 __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ FrankLaunch p) {
-  extern __shared__ unsigned int s_hist[];
+  extern __shared__ unsigned int s_hist_mem[];
   const bool smem_hist = !BATCH && p.n_snap > 0;
+  unsigned int* s_hist = smem_hist ? s_hist_mem : nullptr;
   if (smem_hist) {
-    for (int i = threadIdx.x; i < p.n_snap * kHistBins; i += blockDim.x) s_hist[i] = 0u;
+    for (int i = threadIdx.x; i < p.n_snap * kHistBins; i += blockDim.x) s_hist_mem[i] = 0u;
     __syncthreads();
   }
   FrankCounters cnt = {0, 0, 0, 0, 0, 0, 0};
   unsigned int errors = 0u;
+  GroupState<K> s;
+  s.done = true;
+  bool active = false, exhausted = false;
+  const Threshold* thr = p.thr;
   for (;;) {
-    const long long item = (long long)atomicAdd(p.queue, 1ull) + p.item_begin;
-    if (item >= p.item_end) break;
-    if (!BATCH) {
-      run_group<K>(p, p.ens, p.thr, item, 0, smem_hist ? s_hist : nullptr, cnt, errors);
-    } else {
-      const int ei = p.item_ens[item];
-      const Ensemble e = p.ens_table[ei];
-      run_group<K>(p, e, p.thr + (long long)ei * (p.n_snap + 1), p.item_group[item], ei, nullptr, cnt,
-                   errors);
+    if (!active && !exhausted) {
+      const long long item = (long long)atomicAdd(p.queue, 1ull) + p.item_begin;
+      if (item >= p.item_end) {
+        exhausted = true;
+      } else if (!BATCH) {
+        group_init<K>(p, s, p.ens, thr, item, 0, s_hist);
+        active = true;
+      } else {
+        const int ei = p.item_ens[item];
+        thr = p.thr + (long long)ei * (p.n_snap + 1);
+        group_init<K>(p, s, p.ens_table[ei], thr, p.item_group[item], ei, nullptr);
+        active = true;
+      }
     }
+    if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
+    if (active) {
+      const Ensemble& e = BATCH ? p.ens_table[s.ens] : p.ens;
+      if (!s.done) group_step<K>(p, s, e, thr, s_hist, errors);
+      if (s.done) {
+        group_finish<K>(p, s, e, cnt);
+        active = false;
+      }
+    }
+    __syncwarp();
   }
   // flush: warp sums, one atomic per warp per counter
   unsigned long long v[7] = {cnt.group_steps, cnt.lane_steps, cnt.reactions, cnt.null_steps,
@@ -529,12 +571,12 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&p.counters[ctr_index[k]], x);
   }
-  unsigned int err = __reduce_or_sync(0xFFFFFFFFu, errors);
+  const unsigned int err = __reduce_or_sync(0xFFFFFFFFu, errors);
   if ((threadIdx.x & 31) == 0 && err) atomicOr(p.status, err);
   if (smem_hist) {
     __syncthreads();
     for (int i = threadIdx.x; i < p.n_snap * kHistBins; i += blockDim.x)
-      if (s_hist[i]) atomicAdd(&p.hist[i], (unsigned long long)s_hist[i]);
+      if (s_hist_mem[i]) atomicAdd(&p.hist[i], (unsigned long long)s_hist_mem[i]);
   }
 }
 

@@ -32,6 +32,9 @@ __device__ __forceinline__ uint4 run_counter(long long run, unsigned long long s
 
 }  // namespace
 
+// One run per thread at a time; the loop is warp-synchronous (every thread stays in it
+// until the warp runs out of runs, and the warp reconverges after each step), so runs
+// of different lengths and the rare branches do not leave the warp split.
 __global__ void __launch_bounds__(256) thread_per_run_kernel(const __grid_constant__ ThreadLaunch p) {
   extern __shared__ unsigned int s_hist[];
   const int n_snap = p.n_snap;
@@ -42,159 +45,175 @@ __global__ void __launch_bounds__(256) thread_per_run_kernel(const __grid_consta
   const PhiloxKey key{(uint32_t)e.seed, (uint32_t)(e.seed >> 32)};
   const double k1 = p.rates[0], k2 = p.rates[1], k3 = p.rates[2];
   const double kunit = k1;  // the common rate when unit_rates
-  unsigned long long c_steps = 0, c_react = 0, c_abs = 0;
+  unsigned long long c_steps = 0, c_abs = 0;
   unsigned int errors = 0u;
   unsigned long long outc[4] = {0, 0, 0, 0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
 
-  for (long long run = (long long)blockIdx.x * blockDim.x + threadIdx.x; run < e.n_runs;
-       run += (long long)gridDim.x * blockDim.x) {
-    const long long row = e.run_offset + run;
-    const long long grun = e.group_base * 32 + run;  // run index inside the ensemble
-    int l, d, a;
-    if (p.init_counts) {
-      l = p.init_counts[row * 3 + 0];
-      d = p.init_counts[row * 3 + 1];
-      a = p.init_counts[row * 3 + 2];
-    } else {
-      l = e.init[0];
-      d = e.init[1];
-      a = e.init[2];
+  long long run = (long long)blockIdx.x * blockDim.x + threadIdx.x - stride;
+  long long row = 0, grun = 0;
+  int l = 0, d = 0, a = 0, snap = 0;
+  long long h1 = 0, h2 = 0, h3 = 0;
+  double t = 0.0, t_abs = 0.0;
+  float t_f = 0.0f, c_f = 0.0f;
+  unsigned long long step = 0;
+  bool active = false, exhausted = false, done = false, absorbed = false;
+
+  auto real_total = [&]() {
+    return ((e.active & 1u) ? h1 : 0) + ((e.active & 2u) ? h2 : 0) + ((e.active & 4u) ? h3 : 0);
+  };
+  auto capture = [&](int s) {
+    atomicAdd(&s_hist[s * kHistBins + tpr_ee_bin(l, d)], 1u);
+    if (p.snap_counts) {
+      int* o = p.snap_counts + ((long long)s * p.n_runs_total + row) * p.n_species;
+      o[p.perm[0]] = l;
+      o[p.perm[1]] = d;
+      o[p.perm[2]] = a;
     }
-    double t = 0.0;
-    float t_f = 0.0f, c_f = 0.0f;
-    int snap = 0;
-    double t_abs = __longlong_as_double(0x7FF0000000000000ll);
-    bool absorbed = false;
-    unsigned long long step = 0;
+  };
 
-    auto real_total = [&](long long h1, long long h2, long long h3) {
-      return ((e.active & 1u) ? h1 : 0) + ((e.active & 2u) ? h2 : 0) + ((e.active & 4u) ? h3 : 0);
-    };
-    auto capture = [&](int s) {
-      atomicAdd(&s_hist[s * kHistBins + tpr_ee_bin(l, d)], 1u);
-      if (p.snap_counts) {
-        int* o = p.snap_counts + ((long long)s * p.n_runs_total + row) * p.n_species;
-        o[p.perm[0]] = l;
-        o[p.perm[1]] = d;
-        o[p.perm[2]] = a;
+  for (;;) {
+    if (!active && !exhausted) {
+      run += stride;
+      if (run >= e.n_runs) {
+        exhausted = true;
+      } else {
+        row = e.run_offset + run;
+        grun = e.group_base * 32 + run;  // run index inside the ensemble
+        if (p.init_counts) {
+          l = p.init_counts[row * 3 + 0];
+          d = p.init_counts[row * 3 + 1];
+          a = p.init_counts[row * 3 + 2];
+        } else {
+          l = e.init[0];
+          d = e.init[1];
+          a = e.init[2];
+        }
+        t = 0.0;
+        t_f = c_f = 0.0f;
+        snap = 0;
+        step = 0;
+        t_abs = __longlong_as_double(0x7FF0000000000000ll);
+        h1 = (long long)a * l;
+        h2 = (long long)a * d;
+        h3 = (long long)l * d;
+        absorbed = real_total() == 0;
+        if (absorbed) t_abs = 0.0;
+        done = absorbed;
+        active = true;
       }
-    };
-
-    long long h1 = (long long)a * l, h2 = (long long)a * d, h3 = (long long)l * d;
-    if (real_total(h1, h2, h3) == 0) {
-      absorbed = true;
-      t_abs = 0.0;
     }
-    while (!absorbed) {
+    if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
+    if (active && !done) {
       if (p.step_budget > 0 && (long long)step >= p.step_budget) {
         errors |= kErrTimeout;
-        break;
-      }
-      const uint4 w = philox4x32_10(run_counter(grun, step, 0u), key);
-      int r;
-      double a0;
-      if (p.unit_rates) {
-        // exact uniform integer in [0, H) (Lemire's method with rejection)
-        const unsigned long long H = (unsigned long long)(h1 + h2 + h3);
-        unsigned long long m = (unsigned long long)w.x * H;
-        if ((uint32_t)m < (uint32_t)H) {
-          const uint32_t thresh = (uint32_t)(0u - (uint32_t)H) % (uint32_t)H;
-          uint32_t attempt = 0u, spare = w.y;
-          while ((uint32_t)m < thresh) {
-            if (attempt >= 64u) {
-              errors |= kErrRedraw;
-              break;
+        done = true;
+      } else {
+        const uint4 w = philox4x32_10(run_counter(grun, step, 0u), key);
+        int r;
+        double a0;
+        if (p.unit_rates) {
+          // exact uniform integer in [0, H) (Lemire's method with rejection)
+          const unsigned long long H = (unsigned long long)(h1 + h2 + h3);
+          unsigned long long m = (unsigned long long)w.x * H;
+          if ((uint32_t)m < (uint32_t)H) {
+            const uint32_t thresh = (uint32_t)(0u - (uint32_t)H) % (uint32_t)H;
+            uint32_t attempt = 0u;
+            while ((uint32_t)m < thresh && attempt < 64u) {
+              const uint32_t fresh = attempt == 0u ? w.y : philox4x32_10(run_counter(grun, step, attempt), key).x;
+              ++attempt;
+              m = (unsigned long long)fresh * H;
             }
-            uint32_t fresh;
-            if (attempt == 0u) {
-              fresh = spare;
-            } else {
-              fresh = philox4x32_10(run_counter(grun, step, attempt), key).x;
-            }
-            ++attempt;
-            m = (unsigned long long)fresh * H;
+            if ((uint32_t)m < thresh) errors |= kErrRedraw;
+          }
+          const long long n = (long long)(m >> 32);
+          r = n < h1 ? 0 : (n < h1 + h2 ? 1 : 2);
+          a0 = kunit * (double)H;
+        } else {
+          const double a1 = k1 * (double)h1, a2 = k2 * (double)h2, a3 = k3 * (double)h3;
+          a0 = a1 + a2 + a3;
+          const unsigned long long x = ((unsigned long long)w.y << 21) | (w.x >> 11);
+          const double v = (double)x * 0x1p-53 * a0;
+          r = v < a1 ? 0 : (v < a1 + a2 ? 1 : 2);
+          if (r == 2 && a3 == 0.0) r = a2 > 0.0 ? 1 : 0;  // rounding at the top edge
+        }
+        // clock
+        double t_new = t;
+        float tf_new = t_f, cf_new = c_f;
+        if (p.precision == kP64 || p.precision == kP64LogSum) {
+          const unsigned long long x = ((unsigned long long)w.w << 21) | (w.z >> 11);
+          const double u = (double)(x + 1ull) * 0x1p-53;
+          t_new = t + (-log(u) / a0);
+        } else {
+          const float u = (float)((w.w >> 8) + 1u) * 0x1p-24f;
+          const float tau = -logf(u) / (float)a0;
+          if (p.precision == kP32Kahan) {
+            const float y = tau - c_f;
+            const float s = t_f + y;
+            cf_new = (s - t_f) - y;
+            tf_new = s;
+            t_new = (double)s;
+          } else {
+            t_new = t + (double)tau;
           }
         }
-        const long long n = (long long)(m >> 32);
-        r = n < h1 ? 0 : (n < h1 + h2 ? 1 : 2);
-        a0 = kunit * (double)H;
-      } else {
-        const double a1 = k1 * (double)h1, a2 = k2 * (double)h2, a3 = k3 * (double)h3;
-        a0 = a1 + a2 + a3;
-        const unsigned long long x = ((unsigned long long)w.y << 21) | (w.x >> 11);
-        const double v = (double)x * 0x1p-53 * a0;
-        r = v < a1 ? 0 : (v < a1 + a2 ? 1 : 2);
-        if (r == 2 && a3 == 0.0) r = a2 > 0.0 ? 1 : 0;  // rounding at the top edge
-      }
-      // clock
-      double t_new = t;
-      float tf_new = t_f, cf_new = c_f;
-      if (p.precision == kP64 || p.precision == kP64LogSum) {
-        const unsigned long long x = ((unsigned long long)w.w << 21) | (w.z >> 11);
-        const double u = (double)(x + 1ull) * 0x1p-53;
-        t_new = t + (-log(u) / a0);
-      } else {
-        const float u = (float)((w.w >> 8) + 1u) * 0x1p-24f;
-        const float tau = -logf(u) / (float)a0;
-        if (p.precision == kP32Kahan) {
-          const float y = tau - c_f;
-          const float s = t_f + y;
-          cf_new = (s - t_f) - y;
-          tf_new = s;
-          t_new = (double)s;
+        while (snap < n_snap && (p.precision == kP32Kahan ? tf_new > p.thr[snap].t_f : t_new > p.thr[snap].t)) {
+          capture(snap);
+          ++snap;
+        }
+        if (p.precision == kP32Kahan ? tf_new > p.thr[n_snap].t_f : t_new > p.thr[n_snap].t) {
+          done = true;
         } else {
-          t_new = t + (double)tau;
+          t = t_new;
+          t_f = tf_new;
+          c_f = cf_new;
+          // the reaction (Eq. eq_nu)
+          if (r == 0) {
+            ++l;
+            --a;
+          } else if (r == 1) {
+            ++d;
+            --a;
+          } else {
+            --l;
+            --d;
+            a += 2;
+          }
+          ++step;
+          h1 = (long long)a * l;
+          h2 = (long long)a * d;
+          h3 = (long long)l * d;
+          if (real_total() == 0) {
+            absorbed = true;
+            done = true;
+            t_abs = p.precision == kP32Kahan ? (double)t_f : t;
+          }
         }
       }
-      while (snap < n_snap && (p.precision == kP32Kahan ? tf_new > p.thr[snap].t_f : t_new > p.thr[snap].t)) {
-        capture(snap);
-        ++snap;
-      }
-      if (p.precision == kP32Kahan ? tf_new > p.thr[n_snap].t_f : t_new > p.thr[n_snap].t) break;
-      t = t_new;
-      t_f = tf_new;
-      c_f = cf_new;
-      // the reaction (Eq. eq_nu)
-      if (r == 0) {
-        ++l;
-        --a;
-      } else if (r == 1) {
-        ++d;
-        --a;
-      } else {
-        --l;
-        --d;
-        a += 2;
-      }
-      ++step;
-      h1 = (long long)a * l;
-      h2 = (long long)a * d;
-      h3 = (long long)l * d;
-      if (real_total(h1, h2, h3) == 0) {
-        absorbed = true;
-        t_abs = p.precision == kP32Kahan ? (double)t_f : t;
-      }
     }
-    if (absorbed)
-      for (; snap < n_snap; ++snap) capture(snap);
-    int* o = p.final_counts + row * p.n_species;
-    o[p.perm[0]] = l;
-    o[p.perm[1]] = d;
-    o[p.perm[2]] = a;
-    p.t_abs[row] = t_abs;
-    signed char oc = -1;
-    if (absorbed) {
-      const int nz = (l != 0) + (d != 0) + (a != 0);
-      oc = nz == 1 ? (signed char)(l ? p.perm[0] : (d ? p.perm[1] : p.perm[2])) : (signed char)-2;
-      ++c_abs;
+    if (active && done) {
+      if (absorbed)
+        for (; snap < n_snap; ++snap) capture(snap);
+      int* o = p.final_counts + row * p.n_species;
+      o[p.perm[0]] = l;
+      o[p.perm[1]] = d;
+      o[p.perm[2]] = a;
+      p.t_abs[row] = t_abs;
+      signed char oc = -1;
+      if (absorbed) {
+        const int nz = (l != 0) + (d != 0) + (a != 0);
+        oc = nz == 1 ? (signed char)(l ? p.perm[0] : (d ? p.perm[1] : p.perm[2])) : (signed char)-2;
+        ++c_abs;
+      }
+      p.outcome[row] = oc;
+      outc[oc >= 0 ? oc : 3] += 1;
+      c_steps += step;
+      active = false;
     }
-    p.outcome[row] = oc;
-    outc[oc >= 0 ? oc : 3] += 1;
-    c_steps += step;
-    c_react += step;
+    __syncwarp();
   }
 
-  unsigned long long v[5] = {c_steps, c_steps, c_react, c_abs, 0};
+  unsigned long long v[4] = {c_steps, c_steps, c_steps, c_abs};
   const int idx[4] = {kLaneSteps, kGroupSteps, kReactions, kAbsorbed};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
