@@ -26,11 +26,11 @@ FrankLauncher frank_launcher(int K) {
   }
 }
 
-int frank_max_active_blocks(int K, int batch, int block, int smem, int* blocks) {
+int frank_max_active_blocks(int K, int variant, int block, int smem, int* blocks) {
   switch (K) {
 #define BITSSA_CASE(k) \
   case k:              \
-    return frank_occupancy_k##k(batch, block, smem, blocks);
+    return frank_occupancy_k##k(variant, block, smem, blocks);
     BITSSA_FOR_EACH_K(BITSSA_CASE)
 #undef BITSSA_CASE
     default:
@@ -38,11 +38,11 @@ int frank_max_active_blocks(int K, int batch, int block, int smem, int* blocks) 
   }
 }
 
-int frank_registers(int K, int batch) {
+int frank_registers(int K, int variant) {
   switch (K) {
 #define BITSSA_CASE(k) \
   case k:              \
-    return frank_regs_k##k(batch);
+    return frank_regs_k##k(variant);
     BITSSA_FOR_EACH_K(BITSSA_CASE)
 #undef BITSSA_CASE
     default:

@@ -14,26 +14,44 @@
 
 namespace bitssa {
 
+// variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64)
 int BITSSA_CAT(frank_launch_k, BITSSA_K)(const FrankLaunch& p, int grid, int block, int smem,
                                           void* stream) {
-  if (p.ens_table) frank_kernel<BITSSA_K, true><<<grid, block, smem, (cudaStream_t)stream>>>(p);
-  else frank_kernel<BITSSA_K, false><<<grid, block, smem, (cudaStream_t)stream>>>(p);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const bool prod = p.precision == kP64;
+  if (p.ens_table) {
+    if (prod) frank_kernel<BITSSA_K, true, true><<<grid, block, smem, st>>>(p);
+    else frank_kernel<BITSSA_K, true, false><<<grid, block, smem, st>>>(p);
+  } else {
+    if (prod) frank_kernel<BITSSA_K, false, true><<<grid, block, smem, st>>>(p);
+    else frank_kernel<BITSSA_K, false, false><<<grid, block, smem, st>>>(p);
+  }
   return (int)cudaGetLastError();
 }
 
-int BITSSA_CAT(frank_occupancy_k, BITSSA_K)(int batch, int block, int smem, int* blocks) {
-  if (batch)
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, frank_kernel<BITSSA_K, true>,
-                                                              block, (size_t)smem);
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, frank_kernel<BITSSA_K, false>,
-                                                            block, (size_t)smem);
+namespace {
+template <typename F>
+int with_kernel(int variant, F f) {
+  switch (variant & 3) {
+    case 0: return f(frank_kernel<BITSSA_K, false, false>);
+    case 1: return f(frank_kernel<BITSSA_K, true, false>);
+    case 2: return f(frank_kernel<BITSSA_K, false, true>);
+    default: return f(frank_kernel<BITSSA_K, true, true>);
+  }
+}
+}  // namespace
+
+int BITSSA_CAT(frank_occupancy_k, BITSSA_K)(int variant, int block, int smem, int* blocks) {
+  return with_kernel(variant, [&](auto kern) {
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, block, (size_t)smem);
+  });
 }
 
-int BITSSA_CAT(frank_regs_k, BITSSA_K)(int batch) {
-  cudaFuncAttributes a;
-  const cudaError_t err = batch ? cudaFuncGetAttributes(&a, frank_kernel<BITSSA_K, true>)
-                                : cudaFuncGetAttributes(&a, frank_kernel<BITSSA_K, false>);
-  return err == cudaSuccess ? a.numRegs : -1;
+int BITSSA_CAT(frank_regs_k, BITSSA_K)(int variant) {
+  return with_kernel(variant, [&](auto kern) {
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, kern) == cudaSuccess ? a.numRegs : -1;
+  });
 }
 
 }  // namespace bitssa

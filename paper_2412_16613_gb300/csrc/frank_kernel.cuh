@@ -74,10 +74,6 @@ struct FrankShape {
 
 constexpr double kLn2 = 0x1.62e42fefa39efp-1;  // ln 2 rounded to double
 
-// Per-thread counters, flushed once per kernel.
-struct FrankCounters {
-  unsigned long long group_steps, lane_steps, reactions, null_steps, redraws, absorbed, groups;
-};
 
 // Reads the (L, D, A) of one lane from the L and U planes: X = L + D = (N - 1 - U) / 2.
 template <int B, int WP>
@@ -96,32 +92,119 @@ __device__ __forceinline__ int ee_bin(int l, int d) {
   return b > 63 ? 63 : b;
 }
 
+// ---------------------------------------------------------------------------
+// The group clock.  PROD (SSA_P64): exp(-Lambda t) = m 2^E is kept as an fp64
+// mantissa m in [1, 2) and an integer exponent E; each step multiplies in the
+// step's uniform u (one fp64 multiply, the exponent renormalised with integer
+// ops), so t = -(ln m + E ln 2) / Lambda needs a logarithm only when a time is
+// written out.  Otherwise: the fp64 sum of -log(u) / Lambda (SSA_P64_LOGSUM), or
+// fp32 -logf(u) / Lambda summed with Kahan compensation (SSA_P32_KAHAN) or into
+// an fp64 accumulator (SSA_P32_D64ACC).
+// ---------------------------------------------------------------------------
+template <bool PROD>
+struct Clock;
+
+template <>
+struct Clock<true> {
+  double m;
+  long long E;
+  double th_m;  // the next time point to cross, in the same form
+  long long th_E;
+  __device__ __forceinline__ void reset() {
+    m = 1.0;
+    E = 0;
+  }
+  __device__ __forceinline__ void aim(const Threshold& h) {
+    th_m = h.m;
+    th_E = h.E;
+  }
+  __device__ __forceinline__ double time(const Ensemble& e, int) const {
+    return -(log(m) + (double)E * kLn2) / e.lambda;
+  }
+};
+
+template <>
+struct Clock<false> {
+  double t;
+  float t_f, c_f;
+  double th_t;
+  float th_f;
+  __device__ __forceinline__ void reset() {
+    t = 0.0;
+    t_f = c_f = 0.0f;
+  }
+  __device__ __forceinline__ void aim(const Threshold& h) {
+    th_t = h.t;
+    th_f = h.t_f;
+  }
+  __device__ __forceinline__ double time(const Ensemble&, int precision) const {
+    return precision == kP32Kahan ? (double)t_f : t;
+  }
+};
+
+// Candidate clock after this step's event, from the step's waiting-time words w_K, w_{K+1}.
+__device__ __forceinline__ bool clock_advance(const Clock<true>& c, Clock<true>& nx, uint32_t wk, uint32_t wk1,
+                                              const Ensemble&, int) {
+  const unsigned long long x = ((unsigned long long)wk1 << 21) | (wk >> 11);
+  const double u = (double)(x + 1ull) * 0x1p-53;  // exact: (x + 1) 2^-53 in (0, 1]
+  const double mm = c.m * u;
+  const int hi = __double2hiint(mm), lo = __double2loint(mm);
+  nx = c;
+  nx.E = c.E + (long long)(((hi >> 20) & 0x7FF) - 1023);
+  nx.m = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, lo);
+  return nx.E < c.th_E || (nx.E == c.th_E && nx.m < c.th_m);
+}
+
+__device__ __forceinline__ bool clock_advance(const Clock<false>& c, Clock<false>& nx, uint32_t wk, uint32_t wk1,
+                                              const Ensemble& e, int precision) {
+  nx = c;
+  if (precision == kP64LogSum) {
+    const unsigned long long x = ((unsigned long long)wk1 << 21) | (wk >> 11);
+    const double u = (double)(x + 1ull) * 0x1p-53;
+    nx.t = c.t + (-log(u) / e.lambda);
+    return nx.t > c.th_t;
+  }
+  const float u = (float)((wk1 >> 8) + 1u) * 0x1p-24f;  // the top 24 of the 53 bits
+  const float tau = -logf(u) * e.inv_lambda_f;
+  if (precision == kP32Kahan) {
+    const float y = tau - c.c_f;
+    const float sum = c.t_f + y;
+    nx.c_f = (sum - c.t_f) - y;
+    nx.t_f = sum;
+    return sum > c.th_f;
+  }
+  nx.t = c.t + (double)tau;
+  return nx.t > c.th_t;
+}
+
+__device__ __forceinline__ bool clock_crosses(const Clock<true>& nx) {
+  return nx.E < nx.th_E || (nx.E == nx.th_E && nx.m < nx.th_m);
+}
+__device__ __forceinline__ bool clock_crosses(const Clock<false>& nx, int precision) {
+  return precision == kP32Kahan ? nx.t_f > nx.th_f : nx.t > nx.th_t;
+}
 
 // Everything one thread keeps about its group between steps (all in registers).
-template <int K>
+template <int K, bool PROD>
 struct GroupState {
   uint32_t S1[K], S2[K], S3[K];
   uint32_t L[FrankShape<K>::B], P[FrankShape<K>::WP], U[FrankShape<K>::WP];
   uint32_t R1[FrankShape<K>::WR1], R3[FrankShape<K>::WR3];
-  uint32_t live;       // lanes that can still react
-  uint32_t valid;      // lanes that hold a run (the last group may be partial)
-  uint32_t sgroup;     // stream group index
-  int nvalid;
-  int ens;             // ensemble index
-  int snap;            // next snapshot
-  long long row0;      // output row of lane 0
+  uint32_t live;     // lanes that can still react
+  uint32_t sgroup;   // stream group index
+  int nvalid;        // lanes holding a run (the last group may be partial)
+  int ens;           // ensemble index
+  int snap;          // next snapshot
+  long long row0;    // output row of lane 0
   unsigned long long step;
-  double m;            // product clock: exp(-Lambda t) = m 2^E
-  long long E;
-  double t;            // fp64 sum clocks
-  float t_f, c_f;      // Kahan clock and compensation
-  Threshold cur;       // next time point to cross (snapshot or t_end)
-  unsigned long long reactions, lane_steps, redraws;
+  Clock<PROD> clk;
+  unsigned long long reactions, lane_steps;
+  unsigned int redraws;
   bool done;
 };
 
-template <int K>
-__device__ __forceinline__ uint32_t live_lanes(const GroupState<K>& s, const Ensemble& e) {
+template <int K, bool PROD>
+__device__ __forceinline__ uint32_t live_lanes(const GroupState<K, PROD>& s, const Ensemble& e) {
   if (e.active == 7u) return bs::nonzero(s.S3);
   uint32_t m = 0u;
   if (e.active & 1u) m |= bs::nonzero(s.S1);
@@ -131,9 +214,9 @@ __device__ __forceinline__ uint32_t live_lanes(const GroupState<K>& s, const Ens
 }
 
 // The current state of every valid lane into snapshot `snap`: histogram and per-run counts.
-template <int K>
-__device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K>& s, const Ensemble& e, int snap,
-                                     unsigned int* s_hist) {
+template <int K, bool PROD>
+__device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K, PROD>& s, const Ensemble& e,
+                                        int snap, unsigned int* s_hist) {
   using Sh = FrankShape<K>;
   for (int l = 0; l < s.nvalid; ++l) {
     int cl, cd, ca;
@@ -149,17 +232,10 @@ __device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K
   }
 }
 
-template <int K>
-__device__ __forceinline__ double group_time(const GroupState<K>& s, const Ensemble& e, int precision) {
-  if (precision == kP64) return -(log(s.m) + (double)s.E * kLn2) / e.lambda;
-  if (precision == kP32Kahan) return (double)s.t_f;
-  return s.t;
-}
-
 // Set up group `group_local` of ensemble `e`: initial planes, cumulative propensities by
 // bit-sliced products, the linear forms, the runs that start absorbed.
-template <int K>
-__device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K>& s, const Ensemble& e,
+template <int K, bool PROD>
+__device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e,
                                            const Threshold* thr, long long group_local, int ens_index,
                                            unsigned int* s_hist) {
   using Sh = FrankShape<K>;
@@ -167,7 +243,7 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K>& 
   const long long run0 = group_local * 32;
   const long long left = e.n_runs - run0;
   s.nvalid = left >= 32 ? 32 : (int)left;
-  s.valid = s.nvalid >= 32 ? 0xFFFFFFFFu : ((1u << s.nvalid) - 1u);
+  const uint32_t valid = s.nvalid >= 32 ? 0xFFFFFFFFu : ((1u << s.nvalid) - 1u);
   s.sgroup = (uint32_t)(e.group_base + group_local);
   s.row0 = e.run_offset + run0;
   s.ens = ens_index;
@@ -191,12 +267,12 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K>& 
     bs::broadcast(Ap, e.init[2]);
 #pragma unroll
     for (int i = 0; i < B; ++i) {
-      Lp[i] &= s.valid;
-      Dp[i] &= s.valid;
-      Ap[i] = (Ap[i] & s.valid) | (((n_tot >> i) & 1) ? ~s.valid : 0u);
+      Lp[i] &= valid;
+      Dp[i] &= valid;
+      Ap[i] = (Ap[i] & valid) | (((n_tot >> i) & 1) ? ~valid : 0u);
     }
   }
-  // cumulative propensities (Eq. equation-as)
+  // cumulative propensities (Eq. equation-as) by bit-sliced products
   bs::multiply(s.S1, Ap, Lp);
   bs::multiply(s.S2, Ap, Dp);
   bs::multiply_add(s.S2, Ap, Lp);  // A D + A L
@@ -244,31 +320,28 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K>& 
   }
   bs::add_select3<-1, -1, -1>(s.R3, 0xFFFFFFFFu, 0u, 0u);
 
-  s.live = live_lanes(s, e) & s.valid;
-  uint32_t at0 = s.valid & ~s.live;  // runs that start absorbed are absorbed at t = 0
+  s.live = live_lanes(s, e) & valid;
+  uint32_t at0 = valid & ~s.live;  // runs that start absorbed are absorbed at t = 0
   while (at0) {
     const int l = __ffs(at0) - 1;
     at0 &= at0 - 1;
     p.t_abs[s.row0 + l] = 0.0;
   }
   s.step = 0;
-  s.m = 1.0;
-  s.E = 0;
-  s.t = 0.0;
-  s.t_f = 0.0f;
-  s.c_f = 0.0f;
+  s.clk.reset();
   s.snap = 0;
-  s.cur = thr[0];
-  s.reactions = s.lane_steps = s.redraws = 0;
+  s.clk.aim(thr[0]);
+  s.reactions = s.lane_steps = 0;
+  s.redraws = 0;
   s.done = s.live == 0u;
   if (s.done)
-    for (; s.snap < p.n_snap; ++s.snap) capture<K>(p, s, e, s.snap, s_hist);
+    for (; s.snap < p.n_snap; ++s.snap) capture<K, PROD>(p, s, e, s.snap, s_hist);
 }
 
 // One group step (see the file header).  Never leaves the caller's loop: a group that
 // stops sets s.done.
-template <int K>
-__device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K>& s, const Ensemble& e,
+template <int K, bool PROD>
+__device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e,
                                            const Threshold* thr, unsigned int* s_hist, unsigned int& errors) {
   using Sh = FrankShape<K>;
   constexpr int WP = Sh::WP, WU3 = Sh::WU3, WR1 = Sh::WR1, WR3 = Sh::WR3;
@@ -294,7 +367,12 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K>& 
   uint32_t n[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) n[i] = w[i];
+  // the rejection test and the three comparators are independent borrow chains: run them
+  // together, and redo the comparators only in the rare step where a lane redraws
   uint32_t need = ~bs::less_than_const(n, e.lambda_int) & s.live;
+  uint32_t lt1 = bs::less_than(n, s.S1);
+  uint32_t lt2 = bs::less_than(n, s.S2);
+  uint32_t lt3 = bs::less_than(n, s.S3);
   if (need) {
     for (uint32_t attempt = 1u; need; ++attempt) {
       if (attempt >= 64u) {
@@ -316,71 +394,38 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K>& 
       for (int i = 0; i < K; ++i) n[i] = (n[i] & ~need) | (wr[i] & need);
       need &= ~bs::less_than_const(n, e.lambda_int);
     }
+    lt1 = bs::less_than(n, s.S1);
+    lt2 = bs::less_than(n, s.S2);
+    lt3 = bs::less_than(n, s.S3);
   }
 
-  // (2) the clock: the candidate time of this step's event
-  double m_new = s.m, t_new = s.t;
-  long long E_new = s.E;
-  float tf_new = s.t_f, cf_new = s.c_f;
-  bool crossed;
-  if (precision == kP64) {
-    const unsigned long long x = ((unsigned long long)w[K + 1] << 21) | (w[K] >> 11);
-    const double u = (double)(x + 1ull) * 0x1p-53;
-    const double mm = s.m * u;
-    const int hi = __double2hiint(mm), lo = __double2loint(mm);
-    E_new = s.E + (long long)(((hi >> 20) & 0x7FF) - 1023);
-    m_new = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, lo);
-    crossed = E_new < s.cur.E || (E_new == s.cur.E && m_new < s.cur.m);
-  } else if (precision == kP64LogSum) {
-    const unsigned long long x = ((unsigned long long)w[K + 1] << 21) | (w[K] >> 11);
-    const double u = (double)(x + 1ull) * 0x1p-53;
-    t_new = s.t + (-log(u) / e.lambda);
-    crossed = t_new > s.cur.t;
-  } else {
-    const float u = (float)((w[K + 1] >> 8) + 1u) * 0x1p-24f;
-    const float tau = -logf(u) * e.inv_lambda_f;
-    if (precision == kP32Kahan) {
-      const float y = tau - s.c_f;
-      const float sum = s.t_f + y;
-      cf_new = (sum - s.t_f) - y;
-      tf_new = sum;
-      crossed = sum > s.cur.t_f;
-    } else {
-      t_new = s.t + (double)tau;
-      crossed = t_new > s.cur.t;
-    }
-  }
+  // (2) the clock: the candidate time of this step's event, snapshots, t_end
+  Clock<PROD> nx;
+  bool crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision);
   while (crossed) {
     if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
       s.done = true;
       return;
     }
-    capture<K>(p, s, e, s.snap, s_hist);
+    capture<K, PROD>(p, s, e, s.snap, s_hist);
     ++s.snap;
-    s.cur = thr[s.snap];
-    if (precision == kP64) crossed = E_new < s.cur.E || (E_new == s.cur.E && m_new < s.cur.m);
-    else if (precision == kP32Kahan) crossed = tf_new > s.cur.t_f;
-    else crossed = t_new > s.cur.t;
+    nx.aim(thr[s.snap]);
+    if constexpr (PROD) crossed = clock_crosses(nx);
+    else crossed = clock_crosses(nx, precision);
   }
-  s.m = m_new;
-  s.E = E_new;
-  s.t = t_new;
-  s.t_f = tf_new;
-  s.c_f = cf_new;
+  s.clk = nx;
 
-  // (3) comparators and changer words
-  const uint32_t lt1 = bs::less_than(n, s.S1);
-  const uint32_t lt2 = bs::less_than(n, s.S2);
-  const uint32_t lt3 = bs::less_than(n, s.S3);
-  uint32_t x1 = lt1 & s.live, x2 = lt2 & ~lt1 & s.live, x3 = lt3 & ~lt2 & s.live;
+  // (3) changer words: xi_r = [S_{r-1} <= n < S_r].  A lane that cannot react has S_r = 0
+  // for every reaction with k_r > 0, so only reactions that thinning rejects can be picked.
+  uint32_t x1 = lt1, x2 = lt2 & ~lt1, x3 = lt3 & ~lt2;
 
   // (4) thinning for k_r < k_max: keep iff U < T_r, U read most significant bit first
   if (e.thin) {
     const uint32_t alw1 = (e.thin_always & 1u) ? ~0u : 0u;
     const uint32_t alw2 = (e.thin_always & 2u) ? ~0u : 0u;
     const uint32_t alw3 = (e.thin_always & 4u) ? ~0u : 0u;
-    uint32_t und = (x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3);
-    uint32_t rej = 0u;
+    uint32_t und = ((x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3)) & s.live;
+    uint32_t rej = ((x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3)) & ~s.live;
     const int q = e.thin_bits;
     int i = 0;
     auto thin_bit = [&](uint32_t word) {
@@ -452,14 +497,14 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K>& 
   bs::add_select3<3, 1, -4>(s.R1, x1, x2, x3);
   bs::add_select3<3, 3, -6>(s.R3, x1, x2, x3);
   s.reactions += (unsigned)__popc(x12 | x3);
-  s.lane_steps += (unsigned)__popc(s.live);
   ++s.step;
 
   // (6) absorption
   const uint32_t now_live = live_lanes(s, e) & s.live;
   uint32_t newly = s.live & ~now_live;
   if (newly) {
-    const double tn = group_time(s, e, precision);
+    const double tn = s.clk.time(e, precision);
+    s.lane_steps += (unsigned long long)__popc(newly) * s.step;
     while (newly) {
       const int l = __ffs(newly) - 1;
       newly &= newly - 1;
@@ -468,15 +513,14 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K>& 
     s.live = now_live;
     if (!s.live) {
       s.done = true;
-      for (; s.snap < p.n_snap; ++s.snap) capture<K>(p, s, e, s.snap, s_hist);
+      for (; s.snap < p.n_snap; ++s.snap) capture<K, PROD>(p, s, e, s.snap, s_hist);
     }
   }
 }
 
 // Outputs of a finished group: final counts, outcomes, per-ensemble tallies, counters.
-template <int K>
-__device__ __forceinline__ void group_finish(const FrankLaunch& p, const GroupState<K>& s, const Ensemble& e,
-                                          FrankCounters& cnt) {
+template <int K, bool PROD>
+__device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e) {
   using Sh = FrankShape<K>;
   unsigned long long outc[4] = {0, 0, 0, 0};
   for (int l = 0; l < s.nvalid; ++l) {
@@ -502,13 +546,15 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, const GroupSt
     for (int k = 0; k < 4; ++k)
       if (outc[k]) atomicAdd(&p.ens_absorbed[(long long)s.ens * 4 + k], outc[k]);
   }
-  cnt.group_steps += s.step;
-  cnt.lane_steps += s.lane_steps;
-  cnt.reactions += s.reactions;
-  cnt.null_steps += s.lane_steps - s.reactions;
-  cnt.redraws += s.redraws;
-  cnt.absorbed += (unsigned long long)__popc(s.valid & ~s.live);
-  cnt.groups += 1;
+  const uint32_t valid = s.nvalid >= 32 ? 0xFFFFFFFFu : ((1u << s.nvalid) - 1u);
+  s.lane_steps += (unsigned long long)__popc(s.live) * s.step;  // lanes that never absorbed
+  atomicAdd(&p.counters[kGroupSteps], s.step);
+  atomicAdd(&p.counters[kLaneSteps], s.lane_steps);
+  atomicAdd(&p.counters[kReactions], s.reactions);
+  atomicAdd(&p.counters[kNullLaneSteps], s.lane_steps - s.reactions);
+  if (s.redraws) atomicAdd(&p.counters[kRedrawRounds], (unsigned long long)s.redraws);
+  atomicAdd(&p.counters[kAbsorbed], (unsigned long long)__popc(valid & ~s.live));
+  atomicAdd(&p.counters[kGroupsDone], 1ull);
 }
 
 // The persistent kernel.  Every thread owns one group at a time and takes the next
@@ -518,7 +564,7 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, const GroupSt
 // snapshots, absorptions, a new group) cost one pass each instead of leaving the warp
 // split for the rest of the run.  Single-ensemble launches read the ensemble from the
 // kernel parameters (warp-uniform); batches from a table.
-template <int K, bool BATCH>
+template <int K, bool BATCH, bool PROD>
 __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ FrankLaunch p) {
   extern __shared__ unsigned int s_hist_mem[];
   const bool smem_hist = !BATCH && p.n_snap > 0;
@@ -527,9 +573,8 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
     for (int i = threadIdx.x; i < p.n_snap * kHistBins; i += blockDim.x) s_hist_mem[i] = 0u;
     __syncthreads();
   }
-  FrankCounters cnt = {0, 0, 0, 0, 0, 0, 0};
   unsigned int errors = 0u;
-  GroupState<K> s;
+  GroupState<K, PROD> s;
   s.done = true;
   bool active = false, exhausted = false;
   const Threshold* thr = p.thr;
@@ -539,37 +584,25 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
       if (item >= p.item_end) {
         exhausted = true;
       } else if (!BATCH) {
-        group_init<K>(p, s, p.ens, thr, item, 0, s_hist);
+        group_init<K, PROD>(p, s, p.ens, thr, item, 0, s_hist);
         active = true;
       } else {
         const int ei = p.item_ens[item];
         thr = p.thr + (long long)ei * (p.n_snap + 1);
-        group_init<K>(p, s, p.ens_table[ei], thr, p.item_group[item], ei, nullptr);
+        group_init<K, PROD>(p, s, p.ens_table[ei], thr, p.item_group[item], ei, nullptr);
         active = true;
       }
     }
     if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
     if (active) {
       const Ensemble& e = BATCH ? p.ens_table[s.ens] : p.ens;
-      if (!s.done) group_step<K>(p, s, e, thr, s_hist, errors);
+      if (!s.done) group_step<K, PROD>(p, s, e, thr, s_hist, errors);
       if (s.done) {
-        group_finish<K>(p, s, e, cnt);
+        group_finish<K, PROD>(p, s, e);
         active = false;
       }
     }
     __syncwarp();
-  }
-  // flush: warp sums, one atomic per warp per counter
-  unsigned long long v[7] = {cnt.group_steps, cnt.lane_steps, cnt.reactions, cnt.null_steps,
-                             cnt.redraws, cnt.absorbed, cnt.groups};
-  const int ctr_index[7] = {kGroupSteps, kLaneSteps, kReactions, kNullLaneSteps, kRedrawRounds, kAbsorbed,
-                            kGroupsDone};
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    unsigned long long x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&p.counters[ctr_index[k]], x);
   }
   const unsigned int err = __reduce_or_sync(0xFFFFFFFFu, errors);
   if ((threadIdx.x & 31) == 0 && err) atomicOr(p.status, err);

@@ -119,8 +119,9 @@ struct ThreadLaunch {
 // Entry points implemented by the kernel translation units.
 using FrankLauncher = int (*)(const FrankLaunch&, int grid, int block, int smem, void* stream);
 FrankLauncher frank_launcher(int K);
-int frank_max_active_blocks(int K, int batch, int block, int smem, int* blocks);
-int frank_registers(int K, int batch);
+// variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64)
+int frank_max_active_blocks(int K, int variant, int block, int smem, int* blocks);
+int frank_registers(int K, int variant);
 int thread_per_run_launch(const ThreadLaunch& p, int grid, int block, int smem, void* stream);
 int thread_per_run_max_active_blocks(int block, int smem, int* blocks);
 

@@ -425,7 +425,7 @@ int launch_runs(ssa_ctx* c) {
     fl.queue = c->d_counters + kCounters;
     const int smem = n_snap * kHistBins * (int)sizeof(unsigned int);
     int occ = 0;
-    if (frank_max_active_blocks(K, 0, block, smem, &occ) != 0 || occ < 1)
+    if (frank_max_active_blocks(K, c->opt.precision == SSA_P64 ? 2 : 0, block, smem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (groups + block - 1) / block;
@@ -444,7 +444,7 @@ int launch_runs(ssa_ctx* c) {
     fl.item_end = c->ranges[r].second.second;
     fl.queue = c->d_counters + kCounters + 1 + r;
     int occ = 0;
-    if (frank_max_active_blocks(K, 1, block, 0, &occ) != 0 || occ < 1)
+    if (frank_max_active_blocks(K, c->opt.precision == SSA_P64 ? 3 : 1, block, 0, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (fl.item_end - fl.item_begin + block - 1) / block;

@@ -66,15 +66,20 @@ __global__ void bitslice_kernel(int op, const long long* x, const long long* y, 
 }
 
 __global__ void alu_kernel(uint32_t seed, int iters, uint32_t* sink) {
-  uint32_t a[8];
-  const uint32_t b = seed * 0x9E3779B9u + threadIdx.x, c = seed ^ (blockIdx.x * 0x85EBCA6Bu);
+  // 8 independent chains per thread; each LOP3 mixes the chain's value with two
+  // loop-invariant registers, so the chains never wait on one another
+  uint32_t a[8], b[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) a[j] = threadIdx.x * (j + 1) + seed;
+  for (int j = 0; j < 8; ++j) {
+    a[j] = threadIdx.x * (j + 1) + seed;
+    b[j] = (seed + j) * 0x9E3779B9u ^ blockIdx.x;
+  }
+  const uint32_t c0 = seed ^ 0x85EBCA6Bu, c1 = seed * 0xC2B2AE35u;
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = bs::maj(a[j], a[(j + 3) & 7], (c + (uint32_t)r) ^ b);
+      for (int j = 0; j < 8; ++j) a[j] = bs::maj(a[j], b[j], (r & 1) ? c1 : c0);
     }
   }
   uint32_t s = 0;
