@@ -222,7 +222,7 @@ def main():
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    reactions = absorbed = lane_steps = group_steps = 0
+    reactions = absorbed = lane_steps = group_steps = max_group_steps = 0
     barrier()
     t_wall0 = time.perf_counter()
     for k in range(args.steps):
@@ -235,6 +235,7 @@ def main():
         lane_steps += int(c[1])
         group_steps += int(c[0])
         absorbed += int(c[5])
+        max_group_steps = max(max_group_steps, int(c[8]))
     barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
@@ -276,6 +277,7 @@ def main():
               "data": "synthetic", "config": workload_config(world),
               "absorbed_runs_per_s": absorbed / t_dev, "lane_steps_per_s": lane_steps / t_dev,
               "reactions_per_step": reactions / args.steps, "wall_s": wall,
+              "group_steps_per_step": group_steps / args.steps, "max_group_steps": max_group_steps,
               "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
               "hist_checksum": float(htot.sum().item())}
 

@@ -104,13 +104,14 @@ enum {
                                    (L, D) = (species chiral[0], chiral[1]) at each snapshot:
                                    bin min(63, floor(64 L / (L + D))), bin 64 = L + D == 0 */
   SSA_FIELD_SNAP_COUNTS = 4,    /* int32[n_snap][n_runs][S] (needs keep_snap_counts = 1) */
-  SSA_FIELD_COUNTERS = 5,       /* uint64[8]: group steps, lane steps of live runs, real
+  SSA_FIELD_COUNTERS = 5,       /* uint64[10]: group steps, lane steps of live runs, real
                                    reactions, null lane steps, redraw rounds, absorbed runs,
-                                   groups finished, error flags */
+                                   groups finished, error flags, steps of the longest group,
+                                   0 (reserved) */
   SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,
                                    and runs not absorbed, per ensemble */
 };
-#define SSA_N_COUNTERS 8
+#define SSA_N_COUNTERS 10
 
 void ssa_default_options(ssa_options* opt);
 

@@ -28,9 +28,9 @@ SSA_P64, SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P64_LOGSUM = 0, 1, 2, 3
 SSA_ENGINE_BITSLICED, SSA_ENGINE_THREAD_PER_RUN = 0, 1
 SSA_FIELD_FINAL_COUNTS, SSA_FIELD_ABSORB_TIME, SSA_FIELD_ABSORB_OUTCOME = 0, 1, 2
 SSA_FIELD_EE_HIST, SSA_FIELD_SNAP_COUNTS, SSA_FIELD_COUNTERS, SSA_FIELD_ENS_ABSORBED = 3, 4, 5, 6
-SSA_N_COUNTERS = 8
+SSA_N_COUNTERS = 10
 COUNTER_NAMES = ["group_steps", "lane_steps", "reactions", "null_lane_steps", "redraw_rounds",
-                 "absorbed", "groups_done", "error_flags"]
+                 "absorbed", "groups_done", "error_flags", "max_group_steps", "reserved"]
 
 _FIELD_DTYPE = {
     SSA_FIELD_FINAL_COUNTS: np.int32, SSA_FIELD_ABSORB_TIME: np.float64,

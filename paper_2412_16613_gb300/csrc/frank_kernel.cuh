@@ -456,8 +456,12 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
     x3 &= ~rej;
   }
 
-  // (5) updates from the counts before the reaction (App. B)
+  // (5) updates from the counts before the reaction (App. B).  A step in which no lane
+  // fires (frequent once most lanes of a group have absorbed) changes nothing.
   const uint32_t x12 = x1 | x2;
+  const uint32_t fired = x12 | x3;
+  ++s.step;
+  if (!fired) return;
   {
     uint32_t T[WR1];
 #pragma unroll
@@ -496,8 +500,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   bs::add_select3<-2, -2, 4>(s.U, x1, x2, x3);
   bs::add_select3<3, 1, -4>(s.R1, x1, x2, x3);
   bs::add_select3<3, 3, -6>(s.R3, x1, x2, x3);
-  s.reactions += (unsigned)__popc(x12 | x3);
-  ++s.step;
+  s.reactions += (unsigned)__popc(fired);
 
   // (6) absorption
   const uint32_t now_live = live_lanes(s, e) & s.live;
@@ -555,6 +558,7 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
   if (s.redraws) atomicAdd(&p.counters[kRedrawRounds], (unsigned long long)s.redraws);
   atomicAdd(&p.counters[kAbsorbed], (unsigned long long)__popc(valid & ~s.live));
   atomicAdd(&p.counters[kGroupsDone], 1ull);
+  atomicMax(&p.counters[kMaxGroupSteps], s.step);
 }
 
 // The persistent kernel.  Every thread owns one group at a time and takes the next

@@ -8,7 +8,7 @@ namespace bitssa {
 
 constexpr int kMaxSnap = 64;
 constexpr int kHistBins = 65;  // 64 enantiomeric-excess bins + one for L + D == 0
-constexpr int kCounters = 8;
+constexpr int kCounters = 10;
 constexpr int kMaxK = 31;      // random / propensity planes: N_tot (N_tot - 1) / 2 < 2^31
 
 // Clock precision modes (same values as SSA_P64 ... in bitssa.h).
@@ -23,7 +23,8 @@ enum Counter {
   kRedrawRounds = 4,
   kAbsorbed = 5,
   kGroupsDone = 6,
-  kErrorFlags = 7
+  kErrorFlags = 7,
+  kMaxGroupSteps = 8  // the longest group, in steps
 };
 
 // Error flags (OR-ed into the status word).

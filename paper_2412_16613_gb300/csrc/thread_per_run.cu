@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(256) thread_per_run_kernel(const __grid_consta
       p.outcome[row] = oc;
       outc[oc >= 0 ? oc : 3] += 1;
       c_steps += step;
+      atomicMax(&p.counters[kMaxGroupSteps], step);
       active = false;
     }
     __syncwarp();
