@@ -108,15 +108,15 @@ template <>
 struct Clock<true> {
   double m;
   long long E;
-  double th_m;  // the next time point to cross, in the same form
-  long long th_E;
+  long long th_E;       // exponent of the next time point to cross
+  const double* th_m;   // its mantissa, read only when the exponents tie
   __device__ __forceinline__ void reset() {
     m = 1.0;
     E = 0;
   }
   __device__ __forceinline__ void aim(const Threshold& h) {
-    th_m = h.m;
     th_E = h.E;
+    th_m = &h.m;
   }
   __device__ __forceinline__ double time(const Ensemble& e, int) const {
     return -(log(m) + (double)E * kLn2) / e.lambda;
@@ -152,7 +152,7 @@ __device__ __forceinline__ bool clock_advance(const Clock<true>& c, Clock<true>&
   nx = c;
   nx.E = c.E + (long long)(((hi >> 20) & 0x7FF) - 1023);
   nx.m = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, lo);
-  return nx.E < c.th_E || (nx.E == c.th_E && nx.m < c.th_m);
+  return nx.E < c.th_E || (nx.E == c.th_E && nx.m < *c.th_m);
 }
 
 __device__ __forceinline__ bool clock_advance(const Clock<false>& c, Clock<false>& nx, uint32_t wk, uint32_t wk1,
@@ -178,7 +178,7 @@ __device__ __forceinline__ bool clock_advance(const Clock<false>& c, Clock<false
 }
 
 __device__ __forceinline__ bool clock_crosses(const Clock<true>& nx) {
-  return nx.E < nx.th_E || (nx.E == nx.th_E && nx.m < nx.th_m);
+  return nx.E < nx.th_E || (nx.E == nx.th_E && nx.m < *nx.th_m);
 }
 __device__ __forceinline__ bool clock_crosses(const Clock<false>& nx, int precision) {
   return precision == kP32Kahan ? nx.t_f > nx.th_f : nx.t > nx.th_t;
@@ -195,13 +195,18 @@ struct GroupState {
   int nvalid;        // lanes holding a run (the last group may be partial)
   int ens;           // ensemble index
   int snap;          // next snapshot
-  long long row0;    // output row of lane 0
   unsigned long long step;
   Clock<PROD> clk;
   unsigned long long reactions, lane_steps;
   unsigned int redraws;
   bool done;
 };
+
+// Output row of lane 0 of the group.
+template <int K, bool PROD>
+__device__ __forceinline__ long long group_row0(const GroupState<K, PROD>& s, const Ensemble& e) {
+  return e.run_offset + ((long long)s.sgroup - e.group_base) * 32;
+}
 
 template <int K, bool PROD>
 __device__ __forceinline__ uint32_t live_lanes(const GroupState<K, PROD>& s, const Ensemble& e) {
@@ -224,7 +229,7 @@ __device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K
     if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(cl, cd)], 1u);
     else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + ee_bin(cl, cd)], 1ull);
     if (p.snap_counts) {
-      int* o = p.snap_counts + ((long long)snap * p.n_runs_total + s.row0 + l) * p.n_species;
+      int* o = p.snap_counts + ((long long)snap * p.n_runs_total + group_row0(s, e) + l) * p.n_species;
       o[p.perm[0]] = cl;
       o[p.perm[1]] = cd;
       o[p.perm[2]] = ca;
@@ -245,7 +250,7 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K, P
   s.nvalid = left >= 32 ? 32 : (int)left;
   const uint32_t valid = s.nvalid >= 32 ? 0xFFFFFFFFu : ((1u << s.nvalid) - 1u);
   s.sgroup = (uint32_t)(e.group_base + group_local);
-  s.row0 = e.run_offset + run0;
+  const long long row0 = e.run_offset + run0;
   s.ens = ens_index;
   const int n_tot = e.n_tot;
 
@@ -256,7 +261,7 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K, P
     bs::broadcast(Dp, 0);
     bs::broadcast(Ap, n_tot);
     for (int l = 0; l < s.nvalid; ++l) {
-      const int* c = p.init_counts + (s.row0 + l) * 3;
+      const int* c = p.init_counts + (row0 + l) * 3;
       bs::set_lane(Lp, l, c[0]);
       bs::set_lane(Dp, l, c[1]);
       bs::set_lane(Ap, l, c[2]);
@@ -325,7 +330,7 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K, P
   while (at0) {
     const int l = __ffs(at0) - 1;
     at0 &= at0 - 1;
-    p.t_abs[s.row0 + l] = 0.0;
+    p.t_abs[row0 + l] = 0.0;
   }
   s.step = 0;
   s.clk.reset();
@@ -511,7 +516,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
     while (newly) {
       const int l = __ffs(newly) - 1;
       newly &= newly - 1;
-      p.t_abs[s.row0 + l] = tn;
+      p.t_abs[group_row0(s, e) + l] = tn;
     }
     s.live = now_live;
     if (!s.live) {
@@ -529,7 +534,7 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
   for (int l = 0; l < s.nvalid; ++l) {
     int cl, cd, ca;
     lane_counts<Sh::B, Sh::WP>(s.L, s.U, e.n_tot, l, cl, cd, ca);
-    int* o = p.final_counts + (s.row0 + l) * p.n_species;
+    int* o = p.final_counts + (group_row0(s, e) + l) * p.n_species;
     o[p.perm[0]] = cl;
     o[p.perm[1]] = cd;
     o[p.perm[2]] = ca;
@@ -539,10 +544,10 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
       oc = nz == 1 ? (signed char)(cl ? p.perm[0] : (cd ? p.perm[1] : p.perm[2])) : (signed char)-2;
       outc[nz == 1 ? (int)oc : 3] += 1;  // [3] also counts absorbed-with-several
     } else {
-      p.t_abs[s.row0 + l] = __longlong_as_double(0x7FF0000000000000ll);
+      p.t_abs[group_row0(s, e) + l] = __longlong_as_double(0x7FF0000000000000ll);
       outc[3] += 1;
     }
-    p.outcome[s.row0 + l] = oc;
+    p.outcome[group_row0(s, e) + l] = oc;
   }
   if (p.ens_absorbed) {
 #pragma unroll
