@@ -188,6 +188,48 @@ typedef void* (*ssa_alloc_fn)(size_t bytes, int device, void* stream, void* user
 typedef void (*ssa_free_fn)(void* ptr, size_t bytes, int device, void* stream, void* user);
 int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
 
+/*
+ * ssa_run_frank_noalloc: one run of Frank's model that allocates no device memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that cannot
+ * allocate: work recorded into a CUDA stream capture (where cudaMalloc is not
+ * allowed), plug-ins whose host framework owns all device memory and forbids
+ * allocations outside its pool, and latency-critical loops in which an allocation
+ * could synchronise the device.  It runs the same bit-sliced kernel as ssa_run on
+ * a context-free single ensemble; the caller passes every input and output buffer.
+ *
+ * The kernel's own scratch (work-queue counter, run counters, error word and the
+ * snapshot thresholds, about 2.2 KB) is a fixed device array inside the library,
+ * one per GPU that loads the library, held until the process exits.  Its device
+ * address is looked up on the first call on each device (with that device
+ * current), so make that first call before any stream capture.  Every call clears
+ * the parts that must start at zero, and calls share the array: calls that
+ * overlap on the GPU (other streams, other host threads on the same device) race
+ * and must be serialised by the caller.
+ *
+ *   N0: int64[3] host, the shared initial counts in Frank's species order (L, D, A)
+ *       for the reactions A+L->2L, A+D->2D, L+D->2A (Eqs. 1-3); total in [1, 65536].
+ *   rates: double[3] host, k >= 0 with max > 0 (thinning as in ssa_create, q = thin_bits).
+ *   n_runs >= 0, seed: as in ssa_create (run j is lane j % 32 of group j / 32).
+ *   t_end, snapshot_times (double[n_snap] host, ascending, in [0, t_end]), n_snap in
+ *       [0, 64]: as in ssa_run.  n_snap above 64, the capacity of the fixed scratch,
+ *       is rejected with SSA_EINVAL before any GPU work.
+ *   precision: SSA_P64 ... SSA_P64_LOGSUM.
+ *   outputs, device memory on the current device, written on cuda_stream:
+ *       final_counts int32[n_runs][3], t_abs double[n_runs], outcome int8[n_runs]
+ *       (as SSA_FIELD_FINAL_COUNTS / ABSORB_TIME / ABSORB_OUTCOME, species order L, D, A),
+ *       ee_hist uint64[n_snap][65] (cleared by the call; may be NULL when n_snap == 0).
+ *   counters_out: uint64[10] host (as SSA_FIELD_COUNTERS) or NULL.
+ *   cuda_stream: cudaStream_t, NULL = the legacy default stream.
+ * Blocks until the work is done.  Returns an ssa_status; the message of a failure is
+ * given by ssa_last_error(NULL) on the calling thread.  Calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ */
+int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int64_t n_runs, uint64_t seed,
+                          int32_t thin_bits, double t_end, const double* snapshot_times, int32_t n_snap,
+                          int32_t precision, int32_t* final_counts, double* t_abs, int8_t* outcome,
+                          uint64_t* ee_hist, uint64_t* counters_out, void* cuda_stream);
+
 /* Library version as major * 10000 + minor * 100 + patch. */
 int ssa_version(void);
 

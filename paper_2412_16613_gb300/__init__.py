@@ -95,6 +95,10 @@ def lib():
             L.ssa_last_error.restype = C.c_char_p
             L.ssa_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, C.c_void_p]
             L.ssa_version.restype = C.c_int
+            L.ssa_run_frank_noalloc.argtypes = [P(C.c_int64), P(C.c_double), C.c_int64, C.c_uint64,
+                                                C.c_int32, C.c_double, P(C.c_double), C.c_int32,
+                                                C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                C.c_void_p, P(C.c_uint64), C.c_void_p]
             L.bitssa_test_philox.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32), C.c_int64, C.c_int32]
             L.bitssa_test_bitslice.argtypes = [C.c_int32, P(C.c_int64), P(C.c_int64), P(C.c_int64), C.c_int64]
             L.bitssa_bench_alu.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_double)]
@@ -209,6 +213,29 @@ def ssa_fetch(ctx, field, out=None):
         assert out.is_contiguous() and out.is_cuda
         _check(lib().ssa_fetch(ctx, field, out.data_ptr(), out.numel() * out.element_size(), 1), ctx)
     return out
+
+
+def ssa_run_frank_noalloc(N0, rates, n_runs, seed, t_end, snapshot_times, final_counts, t_abs, outcome,
+                          ee_hist=None, precision=SSA_P64, thin_bits=32, stream=None):
+    """C ssa_run_frank_noalloc: outputs are CUDA torch tensors (or raw device pointers)
+    that the caller owns; the library allocates nothing.  Returns the counters."""
+    n0 = np.ascontiguousarray(N0, dtype=np.int64)
+    k = np.ascontiguousarray(rates, dtype=np.float64)
+    snaps = np.ascontiguousarray(snapshot_times, dtype=np.float64)
+    counters = np.zeros(SSA_N_COUNTERS, dtype=np.uint64)
+
+    def ptr(x):
+        return None if x is None else (x if isinstance(x, int) else x.data_ptr())
+
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    st = lib().ssa_run_frank_noalloc(_p(n0, C.c_int64), _p(k, C.c_double), int(n_runs),
+                                     int(seed) & (2**64 - 1), int(thin_bits), float(t_end),
+                                     _p(snaps, C.c_double) if len(snaps) else None, len(snaps),
+                                     int(precision), ptr(final_counts), ptr(t_abs), ptr(outcome),
+                                     ptr(ee_hist), _p(counters, C.c_uint64), stream)
+    _check(st)
+    return dict(zip(COUNTER_NAMES, counters.tolist()))
 
 
 def ssa_destroy(ctx):

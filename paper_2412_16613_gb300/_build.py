@@ -45,7 +45,7 @@ def _jobs():
     for k in K_VALUES:
         jobs.append((os.path.join(CSRC, "frank_instance.cu"), os.path.join(BUILD, f"frank_k{k:02d}.o"),
                      [f"-DBITSSA_K={k}"]))
-    for name in ("frank_dispatch", "thread_per_run", "runtime", "selftest"):
+    for name in ("frank_dispatch", "thread_per_run", "runtime", "selftest", "noalloc"):
         jobs.append((os.path.join(CSRC, name + ".cu"), os.path.join(BUILD, name + ".o"), []))
     return jobs
 

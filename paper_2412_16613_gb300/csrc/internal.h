@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 
 namespace bitssa {
 
@@ -124,6 +125,8 @@ FrankLauncher frank_launcher(int K);
 int frank_max_active_blocks(int K, int variant, int block, int smem, int* blocks);
 int frank_registers(int K, int variant);
 int thread_per_run_launch(const ThreadLaunch& p, int grid, int block, int smem, void* stream);
+// Sets the calling thread's message returned by ssa_last_error(NULL).
+void set_thread_error(const std::string& msg);
 int thread_per_run_max_active_blocks(int block, int smem, int* blocks);
 
 }  // namespace bitssa

@@ -471,6 +471,10 @@ size_t field_bytes(const ssa_ctx* c, int field) {
 
 }  // namespace
 
+namespace bitssa {
+void set_thread_error(const std::string& msg) { t_err = msg; }
+}  // namespace bitssa
+
 extern "C" {
 
 void ssa_default_options(ssa_options* opt) {
