@@ -156,12 +156,43 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+WORKLOAD = "c2"
+BATCH = None
+PRECISION = 0
+PRECISION_NAMES = {0: "p64", 1: "p32kahan", 2: "p32d64acc", 3: "p64logsum", 4: "p32plain"}
+
+
+def set_workload(name, runs):
+    """Workload constants: the metric's workload (c2) or the other configurations."""
+    global WORKLOAD, N_TOT, INIT, RUNS_PER_GPU, T_END, SNAPS, BATCH
+    WORKLOAD = name
+    if name == "c4":
+        N_TOT, INIT, RUNS_PER_GPU = 10000, (2500, 2500, 5000), 1 << 22
+    if name == "c3":
+        from paper_2412_16613_gb300 import workloads
+        BATCH = workloads.batch_ensembles()
+        RUNS_PER_GPU = int(BATCH["runs"].sum())
+    if runs:
+        RUNS_PER_GPU = runs
+
+
 def workload_config(world):
+    if WORKLOAD == "c3":
+        return {"workload": f"frank_batch{len(BATCH['runs'])}ens_N16-65536loguniform_rates0.5-2_runs1024_tend{T_END:g}"
+                            f"_snap{N_SNAP}log",
+                "model": "Frank, per-ensemble rates", "ensembles": len(BATCH["runs"]),
+                "runs": RUNS_PER_GPU * world, "runs_per_gpu": RUNS_PER_GPU, "t_end": T_END,
+                "global_batch": RUNS_PER_GPU * world, "parallelism": f"replicas x{world}",
+                "l2": "L2 flushed between timed steps (256 MiB write)"}
+    return workload_config_single(world)
+
+
+def workload_config_single(world):
     return {"workload": f"frank_N{N_TOT}_{INIT[0]}-{INIT[1]}-{INIT[2]}_runs{RUNS_PER_GPU}xgpu_tend{T_END:g}"
-                        f"_snap{N_SNAP}log_p64",
+                        f"_snap{N_SNAP}log_{PRECISION_NAMES[PRECISION]}",
             "model": "Frank (A+L->2L, A+D->2D, L+D->2A), k=(1,1,1)", "N_tot": N_TOT, "init": list(INIT),
             "runs": RUNS_PER_GPU * world, "runs_per_gpu": RUNS_PER_GPU, "groups_per_gpu": RUNS_PER_GPU // 32,
-            "seed": SEED, "t_end": T_END, "snapshots": SNAPS, "precision": "P64 (product clock)",
+            "seed": SEED, "t_end": T_END, "snapshots": SNAPS, "precision": PRECISION_NAMES[PRECISION],
             "global_batch": RUNS_PER_GPU * world, "parallelism": f"replicas x{world} (run shards)",
             "l2": "L2 flushed between timed steps (256 MiB write)"}
 
@@ -178,11 +209,17 @@ def main():
     ap.add_argument("--no-baselines", action="store_true", help="skip the K7 and CPU legs")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--precision", type=int, default=0)
-    ap.add_argument("--runs", type=int, default=RUNS_PER_GPU,
+    ap.add_argument("--runs", type=int, default=0,
                     help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+                    help="c2: N_tot=1024, 2^20 runs (the metric's workload); c3: 4096 ensembles "
+                         "with log-uniform N_tot in [16, 65536] and rates in [0.5, 2], 1024 runs each; "
+                         "c4: N_tot=10000, 2^22 runs")
     args = ap.parse_args()
     rank, world, local = env_rank()
-    RUNS_PER_GPU = args.runs
+    set_workload(args.workload, args.runs)
+    global PRECISION
+    PRECISION = args.precision
 
     if args.impl == "reference":
         if world > 1:
@@ -207,8 +244,13 @@ def main():
     stream = torch.cuda.current_stream()
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                   block_size=args.block, first_run=rank * RUNS_PER_GPU)
-    ctx = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
-                         RUNS_PER_GPU, SEED, opt)
+    if WORKLOAD == "c3":
+        opt.first_run = 0
+        ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],
+                                   BATCH["runs"], BATCH["seeds"] + np.uint64(rank * len(BATCH["runs"])), opt)
+    else:
+        ctx = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
+                             RUNS_PER_GPU, SEED, opt)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
 
     def barrier():
@@ -241,7 +283,7 @@ def main():
     clk = clocks.stop()
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
     t_dev = sum(kernel_ms) / 1e3
-    hist = pkg.ssa_fetch(ctx, pkg.SSA_FIELD_EE_HIST).reshape(N_SNAP, 65)
+    hist = pkg.ssa_fetch(ctx, pkg.SSA_FIELD_EE_HIST).reshape(-1, N_SNAP, 65).sum(0)
     # max over ranks of the device time; totals over ranks
     totals = torch.tensor([reactions, absorbed, lane_steps, group_steps], dtype=torch.float64, device="cuda")
     tmax = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
@@ -253,7 +295,8 @@ def main():
     reactions, absorbed, lane_steps, group_steps = [float(x) for x in totals.tolist()]
     t_dev = float(tmax.item())
 
-    # ---- roofline of the bit-sliced kernel (one launch per step)
+    # ---- roofline of the bit-sliced kernel (one launch per step; a batch runs one launch per
+    # number of planes K, so its per-unit count is not a single figure and is not reported)
     K, b = bit_length(N_TOT * (N_TOT - 1) // 2), bit_length(N_TOT)
     ops_unit = algorithmic_ops_per_group_step(K, b)
     gs_per_launch = group_steps / world / args.steps
@@ -270,6 +313,8 @@ def main():
                 "ops_per_group_step": ops_unit, "group_steps_per_launch": gs_per_launch,
                 "peak_basis": f"{SMS} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {MAX_SM_MHZ:g} MHz",
                 "lop3_microbench_gops": micro}
+    if WORKLOAD == "c3":
+        roofline = None
 
     result = {"metric": METRIC, "value": reactions / t_dev, "unit": "lane-reactions/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
@@ -290,13 +335,19 @@ def main():
                "init": np.array(INIT, dtype=np.int64)}
     h2d = sum(v.nbytes for v in host_in.values()) + 8 * (N_SNAP + 1)
     d2h = sum(t.numel() for t in pinned.values())
+    if WORKLOAD == "c3":
+        h2d = sum(np.asarray(BATCH[k]).nbytes for k in ("init", "rates", "runs", "seeds")) + 144
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     e2e_react = 0
     for _ in range(e2e_steps):
-        c2 = pkg.ssa_create(host_in["reac"], host_in["prod"], host_in["rates"], host_in["init"], RUNS_PER_GPU,
-                            SEED, opt)
+        if WORKLOAD == "c3":
+            c2 = pkg.ssa_create_batch(host_in["reac"], host_in["prod"], BATCH["init"], BATCH["rates"], BATCH["runs"],
+                                      BATCH["seeds"] + np.uint64(rank * len(BATCH["runs"])), opt)
+        else:
+            c2 = pkg.ssa_create(host_in["reac"], host_in["prod"], host_in["rates"], host_in["init"], RUNS_PER_GPU,
+                                SEED, opt)
         pkg.ssa_run(c2, T_END, SNAPS)
         for f, t in pinned.items():
             pkg.ssa_fetch(c2, f, t.numpy())
@@ -309,7 +360,7 @@ def main():
     pkg.ssa_destroy(ctx)
 
     # ---- the one-thread-per-run GPU baseline on the same workload and precision
-    if not args.no_baselines:
+    if not args.no_baselines and WORKLOAD != "c3":
         o7 = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                      engine=pkg.SSA_ENGINE_THREAD_PER_RUN, first_run=rank * RUNS_PER_GPU)
         c7 = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
@@ -329,7 +380,8 @@ def main():
                                     "absorbed_runs_per_s": int(c[5]) * world / (ms7 / 1e3),
                                     "speedup_bitsliced_over_thread_per_run": (reactions / t_dev) / (r7 * world)}
         if rank == 0:
-            result["cpu_baseline"] = cpu_baseline(args.cpu_sample, os.cpu_count() or 1)
+            sample = args.cpu_sample if WORKLOAD == "c2" else max(64, args.cpu_sample // 8)
+            result["cpu_baseline"] = cpu_baseline(sample, os.cpu_count() or 1)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:

@@ -63,8 +63,10 @@ enum {
   SSA_P32_KAHAN = 1,  /* fp32: u from the top 24 of those bits, tau = -logf(u) / Lambda,
                          Kahan-compensated fp32 time sum */
   SSA_P32_D64ACC = 2, /* fp32 tau as above, fp64 time accumulator */
-  SSA_P64_LOGSUM = 3  /* fp64: tau = -log(u) / Lambda and t += tau every step, the
+  SSA_P64_LOGSUM = 3, /* fp64: tau = -log(u) / Lambda and t += tau every step, the
                          literal form of Eq. equation-tau and Eq. eq-update-time */
+  SSA_P32_PLAIN = 4   /* fp32 tau, plain fp32 time sum without compensation (a control
+                         for the precision comparison) */
 };
 
 /* Simulation engine. */
@@ -76,7 +78,8 @@ enum {
 };
 
 typedef struct {
-  int32_t precision;         /* SSA_P64 (default) | SSA_P32_KAHAN | SSA_P32_D64ACC | SSA_P64_LOGSUM */
+  int32_t precision;         /* SSA_P64 (default) | SSA_P32_KAHAN | SSA_P32_D64ACC | SSA_P64_LOGSUM |
+                                SSA_P32_PLAIN */
   int32_t engine;            /* SSA_ENGINE_BITSLICED (default) | SSA_ENGINE_THREAD_PER_RUN */
   int32_t block_size;        /* threads per block, 0 = chosen from occupancy */
   int32_t blocks_per_sm;     /* resident blocks per SM to launch, 0 = occupancy limit */
@@ -214,7 +217,7 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
  *   t_end, snapshot_times (double[n_snap] host, ascending, in [0, t_end]), n_snap in
  *       [0, 64]: as in ssa_run.  n_snap above 64, the capacity of the fixed scratch,
  *       is rejected with SSA_EINVAL before any GPU work.
- *   precision: SSA_P64 ... SSA_P64_LOGSUM.
+ *   precision: SSA_P64 ... SSA_P32_PLAIN.
  *   outputs, device memory on the current device, written on cuda_stream:
  *       final_counts int32[n_runs][3], t_abs double[n_runs], outcome int8[n_runs]
  *       (as SSA_FIELD_FINAL_COUNTS / ABSORB_TIME / ABSORB_OUTCOME, species order L, D, A),

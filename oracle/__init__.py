@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-P64, P32_KAHAN, P32_D64ACC = 0, 1, 2
+P64, P32_KAHAN, P32_D64ACC, P32_PLAIN = 0, 1, 2, 3
 OK, EINVAL, ETIMEOUT, ERANGE = 0, -1, -5, -6
 MAX_SPECIES = 8
 MAX_REACTIONS = 8

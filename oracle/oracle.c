@@ -153,7 +153,7 @@ int orc_derive(const orc_problem* p, orc_derived* d) {
   if (p->n_reactions < 1 || p->n_reactions > ORC_MAX_REACTIONS) return ORC_EINVAL;
   if (p->n_tot < 1 || p->n_tot > (1 << 20)) return ORC_EINVAL;
   if (p->thin_bits < 1 || p->thin_bits > 64) return ORC_EINVAL;
-  if (p->precision < ORC_P64 || p->precision > ORC_P32_D64ACC) return ORC_EINVAL;
+  if (p->precision < ORC_P64 || p->precision > ORC_P32_PLAIN) return ORC_EINVAL;
   if (!(p->t_end >= 0.0) || p->n_snap < 0) return ORC_EINVAL;
   for (int s = 0; s < p->n_snap; s++) {
     if (!(p->snap_times[s] >= 0.0) || p->snap_times[s] > p->t_end) return ORC_EINVAL;
@@ -318,6 +318,9 @@ int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index, const
         c_f_new = (sum - t_f) - y;
         t_f_new = sum;
         t_new = (double)sum;
+      } else if (p->precision == ORC_P32_PLAIN) {
+        t_f_new = t_f + tau;
+        t_new = (double)t_f_new;
       } else {
         t_new = t + (double)tau;
       }
@@ -387,7 +390,7 @@ fill_snapshots:
       for (int i = 0; i < S; i++) snap_counts[(int64_t)next_snap * S + i] = n[i];
   for (int i = 0; i < S; i++) out->final_counts[i] = n[i];
   out->steps = step;
-  out->t_last = (p->precision == ORC_P32_KAHAN) ? (double)t_f : t;
+  out->t_last = (p->precision == ORC_P32_KAHAN || p->precision == ORC_P32_PLAIN) ? (double)t_f : t;
   return out->status;
 }
 

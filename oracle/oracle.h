@@ -47,6 +47,7 @@ extern "C" {
 #define ORC_P64 0        /* u from 53 bits, tau = -log(u)/Lambda, double sum */
 #define ORC_P32_KAHAN 1  /* u from 24 bits, tau = -logf(u)*(float)(1/Lambda), Kahan float sum */
 #define ORC_P32_D64ACC 2 /* float tau as above, double accumulator */
+#define ORC_P32_PLAIN 3  /* float tau as above, plain float sum (no compensation) */
 
 /* status codes */
 #define ORC_OK 0
@@ -62,7 +63,7 @@ typedef struct {
   const double* rates;      /* [R] k_r >= 0, max > 0 */
   int64_t n_tot;            /* conserved total count, >= 1 */
   uint64_t seed;            /* Philox key */
-  int32_t precision;        /* ORC_P64 | ORC_P32_KAHAN | ORC_P32_D64ACC */
+  int32_t precision;        /* ORC_P64 | ORC_P32_KAHAN | ORC_P32_D64ACC | ORC_P32_PLAIN */
   int32_t thin_bits;        /* q, 1..64 */
   double t_end;             /* stop before the first event later than t_end */
   const double* snap_times; /* [n_snap] ascending, <= t_end (may be NULL if n_snap == 0) */

@@ -98,8 +98,8 @@ __device__ __forceinline__ int ee_bin(int l, int d) {
 // step's uniform u (one fp64 multiply, the exponent renormalised with integer
 // ops), so t = -(ln m + E ln 2) / Lambda needs a logarithm only when a time is
 // written out.  Otherwise: the fp64 sum of -log(u) / Lambda (SSA_P64_LOGSUM), or
-// fp32 -logf(u) / Lambda summed with Kahan compensation (SSA_P32_KAHAN) or into
-// an fp64 accumulator (SSA_P32_D64ACC).
+// fp32 -logf(u) / Lambda summed with Kahan compensation (SSA_P32_KAHAN), into an
+// fp64 accumulator (SSA_P32_D64ACC) or plainly in fp32 (SSA_P32_PLAIN).
 // ---------------------------------------------------------------------------
 template <bool PROD>
 struct Clock;
@@ -138,7 +138,7 @@ struct Clock<false> {
     th_f = h.t_f;
   }
   __device__ __forceinline__ double time(const Ensemble&, int precision) const {
-    return precision == kP32Kahan ? (double)t_f : t;
+    return (precision == kP32Kahan || precision == kP32Plain) ? (double)t_f : t;
   }
 };
 
@@ -173,6 +173,10 @@ __device__ __forceinline__ bool clock_advance(const Clock<false>& c, Clock<false
     nx.t_f = sum;
     return sum > c.th_f;
   }
+  if (precision == kP32Plain) {
+    nx.t_f = c.t_f + tau;
+    return nx.t_f > c.th_f;
+  }
   nx.t = c.t + (double)tau;
   return nx.t > c.th_t;
 }
@@ -181,7 +185,7 @@ __device__ __forceinline__ bool clock_crosses(const Clock<true>& nx) {
   return nx.E < nx.th_E || (nx.E == nx.th_E && nx.m < *nx.th_m);
 }
 __device__ __forceinline__ bool clock_crosses(const Clock<false>& nx, int precision) {
-  return precision == kP32Kahan ? nx.t_f > nx.th_f : nx.t > nx.th_t;
+  return (precision == kP32Kahan || precision == kP32Plain) ? nx.t_f > nx.th_f : nx.t > nx.th_t;
 }
 
 // Everything one thread keeps about its group between steps (all in registers).

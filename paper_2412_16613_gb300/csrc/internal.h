@@ -13,7 +13,7 @@ constexpr int kCounters = 10;
 constexpr int kMaxK = 31;      // random / propensity planes: N_tot (N_tot - 1) / 2 < 2^31
 
 // Clock precision modes (same values as SSA_P64 ... in bitssa.h).
-enum Precision { kP64 = 0, kP32Kahan = 1, kP32D64Acc = 2, kP64LogSum = 3 };
+enum Precision { kP64 = 0, kP32Kahan = 1, kP32D64Acc = 2, kP64LogSum = 3, kP32Plain = 4 };
 
 // Indices into the device counter array (uint64).
 enum Counter {

@@ -128,7 +128,7 @@ extern "C" int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int
     if (s > 0 && snapshot_times[s] < snapshot_times[s - 1])
       return noalloc_fail(SSA_EINVAL, "snapshot times must be ascending");
   }
-  if (precision < 0 || precision > 3) return noalloc_fail(SSA_EINVAL, "unknown precision mode");
+  if (precision < 0 || precision > 4) return noalloc_fail(SSA_EINVAL, "unknown precision mode");
   if (thin_bits < 1 || thin_bits > 64) return noalloc_fail(SSA_EINVAL, "thin_bits must be in [1, 64]");
   double kmax = 0.0;
   for (int r = 0; r < 3; ++r) {

@@ -85,6 +85,10 @@ struct ssa_ctx {
   int n_snap = 0;
   unsigned long long counters[kCounters] = {0};
   int sm_count = 0;
+  // batch: the K buckets run concurrently on side streams forked from `stream`
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -199,7 +203,7 @@ int check_rates(const double* k, std::string* why) {
 }
 
 int check_options(const ssa_options& o, std::string* why) {
-  if (o.precision < 0 || o.precision > 3) return (*why = "unknown precision mode", SSA_EINVAL);
+  if (o.precision < 0 || o.precision > 4) return (*why = "unknown precision mode", SSA_EINVAL);
   if (o.engine < 0 || o.engine > 1) return (*why = "unknown engine", SSA_EINVAL);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
   if (o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
@@ -438,6 +442,11 @@ int launch_runs(ssa_ctx* c) {
   fl.ens_table = c->d_ens;
   fl.item_ens = c->d_item_ens;
   fl.item_group = c->d_item_group;
+  // one launch per K bucket (largest K first), spread over the side streams so that the
+  // buckets run concurrently; the caller's stream waits for all of them
+  if ((e = cudaEventRecord(c->fork, c->stream)) != cudaSuccess) return cuda_fail(c, e, "fork event");
+  for (cudaStream_t s : c->side)
+    if ((e = cudaStreamWaitEvent(s, c->fork, 0)) != cudaSuccess) return cuda_fail(c, e, "fork wait");
   for (size_t r = 0; r < c->ranges.size(); ++r) {
     const int K = std::max(1, c->ranges[r].first);
     fl.item_begin = c->ranges[r].second.first;
@@ -449,8 +458,13 @@ int launch_runs(ssa_ctx* c) {
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (fl.item_end - fl.item_begin + block - 1) / block;
     const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
-    if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, 0, (void*)c->stream)) != cudaSuccess)
+    cudaStream_t s = c->side[r % c->side.size()];
+    if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, 0, (void*)s)) != cudaSuccess)
       return cuda_fail(c, e, "bit-sliced kernel launch");
+  }
+  for (size_t i = 0; i < c->side.size(); ++i) {
+    if ((e = cudaEventRecord(c->side_done[i], c->side[i])) != cudaSuccess) return cuda_fail(c, e, "join event");
+    if ((e = cudaStreamWaitEvent(c->stream, c->side_done[i], 0)) != cudaSuccess) return cuda_fail(c, e, "join wait");
   }
   return SSA_OK;
 }
@@ -608,9 +622,31 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
   }
   DeviceGuard guard(c->opt.device);
   if ((st = setup_device(c)) != SSA_OK) return bail(st, c->err);
+  {
+    const size_t n_side = std::min<size_t>(8, std::max<size_t>(1, c->ranges.size()));
+    cudaError_t e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    for (size_t i = 0; e == cudaSuccess && i < n_side; ++i) {
+      cudaStream_t s = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e == cudaSuccess) c->side.push_back(s);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) c->side_done.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+      std::string msg = std::string("side streams: ") + cudaGetErrorString(e);
+      for (auto s : c->side) cudaStreamDestroy(s);
+      for (auto ev : c->side_done) cudaEventDestroy(ev);
+      if (c->fork) cudaEventDestroy(c->fork);
+      return bail(SSA_ECUDA, msg);
+    }
+  }
   if ((st = allocate_common(c, {})) != SSA_OK) {
     std::string msg = c->err;
     dev_free_all(c);
+    for (auto s : c->side) cudaStreamDestroy(s);
+    for (auto ev : c->side_done) cudaEventDestroy(ev);
+    if (c->fork) cudaEventDestroy(c->fork);
     return bail(st, msg);
   }
   *out = c;
@@ -719,6 +755,9 @@ int ssa_destroy(ssa_ctx* c) {
   {
     DeviceGuard guard(c->device);
     if (c->stream || !c->bufs.empty()) cudaStreamSynchronize(c->stream);
+    for (auto s : c->side) cudaStreamDestroy(s);
+    for (auto ev : c->side_done) cudaEventDestroy(ev);
+    if (c->fork) cudaEventDestroy(c->fork);
     dev_free_all(c);
   }
   delete c;

@@ -153,15 +153,18 @@ __global__ void __launch_bounds__(256) thread_per_run_kernel(const __grid_consta
             cf_new = (s - t_f) - y;
             tf_new = s;
             t_new = (double)s;
+          } else if (p.precision == kP32Plain) {
+            tf_new = t_f + tau;
+            t_new = (double)tf_new;
           } else {
             t_new = t + (double)tau;
           }
         }
-        while (snap < n_snap && (p.precision == kP32Kahan ? tf_new > p.thr[snap].t_f : t_new > p.thr[snap].t)) {
+        while (snap < n_snap && (p.precision == kP32Kahan || p.precision == kP32Plain ? tf_new > p.thr[snap].t_f : t_new > p.thr[snap].t)) {
           capture(snap);
           ++snap;
         }
-        if (p.precision == kP32Kahan ? tf_new > p.thr[n_snap].t_f : t_new > p.thr[n_snap].t) {
+        if (p.precision == kP32Kahan || p.precision == kP32Plain ? tf_new > p.thr[n_snap].t_f : t_new > p.thr[n_snap].t) {
           done = true;
         } else {
           t = t_new;
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(256) thread_per_run_kernel(const __grid_consta
           if (real_total() == 0) {
             absorbed = true;
             done = true;
-            t_abs = p.precision == kP32Kahan ? (double)t_f : t;
+            t_abs = (p.precision == kP32Kahan || p.precision == kP32Plain) ? (double)t_f : t;
           }
         }
       }

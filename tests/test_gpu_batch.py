@@ -1,0 +1,88 @@
+"""Batched ensembles (one context, many N_tot / rates / seeds) against the oracle and
+against one context per ensemble."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2412_16613_gb300 as pkg
+from paper_2412_16613_gb300 import workloads
+from tests._gpu import assert_parity
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def device():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    pkg.use_torch_allocator()
+
+
+def run_batch(ens, t_end, snaps, **opt):
+    import torch
+    o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), keep_snap_counts=1 if len(snaps) else 0,
+                                **opt)
+    ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, ens["init"], ens["rates"], ens["runs"],
+                               ens["seeds"], o)
+    try:
+        pkg.ssa_run(ctx, t_end, snaps)
+        out = pkg.fetch_all(ctx, snapshots=bool(len(snaps)))
+    finally:
+        pkg.ssa_destroy(ctx)
+    n_total = int(ens["runs"].sum())
+    if len(snaps):
+        out["snap_counts"] = out["snap_counts"].reshape(len(snaps), n_total, 3)
+    out["ee_hist"] = out["ee_hist"].reshape(len(ens["runs"]), len(snaps), 65)
+    return out
+
+
+def test_batch_matches_oracle_per_ensemble():
+    ens = workloads.batch_ensembles(n_ens=14, runs=70, n_min=6, n_max=2500, seed=11)
+    ens["runs"][3] = 33     # ragged groups
+    ens["runs"][5] = 1
+    ens["rates"][2] = [1.0, 1.0, 1.0]  # one unit-rate ensemble (no thinning)
+    snaps = [0.001, 0.01, 0.1]
+    t_end = 50.0
+    g = run_batch(ens, t_end, snaps)
+    off = np.concatenate([[0], np.cumsum(ens["runs"])])
+    for e in range(len(ens["runs"])):
+        sl = slice(off[e], off[e + 1])
+        r = oracle.run(oracle.frank(*ens["rates"][e]), ens["init"][e], int(ens["runs"][e]),
+                       seed=int(ens["seeds"][e]), t_end=t_end, snap_times=snaps, threads=THREADS)
+        ge = {"final_counts": g["final_counts"][sl], "outcome": g["outcome"][sl], "t_abs": g["t_abs"][sl],
+              "snap_counts": g["snap_counts"][:, sl]}
+        ok = assert_parity(ge, r, min_ok=0.9)
+        if ok.all():
+            assert np.array_equal(g["ee_hist"][e], oracle.ee_histogram(r["snap_counts"])), e
+        tally = [np.sum(r["outcome"] == k) for k in range(3)] + [np.sum(r["outcome"] < 0)]
+        assert list(g["ens_absorbed"][e]) == tally, e
+
+
+@pytest.mark.parametrize("precision", [pkg.SSA_P64, pkg.SSA_P32_KAHAN])
+def test_batch_equals_separate_contexts(precision):
+    import torch
+    ens = workloads.batch_ensembles(n_ens=6, runs=100, n_min=20, n_max=5000, seed=3)
+    snaps = [0.001, 0.01]
+    g = run_batch(ens, 1.0, snaps, precision=precision)
+    off = np.concatenate([[0], np.cumsum(ens["runs"])])
+    for e in range(6):
+        o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), precision=precision)
+        ctx = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, ens["rates"][e], ens["init"][e],
+                             int(ens["runs"][e]), int(ens["seeds"][e]), o)
+        try:
+            pkg.ssa_run(ctx, 1.0, snaps)
+            one = pkg.fetch_all(ctx)
+        finally:
+            pkg.ssa_destroy(ctx)
+        sl = slice(off[e], off[e + 1])
+        assert np.array_equal(g["final_counts"][sl], one["final_counts"])
+        assert np.array_equal(g["outcome"][sl], one["outcome"])
+        assert np.array_equal(g["t_abs"][sl], one["t_abs"])
+        assert np.array_equal(g["ee_hist"][e], one["ee_hist"].reshape(len(snaps), 65))
