@@ -282,7 +282,11 @@ int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index, const
       out->status = ORC_ETIMEOUT;
       break;
     }
-    /* (1) the integer n, uniform in [0, lambda_int), by per-lane rejection */
+    /* (1) the integer n, uniform in [0, lambda_int), by per-lane rejection.  A rejected
+     * draw (draw >= lambda_int) redraws its bits from position p up, p being the highest
+     * bit where it differs from lambda_int (all bits when it equals lambda_int), and keeps
+     * the bits below p: they are uniform and independent of the rejection, so the new
+     * draw is again uniform on [0, 2^K) and the accepted one uniform on [0, lambda_int). */
     uint64_t draw = 0;
     for (int i = 0; i < K; i++)
       draw |= (uint64_t)lane_bit(word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)i), lane) << i;
@@ -290,8 +294,9 @@ int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index, const
     while (draw >= d->lambda_int) {
       attempt++;
       if (attempt >= 64) return out->status = ORC_ERANGE;
-      draw = 0;
-      for (int i = 0; i < K; i++)
+      int from = draw == d->lambda_int ? 0 : bit_length(draw ^ d->lambda_int) - 1;
+      draw &= ((uint64_t)1 << from) - 1;
+      for (int i = from; i < K; i++)
         draw |= (uint64_t)lane_bit(word_at(&ws, group, (uint64_t)step, attempt, 0, (uint32_t)i),
                                    lane) << i;
     }

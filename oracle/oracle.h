@@ -16,8 +16,10 @@
  *   word k of the (g, step s, attempt a, tag) stream is element k % 4 of
  *     Philox4x32-10(key = (seed lo, seed hi),
  *                   ctr = (g, s lo32, (s hi16) | a << 16 | tag << 24, k / 4));
- *   n   = sum_{i<K} bit_l(w_i) 2^i, redrawn from attempt a+1 while n >= Lambda_int
- *         (a uniform integer in [0, Lambda_int), Sec. 3 step 5(i) and step a);
+ *   n   = sum_{i<K} bit_l(w_i) 2^i; while n >= Lambda_int, its bits from p up (p the
+ *         highest bit where n and Lambda_int differ, 0 if equal) are replaced by the
+ *         same bits of attempt a+1 (a uniform integer in [0, Lambda_int), Sec. 3 step
+ *         5(i) and step a);
  *   tau = -log(u) / Lambda from the whole words w_K, w_{K+1} of attempt 0
  *         (Eq. equation-tau, with the uniformisation rate of Eq. equation-z):
  *         fp64 u = (x + 1) 2^-53 with x = w_{K+1} << 21 | w_K >> 11; the fp32

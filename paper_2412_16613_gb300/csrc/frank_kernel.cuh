@@ -383,6 +383,10 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   uint32_t lt2 = bs::less_than(n, s.S2);
   uint32_t lt3 = bs::less_than(n, s.S3);
   if (need) {
+    // A lane with n >= lambda_int replaces its planes from p up, p the highest plane where
+    // n and lambda_int differ (every plane when they are equal), with the same planes of the
+    // next attempt; the planes below p are independent of the rejection and stay.  Planes are
+    // visited from the top: `above` collects the lanes that differ above the current plane.
     for (uint32_t attempt = 1u; need; ++attempt) {
       if (attempt >= 64u) {
         errors |= kErrRedraw;
@@ -390,17 +394,28 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
         return;
       }
       ++s.redraws;
-      uint32_t wr[4 * NCR];
+      uint32_t above = 0u;
 #pragma unroll
-      for (int c = 0; c < NCR; ++c) {
-        const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, attempt, 0u, (uint32_t)c), key);
-        wr[4 * c + 0] = r.x;
-        wr[4 * c + 1] = r.y;
-        wr[4 * c + 2] = r.z;
-        wr[4 * c + 3] = r.w;
+      for (int c = NCR - 1; c >= 0; --c) {
+        uint32_t m[4];
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+          const int i = 4 * c + j;
+          if (i < K) {
+            m[j] = need & ~above;
+            above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
+          } else {
+            m[j] = 0u;
+          }
+        }
+        if (m[0] | m[1] | m[2] | m[3]) {  // some lane replaces a plane of this call
+          const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, attempt, 0u, (uint32_t)c), key);
+          const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (4 * c + j < K) n[4 * c + j] = (n[4 * c + j] & ~m[j]) | (wv[j] & m[j]);
+        }
       }
-#pragma unroll
-      for (int i = 0; i < K; ++i) n[i] = (n[i] & ~need) | (wr[i] & need);
       need &= ~bs::less_than_const(n, e.lambda_int);
     }
     lt1 = bs::less_than(n, s.S1);

@@ -179,6 +179,26 @@ def test_first_step_probabilities(orc, rates):
     assert pval > 1e-4, (obs, np.array(p) * n)
 
 
+@pytest.mark.parametrize("init", [(1, 1, 10), (6, 0, 6), (2, 9, 1), (11, 1, 0), (4, 4, 4)])
+def test_first_step_probabilities_under_heavy_rejection(orc, init):
+    """N_tot = 12: lambda_int = 66 of 2^7 = 128 draws, so about half the draws are redrawn;
+    the first reaction must still have probability h_r / 66 exactly, for states whose
+    reactions cover different parts of [0, 66)."""
+    n = 150_000
+    r = orc.run(orc.frank(), init, n, seed=19, step_budget=1, check=False)
+    delta = r["final_counts"] - np.array(init)
+    fired = np.full(n, 3)
+    for k, nu in enumerate(([1, 0, -1], [0, 1, -1], [-1, -1, 2])):
+        fired[(delta == nu).all(1)] = k
+    h = frank_h(*init)
+    p = np.array(h + [66 - sum(h)], dtype=float) / 66
+    obs = np.bincount(fired, minlength=4)
+    keep = p > 0
+    assert np.all(obs[~keep] == 0)
+    assert stats.chisquare(obs[keep], p[keep] * n).pvalue > 1e-4, (obs, p * n)
+    assert r["redraws"].sum() > 0.5 * n
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_waiting_time_exponential(orc, precision):
     """Eq. equation-tau: tau ~ Exp(Lambda), one clock per 32-lane group."""
