@@ -242,8 +242,10 @@ def main():
     pkg.build()
     pkg.use_torch_allocator()
     stream = torch.cuda.current_stream()
+    from paper_2412_16613_gb300 import sharding
+    first_run = sharding.weak_shard(RUNS_PER_GPU, rank)[0] if WORKLOAD != "c3" else 0
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
-                                  block_size=args.block, first_run=rank * RUNS_PER_GPU)
+                                  block_size=args.block, first_run=first_run)
     if WORKLOAD == "c3":
         opt.first_run = 0
         ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],
@@ -362,7 +364,7 @@ def main():
     # ---- the one-thread-per-run GPU baseline on the same workload and precision
     if not args.no_baselines and WORKLOAD != "c3":
         o7 = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
-                                     engine=pkg.SSA_ENGINE_THREAD_PER_RUN, first_run=rank * RUNS_PER_GPU)
+                                     engine=pkg.SSA_ENGINE_THREAD_PER_RUN, first_run=first_run)
         c7 = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
                             RUNS_PER_GPU, SEED, o7)
         pkg.ssa_run(c7, T_END, SNAPS)

@@ -66,20 +66,21 @@ __global__ void bitslice_kernel(int op, const long long* x, const long long* y, 
 }
 
 __global__ void alu_kernel(uint32_t seed, int iters, uint32_t* sink) {
-  // 8 independent chains per thread; each LOP3 mixes the chain's value with two
-  // loop-invariant registers, so the chains never wait on one another
-  uint32_t a[8], b[8];
+  // 8 chains per thread; each step is a majority of the chain, its neighbour's previous value
+  // and a constant, so no step can be folded into another and a round holds 8 independent
+  // 3-input logic operations (one LOP3 each)
+  uint32_t a[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    a[j] = threadIdx.x * (j + 1) + seed;
-    b[j] = (seed + j) * 0x9E3779B9u ^ blockIdx.x;
-  }
-  const uint32_t c0 = seed ^ 0x85EBCA6Bu, c1 = seed * 0xC2B2AE35u;
+  for (int j = 0; j < 8; ++j) a[j] = threadIdx.x * (j + 1) + seed * 0x9E3779B9u + blockIdx.x;
+  const uint32_t k0 = seed ^ 0x85EBCA6Bu, k1 = seed * 0xC2B2AE35u;
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
+      uint32_t b[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = bs::maj(a[j], b[j], (r & 1) ? c1 : c0);
+      for (int j = 0; j < 8; ++j) b[j] = bs::maj(a[j], a[(j + 1) & 7], (r & 1) ? k1 : k0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = b[j];
     }
   }
   uint32_t s = 0;
