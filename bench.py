@@ -47,6 +47,10 @@ SNAPS = [T_END * 10.0 ** (4.0 * (s - (N_SNAP - 1)) / (N_SNAP - 1)) for s in rang
 L2_BYTES = 129 * 2**20
 SMS = 152
 MAX_SM_MHZ = 2070.0
+# DRAM bytes (read + write) of one launch of the bit-sliced kernel on the default workload: the
+# quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (580.6 KB) scaled by the
+# number of runs.  Set to None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_LAUNCH = 4 * 580_608
 
 
 def algorithmic_ops_per_group_step(K: int, b: int) -> int:
@@ -311,7 +315,9 @@ def main():
     except Exception:
         pass
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": TRAFFIC_BYTES_PER_LAUNCH if (WORKLOAD == "c2" and RUNS_PER_GPU == 1 << 20
+                                                        and PRECISION == 0) else None,
                 "ops_per_group_step": ops_unit, "group_steps_per_launch": gs_per_launch,
                 "peak_basis": f"{SMS} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {MAX_SM_MHZ:g} MHz",
                 "lop3_microbench_gops": micro}

@@ -78,7 +78,11 @@ __global__ void alu_kernel(uint32_t seed, int iters, uint32_t* sink) {
     for (int r = 0; r < 16; ++r) {
       uint32_t b[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = bs::maj(a[j], a[(j + 1) & 7], (r & 1) ? k1 : k0);
+      for (int j = 0; j < 8; ++j) {
+        // one LOP3 instruction with the majority truth table (0xE8)
+        asm volatile("lop3.b32 %0, %1, %2, %3, 0xE8;" : "=r"(b[j]) : "r"(a[j]), "r"(a[(j + 1) & 7]),
+                     "r"((r & 1) ? k1 : k0));
+      }
 #pragma unroll
       for (int j = 0; j < 8; ++j) a[j] = b[j];
     }
