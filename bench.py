@@ -50,7 +50,7 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) of one launch of the bit-sliced kernel on the default workload: the
 # quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (580.6 KB) scaled by the
 # number of runs.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 4 * 580_608
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def algorithmic_ops_per_group_step(K: int, b: int) -> int:

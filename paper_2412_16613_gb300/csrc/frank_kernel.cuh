@@ -93,11 +93,11 @@ __device__ __forceinline__ int ee_bin(int l, int d) {
 }
 
 // ---------------------------------------------------------------------------
-// The group clock.  PROD (SSA_P64): exp(-Lambda t) = m 2^E is kept as an fp64
-// mantissa m in [1, 2) and an integer exponent E; each step multiplies in the
-// step's uniform u (one fp64 multiply, the exponent renormalised with integer
-// ops), so t = -(ln m + E ln 2) / Lambda needs a logarithm only when a time is
-// written out.  Otherwise: the fp64 sum of -log(u) / Lambda (SSA_P64_LOGSUM), or
+// The group clock.  PROD (SSA_P64): exp(-Lambda t) = M 2^(E - 63) is kept as a
+// 64-bit fixed-point mantissa M in [2^63, 2^64) and an integer exponent E; each
+// step multiplies in the step's uniform u with integer instructions only (GB300's
+// fp64 rate is 1/64 of its fp32 rate), so t = -(ln M + (E - 63) ln 2) / Lambda needs
+// a logarithm only when a time is written out.  Otherwise: the fp64 sum of -log(u) / Lambda (SSA_P64_LOGSUM), or
 // fp32 -logf(u) / Lambda summed with Kahan compensation (SSA_P32_KAHAN), into an
 // fp64 accumulator (SSA_P32_D64ACC) or plainly in fp32 (SSA_P32_PLAIN).
 // ---------------------------------------------------------------------------
@@ -106,20 +106,20 @@ struct Clock;
 
 template <>
 struct Clock<true> {
-  double m;
+  unsigned long long M;  // exp(-Lambda t) = M 2^(E - 63), M in [2^63, 2^64)
   long long E;
-  long long th_E;       // exponent of the next time point to cross
-  const double* th_m;   // its mantissa, read only when the exponents tie
+  long long th_E;                 // exponent of the next time point to cross
+  const unsigned long long* th_M; // its mantissa, read only when the exponents tie
   __device__ __forceinline__ void reset() {
-    m = 1.0;
+    M = 1ull << 63;
     E = 0;
   }
   __device__ __forceinline__ void aim(const Threshold& h) {
     th_E = h.E;
-    th_m = &h.m;
+    th_M = &h.M;
   }
   __device__ __forceinline__ double time(const Ensemble& e, int) const {
-    return -(log(m) + (double)E * kLn2) / e.lambda;
+    return -(log((double)M) + (double)(E - 63) * kLn2) / e.lambda;
   }
 };
 
@@ -143,16 +143,23 @@ struct Clock<false> {
 };
 
 // Candidate clock after this step's event, from the step's waiting-time words w_K, w_{K+1}.
+// Product clock: u = v 2^-53 with v = x + 1 in [1, 2^53]; the 117-bit product M v is
+// renormalised to its top 64 bits in integer arithmetic (truncation: relative error below
+// 2^-63 per step, far under the fp64 rounding of the summed time it stands for).
 __device__ __forceinline__ bool clock_advance(const Clock<true>& c, Clock<true>& nx, uint32_t wk, uint32_t wk1,
                                               const Ensemble&, int) {
-  const unsigned long long x = ((unsigned long long)wk1 << 21) | (wk >> 11);
-  const double u = (double)(x + 1ull) * 0x1p-53;  // exact: (x + 1) 2^-53 in (0, 1]
-  const double mm = c.m * u;
-  const int hi = __double2hiint(mm), lo = __double2loint(mm);
+  const unsigned long long v = (((unsigned long long)wk1 << 21) | (wk >> 11)) + 1ull;
+  const unsigned long long lo = c.M * v, hi = __umul64hi(c.M, v);
   nx = c;
-  nx.E = c.E + (long long)(((hi >> 20) & 0x7FF) - 1023);
-  nx.m = __hiloint2double((hi & 0x800FFFFF) | 0x3FF00000, lo);
-  return nx.E < c.th_E || (nx.E == c.th_E && nx.m < *c.th_m);
+  if (hi) {
+    const int lz = __clzll((long long)hi);
+    nx.M = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+    nx.E = c.E + 11 - lz;
+  } else {  // v == 1: M v = M already has its top bit set
+    nx.M = lo;
+    nx.E = c.E - 53;
+  }
+  return nx.E < c.th_E || (nx.E == c.th_E && nx.M < *c.th_M);
 }
 
 __device__ __forceinline__ bool clock_advance(const Clock<false>& c, Clock<false>& nx, uint32_t wk, uint32_t wk1,
@@ -182,7 +189,7 @@ __device__ __forceinline__ bool clock_advance(const Clock<false>& c, Clock<false
 }
 
 __device__ __forceinline__ bool clock_crosses(const Clock<true>& nx) {
-  return nx.E < nx.th_E || (nx.E == nx.th_E && nx.m < *nx.th_m);
+  return nx.E < nx.th_E || (nx.E == nx.th_E && nx.M < *nx.th_M);
 }
 __device__ __forceinline__ bool clock_crosses(const Clock<false>& nx, int precision) {
   return (precision == kP32Kahan || precision == kP32Plain) ? nx.t_f > nx.th_f : nx.t > nx.th_t;
@@ -365,20 +372,28 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   }
   // (1) the random words of attempt 0
   uint32_t w[4 * NC0];
-#pragma unroll
-  for (int c = 0; c < NC0; ++c) {
-    const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, (uint32_t)c), key);
-    w[4 * c + 0] = r.x;
-    w[4 * c + 1] = r.y;
-    w[4 * c + 2] = r.z;
-    w[4 * c + 3] = r.w;
-  }
+  philox4x32_10_block<NC0>(w, stream_counter(s.sgroup, s.step, 0u, 0u, 0u), 0u, key);
   uint32_t n[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) n[i] = w[i];
   // the rejection test and the three comparators are independent borrow chains: run them
   // together, and redo the comparators only in the rare step where a lane redraws
-  uint32_t need = ~bs::less_than_const(n, e.lambda_int) & s.live;
+  // n >= lambda_int needs every plane of lambda_int's leading run of ones set in n: test that
+  // first (a shallow AND tree), and run the full comparison only when some lane passes
+  uint32_t need = 0u;
+  {
+    uint32_t a[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) a[i] = n[i] | (((e.top_ones >> i) & 1u) ? 0u : 0xFFFFFFFFu);
+#pragma unroll
+    for (int width = K; width > 1; width = (width + 2) / 3) {
+#pragma unroll
+      for (int j = 0; j < (width + 2) / 3; ++j)
+        a[j] = a[3 * j] & (3 * j + 1 < width ? a[3 * j + 1] : 0xFFFFFFFFu) &
+               (3 * j + 2 < width ? a[3 * j + 2] : 0xFFFFFFFFu);
+    }
+    if (a[0] & s.live) need = ~bs::less_than_const(n, e.lambda_int) & s.live;
+  }
   uint32_t lt1 = bs::less_than(n, s.S1);
   uint32_t lt2 = bs::less_than(n, s.S2);
   uint32_t lt3 = bs::less_than(n, s.S3);

@@ -39,10 +39,10 @@ enum ErrorFlag : uint32_t {
 // Crossing threshold for one time point t of one ensemble, in the forms each
 // clock compares against.
 struct Threshold {
-  double t;        // the time itself (fp64 sum clocks)
-  double m;        // exp(-Lambda t) = m 2^E with m in [1, 2) (product clock)
+  double t;              // the time itself (fp64 sum clocks)
+  unsigned long long M;  // exp(-Lambda t) = M 2^(E - 63), M in [2^63, 2^64) (product clock)
   long long E;
-  float t_f;       // the largest float <= t (fp32 Kahan clock: f > t_f <=> (double)f > t)
+  float t_f;             // the largest float <= t (fp32 Kahan clock: f > t_f <=> (double)f > t)
   int pad;
 };
 
@@ -64,7 +64,8 @@ struct Ensemble {
   unsigned int active;       // bit r: k_r > 0
   int thin;                  // any reaction with k_r < k_max
   int thin_bits;             // q
-  int pad;
+  unsigned int top_ones;     // planes of the leading run of ones of lambda_int (bit i = plane i):
+                             // n >= lambda_int needs all of them set (0: no pre-check)
 };
 
 // One launch of the bit-sliced kernel for one K.

@@ -87,7 +87,7 @@ Threshold threshold_of(double t, double lambda) {
   h.t_f = f;
   if (std::isinf(t) || !(lambda > 0.0)) {
     h.E = LLONG_MIN;
-    h.m = 1.0;
+    h.M = 1ull << 63;
     return h;
   }
   const double theta = -lambda * t;
@@ -102,7 +102,7 @@ Threshold threshold_of(double t, double lambda) {
     --E;
   }
   h.E = E;
-  h.m = m;
+  h.M = (unsigned long long)std::ldexp(m, 63);  // m in [1, 2): exact
   return h;
 }
 
@@ -155,6 +155,7 @@ extern "C" int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int
   const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
   en.lambda_int = (unsigned int)lam;
   en.K = bitlen64(lam);
+  for (int i = en.K - 1; i >= 0 && ((lam >> i) & 1ull); --i) en.top_ones |= 1u << i;
   en.n_tot = (int)n_tot;
   en.lambda = kmax * (double)lam;
   en.inv_lambda_f = (float)(1.0 / en.lambda);

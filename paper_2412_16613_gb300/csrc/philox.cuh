@@ -31,6 +31,45 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, PhiloxKey key) {
   return x;
 }
 
+// Calls call0 .. call0 + NC - 1 of one stream (counters that differ only in the last word),
+// rounds outermost so that the NC independent chains are interleaved in program order.
+template <int NC>
+__device__ __forceinline__ void philox4x32_10_block(uint32_t (&w)[4 * NC], uint4 ctr, uint32_t call0,
+                                                    PhiloxKey key) {
+  uint32_t x0[NC], x1[NC], x2[NC], x3[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    x0[c] = ctr.x;
+    x1[c] = ctr.y;
+    x2[c] = ctr.z;
+    x3[c] = call0 + (uint32_t)c;
+  }
+  uint32_t k0 = key.lo, k1 = key.hi;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const unsigned long long wide_a = (unsigned long long)x0[c] * 0xD2511F53ull;
+      const unsigned long long wide_b = (unsigned long long)x2[c] * 0xCD9E8D57ull;
+      const uint32_t n0 = (uint32_t)(wide_b >> 32) ^ x1[c] ^ k0;
+      const uint32_t n2 = (uint32_t)(wide_a >> 32) ^ x3[c] ^ k1;
+      x1[c] = (uint32_t)wide_b;
+      x3[c] = (uint32_t)wide_a;
+      x0[c] = n0;
+      x2[c] = n2;
+    }
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    w[4 * c + 0] = x0[c];
+    w[4 * c + 1] = x1[c];
+    w[4 * c + 2] = x2[c];
+    w[4 * c + 3] = x3[c];
+  }
+}
+
 // Counter of call `call` of the (group, step, attempt, tag) stream:
 // (group, step lo 32, step hi 16 | attempt << 16 | tag << 24, call).
 __device__ __forceinline__ uint4 stream_counter(uint32_t group, unsigned long long step,

@@ -227,6 +227,7 @@ Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], in
   const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
   e.lambda_int = (unsigned int)lam;
   e.K = bit_len(lam);
+  for (int i = e.K - 1; i >= 0 && ((lam >> i) & 1ull); --i) e.top_ones |= 1u << i;
   const double kmax = std::max(k[0], std::max(k[1], k[2]));
   e.lambda = kmax * (double)lam;
   e.inv_lambda_f = (float)(1.0 / e.lambda);
@@ -255,7 +256,7 @@ Threshold make_threshold(double t, double lambda) {
   h.t_f = f;
   if (std::isinf(t) || !(lambda > 0.0)) {
     h.E = LLONG_MIN;
-    h.m = 1.0;
+    h.M = 1ull << 63;
     return h;
   }
   const double theta = -lambda * t;  // ln exp(-lambda t)
@@ -270,7 +271,7 @@ Threshold make_threshold(double t, double lambda) {
     --E;
   }
   h.E = E;
-  h.m = m;
+  h.M = (unsigned long long)std::ldexp(m, 63);  // m in [1, 2): exact
   return h;
 }
 
