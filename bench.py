@@ -212,6 +212,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--no-baselines", action="store_true", help="skip the K7 and CPU legs")
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--layout", type=int, default=0,
+                    help="0 auto, 1 one thread per group of 32 runs, 2 three warps per 32 groups")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--runs", type=int, default=0,
                     help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
@@ -249,7 +251,7 @@ def main():
     from paper_2412_16613_gb300 import sharding
     first_run = sharding.weak_shard(RUNS_PER_GPU, rank)[0] if WORKLOAD != "c3" else 0
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
-                                  block_size=args.block, first_run=first_run)
+                                  block_size=args.block, first_run=first_run, layout=args.layout)
     if WORKLOAD == "c3":
         opt.first_run = 0
         ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],
@@ -332,7 +334,8 @@ def main():
               "reactions_per_step": reactions / args.steps, "wall_s": wall,
               "group_steps_per_step": group_steps / args.steps, "max_group_steps": max_group_steps,
               "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
-              "hist_checksum": float(htot.sum().item())}
+              "hist_checksum": float(htot.sum().item()),
+              "layout": {0: "auto", 1: "thread", 2: "warps"}[args.layout]}
 
     # ---- end to end through the C ABI with host buffers (create from host arrays, run, read every
     # per-run output into pinned host memory, destroy), rank-local

@@ -58,8 +58,8 @@ typedef enum {
 /* Precision of the waiting-time clock (the integer dynamics are exact in every mode). */
 enum {
   SSA_P64 = 0,        /* fp64: u = (x + 1) 2^-53 from 53 random bits; the clock keeps
-                         exp(-Lambda t) = prod u as an fp64 mantissa and an integer
-                         exponent, so no logarithm is taken per step */
+                         exp(-Lambda t) = prod u as a 64-bit integer mantissa and an
+                         integer exponent, so no logarithm is taken per step */
   SSA_P32_KAHAN = 1,  /* fp32: u from the top 24 of those bits, tau = -logf(u) / Lambda,
                          Kahan-compensated fp32 time sum */
   SSA_P32_D64ACC = 2, /* fp32 tau as above, fp64 time accumulator */
@@ -77,11 +77,22 @@ enum {
                                    without ghosts) and its own per-run Philox stream */
 };
 
+/* How the bit-sliced engine maps a group of 32 runs onto the GPU. */
+enum {
+  SSA_LAYOUT_AUTO = 0,   /* chosen by the library */
+  SSA_LAYOUT_THREAD = 1, /* one thread keeps a group's whole state (S_1..S_3 and every
+                            linear form) and runs its steps alone */
+  SSA_LAYOUT_WARPS = 2   /* three warps of a 96-thread block serve 32 groups: warp r keeps
+                            S_{r+1} and the forms of its increments, the comparisons
+                            [n < S_r] and the updates of the three S_r run side by side
+                            (same streams and results as SSA_LAYOUT_THREAD) */
+};
+
 typedef struct {
   int32_t precision;         /* SSA_P64 (default) | SSA_P32_KAHAN | SSA_P32_D64ACC | SSA_P64_LOGSUM |
                                 SSA_P32_PLAIN */
   int32_t engine;            /* SSA_ENGINE_BITSLICED (default) | SSA_ENGINE_THREAD_PER_RUN */
-  int32_t block_size;        /* threads per block, 0 = chosen from occupancy */
+  int32_t block_size;        /* threads per block, 0 = default (SSA_LAYOUT_WARPS always uses 96) */
   int32_t blocks_per_sm;     /* resident blocks per SM to launch, 0 = occupancy limit */
   int32_t thin_bits;         /* q in [1, 64], bits of the thinning threshold (default 32) */
   int32_t keep_snap_counts;  /* 1: keep per-run counts at each snapshot (SSA_FIELD_SNAP_COUNTS) */
@@ -91,7 +102,8 @@ typedef struct {
                                 ensemble with results identical to one context */
   void* cuda_stream;         /* cudaStream_t to use; NULL = the legacy default stream */
   int32_t device;            /* CUDA device ordinal, -1 = the current device */
-  int32_t reserved[7];
+  int32_t layout;            /* SSA_LAYOUT_AUTO (default) | SSA_LAYOUT_THREAD | SSA_LAYOUT_WARPS */
+  int32_t reserved[6];
 } ssa_options;
 
 /* Fields for ssa_fetch.  n_runs = the context's total number of runs (for a batch,
@@ -104,7 +116,8 @@ enum {
   SSA_FIELD_ABSORB_OUTCOME = 2, /* int8[n_runs]: -1 not absorbed, else the index of the one
                                    species left (-2: absorbed with several species left) */
   SSA_FIELD_EE_HIST = 3,        /* uint64[n_ens][n_snap][65]: enantiomeric-excess histogram of
-                                   (L, D) = (species chiral[0], chiral[1]) at each snapshot:
+                                   (L, D) at each snapshot, L the species X of reaction 0
+                                   (A + X -> 2X) and D the species Y of reaction 1 (A + Y -> 2Y):
                                    bin min(63, floor(64 L / (L + D))), bin 64 = L + D == 0 */
   SSA_FIELD_SNAP_COUNTS = 4,    /* int32[n_snap][n_runs][S] (needs keep_snap_counts = 1) */
   SSA_FIELD_COUNTERS = 5,       /* uint64[10]: group steps, lane steps of live runs, real

@@ -11,7 +11,10 @@ namespace bitssa {
 #define BITSSA_DECLARE(k)                                                                      \
   int frank_launch_k##k(const FrankLaunch&, int, int, int, void*);                             \
   int frank_occupancy_k##k(int, int, int, int*);                                               \
-  int frank_regs_k##k(int);
+  int frank_regs_k##k(int);                                                                    \
+  int frank_trio_launch_k##k(const FrankLaunch&, int, int, void*);                             \
+  int frank_trio_occupancy_k##k(int, int, int*);                                               \
+  int frank_trio_regs_k##k(int);
 BITSSA_FOR_EACH_K(BITSSA_DECLARE)
 
 FrankLauncher frank_launcher(int K) {
@@ -43,6 +46,42 @@ int frank_registers(int K, int variant) {
 #define BITSSA_CASE(k) \
   case k:              \
     return frank_regs_k##k(variant);
+    BITSSA_FOR_EACH_K(BITSSA_CASE)
+#undef BITSSA_CASE
+    default:
+      return -1;
+  }
+}
+
+FrankTrioLauncher frank_trio_launcher(int K) {
+  switch (K) {
+#define BITSSA_CASE(k) \
+  case k:              \
+    return &frank_trio_launch_k##k;
+    BITSSA_FOR_EACH_K(BITSSA_CASE)
+#undef BITSSA_CASE
+    default:
+      return nullptr;
+  }
+}
+
+int frank_trio_max_active_blocks(int K, int variant, int smem, int* blocks) {
+  switch (K) {
+#define BITSSA_CASE(k) \
+  case k:              \
+    return frank_trio_occupancy_k##k(variant, smem, blocks);
+    BITSSA_FOR_EACH_K(BITSSA_CASE)
+#undef BITSSA_CASE
+    default:
+      return -1;
+  }
+}
+
+int frank_trio_registers(int K, int variant) {
+  switch (K) {
+#define BITSSA_CASE(k) \
+  case k:              \
+    return frank_trio_regs_k##k(variant);
     BITSSA_FOR_EACH_K(BITSSA_CASE)
 #undef BITSSA_CASE
     default:

@@ -384,7 +384,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   {
     uint32_t a[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i) a[i] = n[i] | (((e.top_ones >> i) & 1u) ? 0u : 0xFFFFFFFFu);
+    for (int i = 0; i < K; ++i) a[i] = n[i] | e.top_mask[i];
 #pragma unroll
     for (int width = K; width > 1; width = (width + 2) / 3) {
 #pragma unroll
@@ -402,6 +402,8 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
     // n and lambda_int differ (every plane when they are equal), with the same planes of the
     // next attempt; the planes below p are independent of the rejection and stay.  Planes are
     // visited from the top: `above` collects the lanes that differ above the current plane.
+    // Every call of the attempt is made: a warp takes this branch whenever one of its 1024
+    // runs is rejected, and the interleaved calls cost little more than one.
     for (uint32_t attempt = 1u; need; ++attempt) {
       if (attempt >= 64u) {
         errors |= kErrRedraw;
@@ -409,27 +411,14 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
         return;
       }
       ++s.redraws;
+      uint32_t wr[4 * NCR];  // all calls of the attempt at once: their chains interleave
+      philox4x32_10_block<NCR>(wr, stream_counter(s.sgroup, s.step, attempt, 0u, 0u), 0u, key);
       uint32_t above = 0u;
 #pragma unroll
-      for (int c = NCR - 1; c >= 0; --c) {
-        uint32_t m[4];
-#pragma unroll
-        for (int j = 3; j >= 0; --j) {
-          const int i = 4 * c + j;
-          if (i < K) {
-            m[j] = need & ~above;
-            above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
-          } else {
-            m[j] = 0u;
-          }
-        }
-        if (m[0] | m[1] | m[2] | m[3]) {  // some lane replaces a plane of this call
-          const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, attempt, 0u, (uint32_t)c), key);
-          const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (4 * c + j < K) n[4 * c + j] = (n[4 * c + j] & ~m[j]) | (wv[j] & m[j]);
-        }
+      for (int i = K - 1; i >= 0; --i) {
+        const uint32_t m = need & ~above;
+        above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
+        n[i] = (n[i] & ~m) | (wr[i] & m);
       }
       need &= ~bs::less_than_const(n, e.lambda_int);
     }

@@ -11,6 +11,7 @@ constexpr int kMaxSnap = 64;
 constexpr int kHistBins = 65;  // 64 enantiomeric-excess bins + one for L + D == 0
 constexpr int kCounters = 10;
 constexpr int kMaxK = 31;      // random / propensity planes: N_tot (N_tot - 1) / 2 < 2^31
+constexpr int kTrioBlock = 96; // threads of a block of the three-warp layout (32 groups)
 
 // Clock precision modes (same values as SSA_P64 ... in bitssa.h).
 enum Precision { kP64 = 0, kP32Kahan = 1, kP32D64Acc = 2, kP64LogSum = 3, kP32Plain = 4 };
@@ -66,7 +67,16 @@ struct Ensemble {
   int thin_bits;             // q
   unsigned int top_ones;     // planes of the leading run of ones of lambda_int (bit i = plane i):
                              // n >= lambda_int needs all of them set (0: no pre-check)
+  unsigned int top_mask[32]; // per plane: 0 on the run, ~0 elsewhere, so that the AND over planes
+                             // of (n_i | top_mask[i]) is the lanes that pass the pre-check
 };
+
+// Fills top_ones and top_mask from lambda_int and K.
+inline void set_precheck(Ensemble& e) {
+  e.top_ones = 0u;
+  for (int i = e.K - 1; i >= 0 && ((e.lambda_int >> i) & 1u); --i) e.top_ones |= 1u << i;
+  for (int i = 0; i < 32; ++i) e.top_mask[i] = ((e.top_ones >> i) & 1u) ? 0u : 0xFFFFFFFFu;
+}
 
 // One launch of the bit-sliced kernel for one K.
 struct FrankLaunch {
@@ -125,6 +135,11 @@ FrankLauncher frank_launcher(int K);
 // variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64)
 int frank_max_active_blocks(int K, int variant, int block, int smem, int* blocks);
 int frank_registers(int K, int variant);
+// The three-warp layout (block of kTrioBlock threads serving 32 groups).
+using FrankTrioLauncher = int (*)(const FrankLaunch&, int grid, int smem, void* stream);
+FrankTrioLauncher frank_trio_launcher(int K);
+int frank_trio_max_active_blocks(int K, int variant, int smem, int* blocks);
+int frank_trio_registers(int K, int variant);
 int thread_per_run_launch(const ThreadLaunch& p, int grid, int block, int smem, void* stream);
 // Sets the calling thread's message returned by ssa_last_error(NULL).
 void set_thread_error(const std::string& msg);

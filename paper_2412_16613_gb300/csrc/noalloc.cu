@@ -155,7 +155,7 @@ extern "C" int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int
   const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
   en.lambda_int = (unsigned int)lam;
   en.K = bitlen64(lam);
-  for (int i = en.K - 1; i >= 0 && ((lam >> i) & 1ull); --i) en.top_ones |= 1u << i;
+  set_precheck(en);
   en.n_tot = (int)n_tot;
   en.lambda = kmax * (double)lam;
   en.inv_lambda_f = (float)(1.0 / en.lambda);

@@ -31,18 +31,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, PhiloxKey key) {
   return x;
 }
 
-// Calls call0 .. call0 + NC - 1 of one stream (counters that differ only in the last word),
-// rounds outermost so that the NC independent chains are interleaved in program order.
+// Calls call0, call0 + stride, ... (NC of them) of one stream (counters that differ only in
+// the last word), rounds outermost so that the NC independent chains are interleaved in
+// program order.
 template <int NC>
 __device__ __forceinline__ void philox4x32_10_block(uint32_t (&w)[4 * NC], uint4 ctr, uint32_t call0,
-                                                    PhiloxKey key) {
+                                                    PhiloxKey key, uint32_t stride = 1u) {
   uint32_t x0[NC], x1[NC], x2[NC], x3[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     x0[c] = ctr.x;
     x1[c] = ctr.y;
     x2[c] = ctr.z;
-    x3[c] = call0 + (uint32_t)c;
+    x3[c] = call0 + stride * (uint32_t)c;
   }
   uint32_t k0 = key.lo, k1 = key.hi;
 #pragma unroll

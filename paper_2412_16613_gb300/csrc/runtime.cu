@@ -205,6 +205,7 @@ int check_rates(const double* k, std::string* why) {
 int check_options(const ssa_options& o, std::string* why) {
   if (o.precision < 0 || o.precision > 4) return (*why = "unknown precision mode", SSA_EINVAL);
   if (o.engine < 0 || o.engine > 1) return (*why = "unknown engine", SSA_EINVAL);
+  if (o.layout < SSA_LAYOUT_AUTO || o.layout > SSA_LAYOUT_WARPS) return (*why = "unknown layout", SSA_EINVAL);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
   if (o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
     return (*why = "block_size must be 0 or a multiple of 32 up to 256", SSA_EINVAL);
@@ -227,7 +228,7 @@ Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], in
   const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
   e.lambda_int = (unsigned int)lam;
   e.K = bit_len(lam);
-  for (int i = e.K - 1; i >= 0 && ((lam >> i) & 1ull); --i) e.top_ones |= 1u << i;
+  set_precheck(e);
   const double kmax = std::max(k[0], std::max(k[1], k[2]));
   e.lambda = kmax * (double)lam;
   e.inv_lambda_f = (float)(1.0 / e.lambda);
@@ -360,6 +361,18 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
   return SSA_OK;
 }
 
+// The layout of the bit-sliced engine.  The three-warp layout finishes a group's step sooner
+// (its work is split over three schedulers) but holds a group in three times as many threads;
+// SSA_LAYOUT_AUTO takes it while its blocks fit at most two to an SM, where a run's time is
+// its longest group's steps times the step latency, and the one-thread layout beyond that,
+// where the three-warp blocks would no longer all be resident (measured on GB300 at
+// N_tot = 1024: three warps ahead up to 2^18 runs, one thread ahead from 2^19).
+bool use_warps_layout(const ssa_options& o, long long groups, int sm_count) {
+  if (o.layout == SSA_LAYOUT_THREAD) return false;
+  if (o.layout == SSA_LAYOUT_WARPS) return true;
+  return groups <= 64ll * sm_count;
+}
+
 int launch_runs(ssa_ctx* c) {
   const int n_snap = c->n_snap;
   cudaError_t e;
@@ -419,6 +432,10 @@ int launch_runs(ssa_ctx* c) {
     return SSA_OK;
   }
 
+  long long all_groups = 0;
+  for (const Ensemble& en : c->ens) all_groups += (en.n_runs + 31) / 32;
+  const bool warps = use_warps_layout(c->opt, all_groups, c->sm_count);
+  const int clock_variant = c->opt.precision == SSA_P64 ? 2 : 0;
   if (!c->batch) {
     const Ensemble& en = c->ens[0];
     const long long groups = (en.n_runs + 31) / 32;
@@ -430,7 +447,17 @@ int launch_runs(ssa_ctx* c) {
     fl.queue = c->d_counters + kCounters;
     const int smem = n_snap * kHistBins * (int)sizeof(unsigned int);
     int occ = 0;
-    if (frank_max_active_blocks(K, c->opt.precision == SSA_P64 ? 2 : 0, block, smem, &occ) != 0 || occ < 1)
+    if (warps) {
+      if (frank_trio_max_active_blocks(K, clock_variant, smem, &occ) != 0 || occ < 1)
+        return fail(c, SSA_ECUDA, "occupancy query failed for the three-warp bit-sliced kernel");
+      const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+      const long long need = (groups + 31) / 32;
+      const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
+      if ((e = (cudaError_t)frank_trio_launcher(K)(fl, grid, smem, (void*)c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "three-warp bit-sliced kernel launch");
+      return SSA_OK;
+    }
+    if (frank_max_active_blocks(K, clock_variant, block, smem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (groups + block - 1) / block;
@@ -454,12 +481,22 @@ int launch_runs(ssa_ctx* c) {
     fl.item_end = c->ranges[r].second.second;
     fl.queue = c->d_counters + kCounters + 1 + r;
     int occ = 0;
-    if (frank_max_active_blocks(K, c->opt.precision == SSA_P64 ? 3 : 1, block, 0, &occ) != 0 || occ < 1)
+    cudaStream_t s = c->side[r % c->side.size()];
+    if (warps) {
+      if (frank_trio_max_active_blocks(K, clock_variant | 1, 0, &occ) != 0 || occ < 1)
+        return fail(c, SSA_ECUDA, "occupancy query failed for the three-warp bit-sliced kernel");
+      const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+      const long long need = (fl.item_end - fl.item_begin + 31) / 32;
+      const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
+      if ((e = (cudaError_t)frank_trio_launcher(K)(fl, grid, 0, (void*)s)) != cudaSuccess)
+        return cuda_fail(c, e, "three-warp bit-sliced kernel launch");
+      continue;
+    }
+    if (frank_max_active_blocks(K, clock_variant | 1, block, 0, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (fl.item_end - fl.item_begin + block - 1) / block;
     const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
-    cudaStream_t s = c->side[r % c->side.size()];
     if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, 0, (void*)s)) != cudaSuccess)
       return cuda_fail(c, e, "bit-sliced kernel launch");
   }

@@ -12,6 +12,8 @@ from tests._gpu import assert_parity
 
 pytestmark = pytest.mark.gpu
 THREADS = os.cpu_count() or 4
+LAYOUTS = pytest.mark.parametrize("layout", [pkg.SSA_LAYOUT_THREAD, pkg.SSA_LAYOUT_WARPS],
+                                  ids=["thread", "warps"])
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -43,14 +45,15 @@ def run_batch(ens, t_end, snaps, **opt):
     return out
 
 
-def test_batch_matches_oracle_per_ensemble():
+@LAYOUTS
+def test_batch_matches_oracle_per_ensemble(layout):
     ens = workloads.batch_ensembles(n_ens=14, runs=70, n_min=6, n_max=2500, seed=11)
     ens["runs"][3] = 33     # ragged groups
     ens["runs"][5] = 1
     ens["rates"][2] = [1.0, 1.0, 1.0]  # one unit-rate ensemble (no thinning)
     snaps = [0.001, 0.01, 0.1]
     t_end = 50.0
-    g = run_batch(ens, t_end, snaps)
+    g = run_batch(ens, t_end, snaps, layout=layout)
     off = np.concatenate([[0], np.cumsum(ens["runs"])])
     for e in range(len(ens["runs"])):
         sl = slice(off[e], off[e + 1])
@@ -66,14 +69,16 @@ def test_batch_matches_oracle_per_ensemble():
 
 
 @pytest.mark.parametrize("precision", [pkg.SSA_P64, pkg.SSA_P32_KAHAN])
-def test_batch_equals_separate_contexts(precision):
+@LAYOUTS
+def test_batch_equals_separate_contexts(precision, layout):
     import torch
     ens = workloads.batch_ensembles(n_ens=6, runs=100, n_min=20, n_max=5000, seed=3)
     snaps = [0.001, 0.01]
-    g = run_batch(ens, 1.0, snaps, precision=precision)
+    g = run_batch(ens, 1.0, snaps, precision=precision, layout=layout)
     off = np.concatenate([[0], np.cumsum(ens["runs"])])
     for e in range(6):
-        o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), precision=precision)
+        o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), precision=precision,
+                                    layout=pkg.SSA_LAYOUT_THREAD)
         ctx = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, ens["rates"][e], ens["init"][e],
                              int(ens["runs"][e]), int(ens["seeds"][e]), o)
         try:

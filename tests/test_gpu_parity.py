@@ -14,6 +14,9 @@ from tests._gpu import FRANK_P, FRANK_R, assert_parity, gpu_run, log_snapshots
 pytestmark = pytest.mark.gpu
 
 THREADS = os.cpu_count() or 4
+# the two layouts of the bit-sliced engine must produce the same runs
+LAYOUTS = pytest.mark.parametrize("layout", [pkg.SSA_LAYOUT_THREAD, pkg.SSA_LAYOUT_WARPS],
+                                  ids=["thread", "warps"])
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -74,10 +77,11 @@ def test_paper_fig1_sum():
 # --------------------------------------------------------------------------
 # Whole runs against the oracle
 # --------------------------------------------------------------------------
-def test_parity_n64_all_runs():
+@LAYOUTS
+def test_parity_n64_all_runs(layout):
     """N_tot = 64, (16, 16, 32), 64 runs in two groups, seed 0, t_end 10."""
     snaps = [0.01, 0.05, 0.1, 0.5, 10.0]
-    g = gpu_run((16, 16, 32), 64, seed=0, t_end=10.0, snaps=snaps)
+    g = gpu_run((16, 16, 32), 64, seed=0, t_end=10.0, snaps=snaps, layout=layout)
     r = oracle.run(oracle.frank(), (16, 16, 32), 64, seed=0, t_end=10.0, snap_times=snaps)
     ok = assert_parity(g, r)
     assert ok.all()
@@ -86,12 +90,13 @@ def test_parity_n64_all_runs():
     assert np.array_equal(g["ee_hist"], oracle.ee_histogram(r["snap_counts"]))
 
 
-def test_parity_n1024_subset_ragged():
+@LAYOUTS
+def test_parity_n1024_subset_ragged(layout):
     """N_tot = 1024, (256, 256, 512), 4113 runs (129 groups, ragged last group), 10 log-spaced
     snapshots, t_end = 50: every run, every snapshot, the histograms and the counters."""
     n = 4096 + 17
     snaps = log_snapshots(50.0, 10)
-    g = gpu_run((256, 256, 512), n, seed=0, t_end=50.0, snaps=snaps)
+    g = gpu_run((256, 256, 512), n, seed=0, t_end=50.0, snaps=snaps, layout=layout)
     r = oracle.run(oracle.frank(), (256, 256, 512), n, seed=0, t_end=50.0, snap_times=snaps,
                    threads=THREADS)
     ok = assert_parity(g, r)
@@ -130,60 +135,81 @@ def test_parity_n1024_full_size_sampled():
     (pkg.SSA_P32_KAHAN, oracle.P32_KAHAN, 2e-5, 1e-6),
     (pkg.SSA_P32_D64ACC, oracle.P32_D64ACC, 2e-5, 1e-6),
 ])
-def test_parity_precision_modes(mode, omode, rtol, tie):
+@LAYOUTS
+def test_parity_precision_modes(mode, omode, rtol, tie, layout):
     """fp32 clocks: CUDA's logf and the host's may differ by an ulp, so event times agree to
     ~1e-7 relative; runs with an event within `tie` of a snapshot are left out of the
     count comparison (several percent of runs at 10 snapshots)."""
     snaps = log_snapshots(50.0, 10)
     n = 1024 + 5
-    g = gpu_run((256, 256, 512), n, seed=3, t_end=50.0, snaps=snaps, precision=mode)
+    g = gpu_run((256, 256, 512), n, seed=3, t_end=50.0, snaps=snaps, precision=mode, layout=layout)
     r = oracle.run(oracle.frank(), (256, 256, 512), n, seed=3, t_end=50.0, snap_times=snaps,
                    precision=omode, threads=THREADS)
     assert_parity(g, r, rtol=rtol, tie=tie, min_ok=0.95)
 
 
 def test_results_do_not_depend_on_launch_shape():
+    """Block size and resident blocks of the one-thread layout, resident blocks of the
+    three-warp layout, and the layout itself: every output identical."""
     snaps = [0.005, 0.02]
-    base = gpu_run((256, 256, 512), 3000, seed=5, t_end=0.05, snaps=snaps)
-    for block, bpsm in [(32, 1), (128, 0), (256, 1)]:
-        g = gpu_run((256, 256, 512), 3000, seed=5, t_end=0.05, snaps=snaps, block_size=block,
-                    blocks_per_sm=bpsm)
+    base = gpu_run((256, 256, 512), 3000, seed=5, t_end=0.05, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD)
+    shapes = [dict(layout=pkg.SSA_LAYOUT_THREAD, block_size=b, blocks_per_sm=m) for b, m in
+              [(32, 1), (128, 0), (256, 1)]]
+    shapes += [dict(layout=pkg.SSA_LAYOUT_WARPS, blocks_per_sm=m) for m in (0, 1, 2)]
+    for shape in shapes:
+        g = gpu_run((256, 256, 512), 3000, seed=5, t_end=0.05, snaps=snaps, **shape)
         for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
-            assert np.array_equal(g[k], base[k]), k
-        assert g["counters"] == base["counters"]
+            assert np.array_equal(g[k], base[k]), (shape, k)
+        assert g["counters"] == base["counters"], shape
 
 
-def test_sharded_contexts_equal_one_context():
+@pytest.mark.parametrize("init,n,t_end,seed", [((256, 256, 512), 1 << 16, 50.0, 21),
+                                               ((3, 3, 6), 5000, 5.0, 22),
+                                               ((1000, 0, 3000), 3000, 1.0, 23)])
+def test_layouts_agree_bit_for_bit(init, n, t_end, seed):
+    """The same context on both layouts: counts, times, histograms and every counter equal."""
+    snaps = log_snapshots(t_end, 6)
+    a = gpu_run(init, n, seed=seed, t_end=t_end, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD)
+    b = gpu_run(init, n, seed=seed, t_end=t_end, snaps=snaps, layout=pkg.SSA_LAYOUT_WARPS)
+    for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["counters"] == b["counters"]
+
+
+@LAYOUTS
+def test_sharded_contexts_equal_one_context(layout):
     """Two contexts holding runs [0, 2048) and [2048, 4096) (first_run) give the runs of one
     context of 4096: the stream is keyed by the global group index."""
     snaps = [0.01, 0.03]
-    whole = gpu_run((256, 256, 512), 4096, seed=9, t_end=0.1, snaps=snaps)
-    a = gpu_run((256, 256, 512), 2048, seed=9, t_end=0.1, snaps=snaps, first_run=0)
-    b = gpu_run((256, 256, 512), 2048, seed=9, t_end=0.1, snaps=snaps, first_run=2048)
+    whole = gpu_run((256, 256, 512), 4096, seed=9, t_end=0.1, snaps=snaps, layout=layout)
+    a = gpu_run((256, 256, 512), 2048, seed=9, t_end=0.1, snaps=snaps, first_run=0, layout=layout)
+    b = gpu_run((256, 256, 512), 2048, seed=9, t_end=0.1, snaps=snaps, first_run=2048, layout=layout)
     for k in ("final_counts", "outcome", "t_abs"):
         assert np.array_equal(np.concatenate([a[k], b[k]]), whole[k]), k
     assert np.array_equal(a["ee_hist"] + b["ee_hist"], whole["ee_hist"])
 
 
-def test_parity_per_run_initial_states():
+@LAYOUTS
+def test_parity_per_run_initial_states(layout):
     """Independent multinomial initial states around the racemic point (Sec. 5, Fig. 4)."""
     rng = np.random.default_rng(77)
     n = 2000
     init = rng.multinomial(256, [0.25, 0.25, 0.5], size=n)
     snaps = [0.01, 0.05]
-    g = gpu_run(init, n, seed=4, t_end=1.0, snaps=snaps)
+    g = gpu_run(init, n, seed=4, t_end=1.0, snaps=snaps, layout=layout)
     r = oracle.run(oracle.frank(), init, seed=4, t_end=1.0, snap_times=snaps, threads=THREADS)
     assert_parity(g, r)
 
 
-def test_relabelled_species_give_the_same_runs():
+@LAYOUTS
+def test_relabelled_species_give_the_same_runs(layout):
     """Species order (A, L, D) with the reactions in Frank's order: the same trajectories,
     reported in the caller's species order."""
     reac = [[1, 1, 0], [1, 0, 1], [0, 1, 1]]
     prod = [[0, 2, 0], [0, 0, 2], [2, 0, 0]]
     snaps = [0.02]
-    base = gpu_run((16, 16, 32), 256, seed=6, t_end=1.0, snaps=snaps)
-    g = gpu_run((32, 16, 16), 256, seed=6, t_end=1.0, snaps=snaps, reac=reac, prod=prod)
+    base = gpu_run((16, 16, 32), 256, seed=6, t_end=1.0, snaps=snaps, layout=layout)
+    g = gpu_run((32, 16, 16), 256, seed=6, t_end=1.0, snaps=snaps, reac=reac, prod=prod, layout=layout)
     assert np.array_equal(g["final_counts"][:, [1, 2, 0]], base["final_counts"])
     assert np.array_equal(g["snap_counts"][:, :, [1, 2, 0]], base["snap_counts"])
     remap = np.array([-2, -1, 2, 0, 1])  # caller's outcome -2..2 (A=0, L=1, D=2) -> (L=0, D=1, A=2)
@@ -192,10 +218,11 @@ def test_relabelled_species_give_the_same_runs():
 
 @pytest.mark.parametrize("rates,q", [((1.0, 0.5, 0.25), 32), ((0.7, 2.0, 1.3), 64), ((0.0, 0.0, 1.0), 32),
                                      ((1.0, 1.0, 0.5), 5)])
-def test_parity_thinning(rates, q):
+@LAYOUTS
+def test_parity_thinning(rates, q, layout):
     snaps = [0.01, 0.1]
     n = 1024 + 3
-    g = gpu_run((64, 64, 128), n, seed=12, t_end=2.0, snaps=snaps, rates=rates, thin_bits=q)
+    g = gpu_run((64, 64, 128), n, seed=12, t_end=2.0, snaps=snaps, rates=rates, thin_bits=q, layout=layout)
     r = oracle.run(oracle.frank(*rates), (64, 64, 128), n, seed=12, t_end=2.0, snap_times=snaps,
                    thin_bits=q, threads=THREADS)
     assert_parity(g, r)
@@ -211,27 +238,30 @@ def test_empty_context():
 
 @pytest.mark.parametrize("init", [(1, 0, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 0, 50), (25, 0, 0),
                                   (2, 1, 0)])
-def test_small_and_absorbed_systems(init):
+@LAYOUTS
+def test_small_and_absorbed_systems(init, layout):
     n = 70
     snaps = [0.0, 0.5, 3.0]
-    g = gpu_run(init, n, seed=2, t_end=3.0, snaps=snaps)
+    g = gpu_run(init, n, seed=2, t_end=3.0, snaps=snaps, layout=layout)
     r = oracle.run(oracle.frank(), init, n, seed=2, t_end=3.0, snap_times=snaps)
     assert_parity(g, r)
 
 
-def test_t_end_zero_and_snapshot_at_t_end():
-    g = gpu_run((10, 10, 10), 40, seed=1, t_end=0.0, snaps=[0.0])
+@LAYOUTS
+def test_t_end_zero_and_snapshot_at_t_end(layout):
+    g = gpu_run((10, 10, 10), 40, seed=1, t_end=0.0, snaps=[0.0], layout=layout)
     assert np.all(g["final_counts"] == [10, 10, 10]) and np.all(g["outcome"] == -1)
     assert np.all(np.isinf(g["t_abs"])) and np.all(g["snap_counts"] == [10, 10, 10])
     snaps = [0.02, 0.04]
-    g = gpu_run((16, 16, 32), 96, seed=1, t_end=0.04, snaps=snaps)
+    g = gpu_run((16, 16, 32), 96, seed=1, t_end=0.04, snaps=snaps, layout=layout)
     r = oracle.run(oracle.frank(), (16, 16, 32), 96, seed=1, t_end=0.04, snap_times=snaps)
     assert_parity(g, r)
     assert np.array_equal(g["snap_counts"][1], g["final_counts"])
 
 
-def test_step_budget_reports_timeout():
-    g = gpu_run((256, 256, 512), 64, seed=1, t_end=50.0, step_budget=100, expect_status=pkg.SSA_ETIMEOUT)
+@LAYOUTS
+def test_step_budget_reports_timeout(layout):
+    g = gpu_run((256, 256, 512), 64, seed=1, t_end=50.0, step_budget=100, expect_status=pkg.SSA_ETIMEOUT, layout=layout)
     assert g["counters"]["group_steps"] == 2 * 100
     r = oracle.run(oracle.frank(), (256, 256, 512), 64, seed=1, t_end=50.0, step_budget=100, check=False)
     assert np.array_equal(g["final_counts"], r["final_counts"])
