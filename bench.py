@@ -47,10 +47,10 @@ SNAPS = [T_END * 10.0 ** (4.0 * (s - (N_SNAP - 1)) / (N_SNAP - 1)) for s in rang
 L2_BYTES = 129 * 2**20
 SMS = 152
 MAX_SM_MHZ = 2070.0
-# DRAM bytes (read + write) of one launch of the bit-sliced kernel on the default workload: the
-# quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (580.6 KB) scaled by the
-# number of runs.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) of one launch of the one-thread bit-sliced kernel on the default
+# workload: the quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (592 640 B)
+# scaled x4 by the number of runs.  Set to None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_LAUNCH = 4 * 592_640
 
 
 def algorithmic_ops_per_group_step(K: int, b: int) -> int:
@@ -272,7 +272,7 @@ def main():
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    reactions = absorbed = lane_steps = group_steps = max_group_steps = 0
+    reactions = absorbed = lane_steps = group_steps = max_group_steps = layout_used = 0
     barrier()
     t_wall0 = time.perf_counter()
     for k in range(args.steps):
@@ -286,6 +286,7 @@ def main():
         group_steps += int(c[0])
         absorbed += int(c[5])
         max_group_steps = max(max_group_steps, int(c[8]))
+        layout_used = int(c[9])
     barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
@@ -319,7 +320,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak,
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH if (WORKLOAD == "c2" and RUNS_PER_GPU == 1 << 20
-                                                        and PRECISION == 0) else None,
+                                                        and PRECISION == 0 and layout_used == 1) else None,
                 "ops_per_group_step": ops_unit, "group_steps_per_launch": gs_per_launch,
                 "peak_basis": f"{SMS} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {MAX_SM_MHZ:g} MHz",
                 "lop3_microbench_gops": micro}
@@ -335,7 +336,7 @@ def main():
               "group_steps_per_step": group_steps / args.steps, "max_group_steps": max_group_steps,
               "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
               "hist_checksum": float(htot.sum().item()),
-              "layout": {0: "auto", 1: "thread", 2: "warps"}[args.layout]}
+              "layout": {0: "none", 1: "thread", 2: "warps"}[layout_used]}
 
     # ---- end to end through the C ABI with host buffers (create from host arrays, run, read every
     # per-run output into pinned host memory, destroy), rank-local

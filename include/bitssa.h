@@ -4,7 +4,7 @@
  * "Parallelization of Gillespie algorithm based on binary words"
  * (arXiv 2412.16613).
  *
- * The method (Sec. 3): M independent runs of a conserved mass-action network
+ * The method (Sec. 4): M independent runs of a conserved mass-action network
  * are packed one per bit of a machine word, species counts live as bit-planes
  * (Eqs. eq3, eq1, eq2, eq4, eq6), and one Gillespie step for all M runs is
  * done with word-wide logic: a uniform integer n in [0, Lambda) per run, the
@@ -123,7 +123,8 @@ enum {
   SSA_FIELD_COUNTERS = 5,       /* uint64[10]: group steps, lane steps of live runs, real
                                    reactions, null lane steps, redraw rounds, absorbed runs,
                                    groups finished, error flags, steps of the longest group,
-                                   0 (reserved) */
+                                   the layout that ran (1 SSA_LAYOUT_THREAD, 2 SSA_LAYOUT_WARPS,
+                                   0 no bit-sliced launch) */
   SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,
                                    and runs not absorbed, per ensemble */
 };
@@ -135,14 +136,14 @@ void ssa_default_options(ssa_options* opt);
  * Create a context for n_runs runs of one network.
  *   reactants, products: int32[n_reactions][n_species] multiplicities; every reaction
  *     has order 1 or 2 and conserves the total count (Sec. 2: the model conserves
- *     N_tot = N_L + N_R + N_A, which the method relies on, Sec. 3).
+ *     N_tot = N_L + N_R + N_A, which the method relies on, Sec. 4).
  *   rates: double[n_reactions], k_r >= 0 with max > 0.  Non-unit ratios k_r / k_max
  *     are applied by thinning: the drawn reaction is kept iff a q-bit uniform U is
  *     below T_r = floor(k_r / k_max 2^q) (the paper leaves general rates to future
  *     work, Sec. 6; this is an exact-in-the-limit integer form of it).
  *   N0: int64[n_species] shared initial counts (n0_per_run = 0) or
  *     int64[n_runs][n_species] (n0_per_run = 1); every run must have the same total
- *     (Sec. 3: the copies share N_tot).
+ *     (Sec. 4: the copies share N_tot).
  *   seed: the Philox key.
  * SSA_EUNSUPPORTED unless the network is Frank's model (Eqs. 1-3) up to a
  * relabelling of species: three species X, Y, A and, in this order,

@@ -26,7 +26,7 @@ extern "C" {
 int bitssa_test_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, int32_t which);
 
 /*
- * Bit-sliced integer primitives of Sec. 3.1-3.2 run on 8-bit operands.  x, y:
+ * Bit-sliced integer primitives of Sec. 4.1 run on 8-bit operands.  x, y:
  * int64[n] per-lane operands in [0, 255] (n a multiple of 32); lane j of the
  * device words holds x[j], y[j].  out: int64[n].
  *   op 0: x + y (ripple-carry add, 9-bit result)

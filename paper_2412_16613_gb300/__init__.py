@@ -31,7 +31,7 @@ SSA_FIELD_FINAL_COUNTS, SSA_FIELD_ABSORB_TIME, SSA_FIELD_ABSORB_OUTCOME = 0, 1, 
 SSA_FIELD_EE_HIST, SSA_FIELD_SNAP_COUNTS, SSA_FIELD_COUNTERS, SSA_FIELD_ENS_ABSORBED = 3, 4, 5, 6
 SSA_N_COUNTERS = 10
 COUNTER_NAMES = ["group_steps", "lane_steps", "reactions", "null_lane_steps", "redraw_rounds",
-                 "absorbed", "groups_done", "error_flags", "max_group_steps", "reserved"]
+                 "absorbed", "groups_done", "error_flags", "max_group_steps", "layout"]
 
 _FIELD_DTYPE = {
     SSA_FIELD_FINAL_COUNTS: np.int32, SSA_FIELD_ABSORB_TIME: np.float64,

@@ -1,7 +1,7 @@
 // bitslice.cuh -- bit-sliced integer arithmetic on plane arrays (sm_103a).
 //
 // A bit-sliced integer of W planes is uint32_t x[W]; plane i holds bit i of
-// 32 independent integers, one per lane (Sec. 3, Eqs. eq4 and eq6).  Every
+// 32 independent integers, one per lane (Sec. 4, Eqs. eq4 and eq6).  Every
 // routine below works on all 32 lanes at once with word-wide logic; plane
 // counts are compile-time so that loops unroll and the planes stay in
 // registers.  The compiler maps each 2- or 3-input expression to one LOP3.
@@ -16,7 +16,7 @@
 namespace bitssa {
 namespace bs {
 
-// Full-adder carry (majority) and sum.  Sec. 3.1 prints the carry as
+// Full-adder carry (majority) and sum.  Sec. 4.1 prints the carry as
 // (b2 & (b1 | c)) | (b1 & c) -- the majority -- and the partial sum must be the
 // three-way xor (the printed "b1 & b2" cannot produce the paper's own Fig. 1).
 __device__ __forceinline__ uint32_t maj(uint32_t a, uint32_t b, uint32_t c) {
@@ -63,7 +63,7 @@ __device__ __forceinline__ void add_signed(uint32_t (&S)[KW], const uint32_t (&T
   }
 }
 
-// Lanes where n < S, both unsigned: the borrow out of n - S (Sec. 3 step c:
+// Lanes where n < S, both unsigned: the borrow out of n - S (Sec. 4 step c:
 // the comparison word [m <= n] is the complement of [n < m]).
 template <int KW>
 __device__ __forceinline__ uint32_t less_than(const uint32_t (&n)[KW], const uint32_t (&S)[KW]) {
@@ -104,7 +104,7 @@ __device__ __forceinline__ uint32_t differ(const uint32_t (&x)[KW], const uint32
 }
 
 // Schoolbook product of two unsigned bit-sliced integers, truncated to RW planes
-// (the O(N_2^2) multiplication of Sec. 3.2; used once per group to build the
+// (the O(N_2^2) multiplication of Sec. 4.1; used once per group to build the
 // initial propensities).
 template <int RW, int XW, int YW>
 __device__ __forceinline__ void multiply(uint32_t (&out)[RW], const uint32_t (&x)[XW],

@@ -17,7 +17,7 @@
 // D and A are read back from L and U (U = N - 2(L+D) - 1) when a snapshot or
 // an output needs them.
 //
-// One group step (Sec. 3, steps 1-7 with steps 5-6 replaced by a-d):
+// One group step (Sec. 3, steps 1-7, with the draw of step 5 done by Sec. 4's steps a-d):
 //   1. Philox words of attempt 0: planes of the uniform integer n and the
 //      group's waiting-time bits; lanes with n >= lambda_int redraw from the
 //      next attempt.

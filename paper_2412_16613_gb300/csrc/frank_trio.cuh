@@ -9,7 +9,7 @@
 //   warp 1: dS2 = U | U  | V      forms U = A-L-D-1, V = -2U-6
 //   warp 2: dS3 = P | Q  | R3     forms P, Q = A-D-1, R3 = L+D-2A-3
 // Each form changes by a per-reaction constant, so all of them are kept up to date with
-// one masked constant add per step.  The CDF walk of Sec. 3 (steps a-d) becomes parallel
+// one masked constant add per step.  The CDF walk of Sec. 4 (steps a-d) becomes parallel
 // over r: warp r forms lt_r = [n < S_r] and the three comparator words meet in shared
 // memory, so that every warp forms the same changer words xi_r.
 //

@@ -26,7 +26,8 @@ enum Counter {
   kAbsorbed = 5,
   kGroupsDone = 6,
   kErrorFlags = 7,
-  kMaxGroupSteps = 8  // the longest group, in steps
+  kMaxGroupSteps = 8, // the longest group, in steps
+  kLayoutUsed = 9     // set by the host: 1 one thread per group, 2 three warps per 32 groups
 };
 
 // Error flags (OR-ed into the status word).

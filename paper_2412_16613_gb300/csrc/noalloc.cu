@@ -232,6 +232,7 @@ extern "C" int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int
   if ((e = cudaStreamSynchronize(stream)) != cudaSuccess)
     return noalloc_fail(SSA_ECUDA, std::string("simulation: ") + cudaGetErrorString(e));
   host_counters[kErrorFlags] = status;
+  host_counters[kLayoutUsed] = n_runs > 0 ? SSA_LAYOUT_THREAD : 0;
   if (counters_out) std::memcpy(counters_out, host_counters, sizeof host_counters);
   if (status & kErrRedraw) return noalloc_fail(SSA_EOVERFLOW, "64 redraws of n in a row");
   if (status & kErrRange) return noalloc_fail(SSA_EOVERFLOW, "internal range check failed");

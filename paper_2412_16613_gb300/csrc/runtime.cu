@@ -80,6 +80,7 @@ struct ssa_ctx {
   size_t snap_cap = 0;
   unsigned long long* d_counters = nullptr;  // [kCounters] then the queues
   unsigned int* d_status = nullptr;
+  int layout_used = 0;  // SSA_LAYOUT_* of the last launch, 0 if none
   int n_queues = 0;
   bool ran = false;
   int n_snap = 0;
@@ -396,6 +397,7 @@ int launch_runs(ssa_ctx* c) {
   fl.status = c->d_status;
   const int block = c->opt.block_size ? c->opt.block_size : 64;
 
+  c->layout_used = 0;
   if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN) {
     if (c->batch) return fail(c, SSA_EUNSUPPORTED, "the thread-per-run engine runs single-ensemble contexts");
     ThreadLaunch tl;
@@ -435,6 +437,7 @@ int launch_runs(ssa_ctx* c) {
   long long all_groups = 0;
   for (const Ensemble& en : c->ens) all_groups += (en.n_runs + 31) / 32;
   const bool warps = use_warps_layout(c->opt, all_groups, c->sm_count);
+  c->layout_used = warps ? SSA_LAYOUT_WARPS : SSA_LAYOUT_THREAD;
   const int clock_variant = c->opt.precision == SSA_P64 ? 2 : 0;
   if (!c->batch) {
     const Ensemble& en = c->ens[0];
@@ -558,7 +561,7 @@ int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_spec
   if (n_runs < 0) return bail(SSA_EINVAL, "n_runs must be >= 0");
   if (n0_per_run != 0 && n0_per_run != 1) return bail(SSA_EINVAL, "n0_per_run must be 0 or 1");
   if (c->opt.first_run + n_runs > (1ll << 37)) return bail(SSA_EINVAL, "run index beyond 2^37");
-  // total count, identical for every run (Sec. 3)
+  // total count, identical for every run (Sec. 4)
   long long n_tot = -1;
   std::vector<int> rows;
   const long long nrows = n0_per_run ? n_runs : 1;
@@ -737,6 +740,7 @@ int ssa_run(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_sn
     return cuda_fail(c, e, "read status");
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "simulation");
   c->counters[kErrorFlags] = status;
+  c->counters[kLayoutUsed] = c->layout_used;
   c->ran = true;
   if (status & kErrRedraw) return fail(c, SSA_EOVERFLOW, "64 redraws of n in a row");
   if (status & kErrRange) return fail(c, SSA_EOVERFLOW, "internal range check failed");

@@ -33,8 +33,9 @@ def weak_shard(runs_per_rank: int, rank: int) -> tuple[int, int]:
     return rank * runs_per_rank, runs_per_rank
 
 
-# counter indices whose combination over ranks is a maximum rather than a sum
-MAX_COUNTERS = (8,)
+# counter indices whose combination over ranks is a maximum rather than a sum (the longest group,
+# the layout)
+MAX_COUNTERS = (8, 9)
 
 
 def combine(hist: np.ndarray, counters: np.ndarray, dist=None):

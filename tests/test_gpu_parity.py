@@ -19,6 +19,12 @@ LAYOUTS = pytest.mark.parametrize("layout", [pkg.SSA_LAYOUT_THREAD, pkg.SSA_LAYO
                                   ids=["thread", "warps"])
 
 
+def same_counters(a, b):
+    """Every run counter equal; the layout counter names the layout that ran."""
+    return {k: v for k, v in a["counters"].items() if k != "layout"} == \
+        {k: v for k, v in b["counters"].items() if k != "layout"}
+
+
 @pytest.fixture(scope="module", autouse=True)
 def device():
     import torch
@@ -160,7 +166,7 @@ def test_results_do_not_depend_on_launch_shape():
         g = gpu_run((256, 256, 512), 3000, seed=5, t_end=0.05, snaps=snaps, **shape)
         for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
             assert np.array_equal(g[k], base[k]), (shape, k)
-        assert g["counters"] == base["counters"], shape
+        assert same_counters(g, base), shape
 
 
 @pytest.mark.parametrize("init,n,t_end,seed", [((256, 256, 512), 1 << 16, 50.0, 21),
@@ -173,7 +179,8 @@ def test_layouts_agree_bit_for_bit(init, n, t_end, seed):
     b = gpu_run(init, n, seed=seed, t_end=t_end, snaps=snaps, layout=pkg.SSA_LAYOUT_WARPS)
     for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
         assert np.array_equal(a[k], b[k]), k
-    assert a["counters"] == b["counters"]
+    assert same_counters(a, b)
+    assert (a["counters"]["layout"], b["counters"]["layout"]) == (pkg.SSA_LAYOUT_THREAD, pkg.SSA_LAYOUT_WARPS)
 
 
 @LAYOUTS

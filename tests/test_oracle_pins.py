@@ -453,7 +453,7 @@ def _golden_examples():
 
 
 def test_sum_pseudocode_reading():
-    """Sec. 3.1: the printed partial sum s = b1 & b2 cannot give Fig. 1's 1 + 1 = 2;
+    """Sec. 4.1: the printed partial sum s = b1 & b2 cannot give Fig. 1's 1 + 1 = 2;
     the full-adder sum s = b1 ^ b2 ^ c with the printed carry can."""
     g = _golden_examples()
 
