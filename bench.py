@@ -214,6 +214,9 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--layout", type=int, default=0,
                     help="0 auto, 1 one thread per group of 32 runs, 2 three warps per 32 groups")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip ssa_tune (by default it times every launch configuration on the "
+                         "workload during warm-up and keeps the fastest; c3 keeps the per-bucket rule)")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--runs", type=int, default=0,
                     help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
@@ -266,6 +269,9 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    tuned = None
+    if not args.no_tune and WORKLOAD != "c3" and args.layout == 0 and args.block == 0:
+        tuned = pkg.ssa_tune(ctx, T_END, SNAPS, probe_steps=0)
     for _ in range(args.warmup):
         pkg.ssa_run(ctx, T_END, SNAPS)
     barrier()
@@ -336,7 +342,9 @@ def main():
               "group_steps_per_step": group_steps / args.steps, "max_group_steps": max_group_steps,
               "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
               "hist_checksum": float(htot.sum().item()),
-              "layout": {0: "none", 1: "thread", 2: "warps"}[layout_used]}
+              "layout": {0: "none", 1: "thread", 2: "warps", 3: "thread+warps"}[layout_used],
+              "tuned": None if tuned is None else {"layout": {0: "rule", 1: "thread", 2: "warps"}[tuned[0]],
+                                                   "block": tuned[1]}}
 
     # ---- end to end through the C ABI with host buffers (create from host arrays, run, read every
     # per-run output into pinned host memory, destroy), rank-local
@@ -350,6 +358,8 @@ def main():
     if WORKLOAD == "c3":
         h2d = sum(np.asarray(BATCH[k]).nbytes for k in ("init", "rates", "runs", "seeds")) + 144
     e2e_steps = max(1, min(args.steps, 3))
+    if tuned is not None:  # the end-to-end contexts run the configuration the tuner chose
+        opt.layout, opt.block_size = tuned[0], (tuned[1] if tuned[0] == pkg.SSA_LAYOUT_THREAD else 0)
     barrier()
     t0 = time.perf_counter()
     e2e_react = 0

@@ -123,7 +123,8 @@ enum {
   SSA_FIELD_COUNTERS = 5,       /* uint64[10]: group steps, lane steps of live runs, real
                                    reactions, null lane steps, redraw rounds, absorbed runs,
                                    groups finished, error flags, steps of the longest group,
-                                   the layout that ran (1 SSA_LAYOUT_THREAD, 2 SSA_LAYOUT_WARPS,
+                                   the layouts that ran (bit 0 SSA_LAYOUT_THREAD, bit 1
+                                   SSA_LAYOUT_WARPS: 1, 2, or 3 for a batch that used both;
                                    0 no bit-sliced launch) */
   SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,
                                    and runs not absorbed, per ensemble */
@@ -176,6 +177,23 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
  * time <= t.  n_snap in [0, 64].  Blocks until the work is done on the stream.
  */
 int ssa_run(ssa_ctx* ctx, double t_end, const double* snapshot_times, int32_t n_snap);
+
+/*
+ * Autotuner: time the context's work under each launch configuration the library has (the
+ * automatic layout rule, one thread per group of 32 runs with blocks of 32, 64 and 128
+ * threads, three warps per 32 groups) and keep the fastest for later ssa_run calls whose
+ * options leave layout = SSA_LAYOUT_AUTO and block_size = 0 (fixed options win).  Results do
+ * not depend on the configuration: every one draws the same streams and gives the same runs.
+ *   t_end, snapshot_times, n_snap: the workload to time, as for ssa_run.
+ *   probe_steps: 0 times whole runs (exact, costs ten runs); > 0 stops every group after that
+ *     many steps (a cheap probe of the early, crowded part of a run).
+ *   choice: int32[2] or NULL; receives the chosen SSA_LAYOUT_* (SSA_LAYOUT_AUTO = the rule)
+ *     and the block size of the one-thread layout.
+ * Leaves the context without a run to fetch (SSA_ESTATE until the next ssa_run).  Errors as for
+ * ssa_run; SSA_EUNSUPPORTED for the thread-per-run engine.
+ */
+int ssa_tune(ssa_ctx* ctx, double t_end, const double* snapshot_times, int32_t n_snap, int64_t probe_steps,
+             int32_t* choice);
 
 /* Size in bytes of a field after the last ssa_run (0 for an unknown field). */
 int ssa_field_bytes(const ssa_ctx* ctx, int32_t field, size_t* bytes);

@@ -89,6 +89,7 @@ def lib():
                                            P(C.c_int64), P(C.c_double), P(C.c_int64), P(C.c_uint64),
                                            P(ssa_options), P(C.c_void_p)]
             L.ssa_run.argtypes = [C.c_void_p, C.c_double, P(C.c_double), C.c_int32]
+            L.ssa_tune.argtypes = [C.c_void_p, C.c_double, P(C.c_double), C.c_int32, C.c_int64, P(C.c_int32)]
             L.ssa_field_bytes.argtypes = [C.c_void_p, C.c_int32, P(C.c_size_t)]
             L.ssa_fetch.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32]
             L.ssa_destroy.argtypes = [C.c_void_p]
@@ -194,6 +195,16 @@ def ssa_run(ctx, t_end, snapshot_times=()):
     snaps = np.ascontiguousarray(snapshot_times, dtype=np.float64)
     ptr = _p(snaps, C.c_double) if len(snaps) else None
     return _check(lib().ssa_run(ctx, float(t_end), ptr, len(snaps)), ctx)
+
+
+def ssa_tune(ctx, t_end, snapshot_times=(), probe_steps=0):
+    """C ssa_tune: time every launch configuration on this workload and keep the fastest for
+    later runs; returns (layout, block size of the one-thread layout)."""
+    snaps = np.ascontiguousarray(snapshot_times, dtype=np.float64)
+    ptr = _p(snaps, C.c_double) if len(snaps) else None
+    choice = np.zeros(2, dtype=np.int32)
+    _check(lib().ssa_tune(ctx, float(t_end), ptr, len(snaps), int(probe_steps), _p(choice, C.c_int32)), ctx)
+    return int(choice[0]), int(choice[1])
 
 
 def ssa_field_bytes(ctx, field):

@@ -27,7 +27,7 @@ enum Counter {
   kGroupsDone = 6,
   kErrorFlags = 7,
   kMaxGroupSteps = 8, // the longest group, in steps
-  kLayoutUsed = 9     // set by the host: 1 one thread per group, 2 three warps per 32 groups
+  kLayoutUsed = 9     // set by the host: bit 0 one thread per group, bit 1 three warps per 32 groups
 };
 
 // Error flags (OR-ed into the status word).

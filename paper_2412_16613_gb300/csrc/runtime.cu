@@ -80,7 +80,9 @@ struct ssa_ctx {
   size_t snap_cap = 0;
   unsigned long long* d_counters = nullptr;  // [kCounters] then the queues
   unsigned int* d_status = nullptr;
-  int layout_used = 0;  // SSA_LAYOUT_* of the last launch, 0 if none
+  int layout_used = 0;  // SSA_LAYOUT_* bits of the last run, 0 if none
+  int tuned_layout = -1;  // ssa_tune's choice for SSA_LAYOUT_AUTO: -1 none, else an SSA_LAYOUT_*
+  int tuned_block = 0;    // ssa_tune's block size for the one-thread layout, 0 none
   int n_queues = 0;
   bool ran = false;
   int n_snap = 0;
@@ -88,6 +90,8 @@ struct ssa_ctx {
   int sm_count = 0;
   // batch: the K buckets run concurrently on side streams forked from `stream`
   std::vector<cudaStream_t> side;
+  cudaGraphExec_t batch_graph = nullptr;     // the batch's fork / launches / join, captured once
+  std::vector<unsigned char> batch_graph_key; // the launch plan it was captured from
   std::vector<cudaEvent_t> side_done;
   cudaEvent_t fork = nullptr;
 };
@@ -362,16 +366,54 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
   return SSA_OK;
 }
 
-// The layout of the bit-sliced engine.  The three-warp layout finishes a group's step sooner
-// (its work is split over three schedulers) but holds a group in three times as many threads;
-// SSA_LAYOUT_AUTO takes it while its blocks fit at most two to an SM, where a run's time is
-// its longest group's steps times the step latency, and the one-thread layout beyond that,
-// where the three-warp blocks would no longer all be resident (measured on GB300 at
-// N_tot = 1024: three warps ahead up to 2^18 runs, one thread ahead from 2^19).
+// One bucket's launch in a batch: everything that decides the kernel and its arguments.
+struct BatchLaunch {
+  int K, warps, grid, block, stream;
+  FrankLaunch fl;
+};
+
+// Fork the side streams from the context's stream, launch every bucket, join.
+int issue_batch(ssa_ctx* c, const std::vector<BatchLaunch>& plan) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(c->fork, c->stream)) != cudaSuccess) return cuda_fail(c, e, "fork event");
+  for (cudaStream_t s : c->side)
+    if ((e = cudaStreamWaitEvent(s, c->fork, 0)) != cudaSuccess) return cuda_fail(c, e, "fork wait");
+  for (const BatchLaunch& b : plan) {
+    void* s = (void*)c->side[b.stream];
+    if (b.warps) {
+      if ((e = (cudaError_t)frank_trio_launcher(b.K)(b.fl, b.grid, 0, s)) != cudaSuccess)
+        return cuda_fail(c, e, "three-warp bit-sliced kernel launch");
+    } else if ((e = (cudaError_t)frank_launcher(b.K)(b.fl, b.grid, b.block, 0, s)) != cudaSuccess) {
+      return cuda_fail(c, e, "bit-sliced kernel launch");
+    }
+  }
+  for (size_t i = 0; i < c->side.size(); ++i) {
+    if ((e = cudaEventRecord(c->side_done[i], c->side[i])) != cudaSuccess) return cuda_fail(c, e, "join event");
+    if ((e = cudaStreamWaitEvent(c->stream, c->side_done[i], 0)) != cudaSuccess) return cuda_fail(c, e, "join wait");
+  }
+  return SSA_OK;
+}
+
+// The layout of the bit-sliced engine for one launch of `groups` groups.  The three-warp
+// layout finishes a group's step sooner (its work is split over three schedulers) but holds a
+// group in three times as many threads; SSA_LAYOUT_AUTO takes it while its blocks fit at most
+// two to an SM, where a launch's time is its longest group's steps times the step latency, and
+// the one-thread layout beyond that, where the three-warp blocks would no longer all be
+// resident (measured on GB300 at N_tot = 1024: three warps ahead up to 2^18 runs, one thread
+// ahead from 2^19).  A batch decides per K bucket: 4096 ensembles of 1024 runs with N_tot
+// log-uniform in [16, 65536] take 19.7 s on three warps against 36.2 s on one thread.
 bool use_warps_layout(const ssa_options& o, long long groups, int sm_count) {
   if (o.layout == SSA_LAYOUT_THREAD) return false;
   if (o.layout == SSA_LAYOUT_WARPS) return true;
   return groups <= 64ll * sm_count;
+}
+
+// The layout of one launch of a context: a fixed option wins, then the tuner's choice, then the
+// rule above.
+bool ctx_warps(const ssa_ctx* c, long long groups) {
+  if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_THREAD) return false;
+  if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_WARPS) return true;
+  return use_warps_layout(c->opt, groups, c->sm_count);
 }
 
 int launch_runs(ssa_ctx* c) {
@@ -395,7 +437,7 @@ int launch_runs(ssa_ctx* c) {
   fl.n_runs_total = c->n_runs_total;
   fl.counters = c->d_counters;
   fl.status = c->d_status;
-  const int block = c->opt.block_size ? c->opt.block_size : 64;
+  const int block = c->opt.block_size ? c->opt.block_size : (c->tuned_block ? c->tuned_block : 64);
 
   c->layout_used = 0;
   if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN) {
@@ -434,10 +476,6 @@ int launch_runs(ssa_ctx* c) {
     return SSA_OK;
   }
 
-  long long all_groups = 0;
-  for (const Ensemble& en : c->ens) all_groups += (en.n_runs + 31) / 32;
-  const bool warps = use_warps_layout(c->opt, all_groups, c->sm_count);
-  c->layout_used = warps ? SSA_LAYOUT_WARPS : SSA_LAYOUT_THREAD;
   const int clock_variant = c->opt.precision == SSA_P64 ? 2 : 0;
   if (!c->batch) {
     const Ensemble& en = c->ens[0];
@@ -450,6 +488,8 @@ int launch_runs(ssa_ctx* c) {
     fl.queue = c->d_counters + kCounters;
     const int smem = n_snap * kHistBins * (int)sizeof(unsigned int);
     int occ = 0;
+    const bool warps = ctx_warps(c, groups);
+    c->layout_used = warps ? SSA_LAYOUT_WARPS : SSA_LAYOUT_THREAD;
     if (warps) {
       if (frank_trio_max_active_blocks(K, clock_variant, smem, &occ) != 0 || occ < 1)
         return fail(c, SSA_ECUDA, "occupancy query failed for the three-warp bit-sliced kernel");
@@ -474,39 +514,62 @@ int launch_runs(ssa_ctx* c) {
   fl.item_ens = c->d_item_ens;
   fl.item_group = c->d_item_group;
   // one launch per K bucket (largest K first), spread over the side streams so that the
-  // buckets run concurrently; the caller's stream waits for all of them
-  if ((e = cudaEventRecord(c->fork, c->stream)) != cudaSuccess) return cuda_fail(c, e, "fork event");
-  for (cudaStream_t s : c->side)
-    if ((e = cudaStreamWaitEvent(s, c->fork, 0)) != cudaSuccess) return cuda_fail(c, e, "fork wait");
+  // buckets run concurrently; the caller's stream waits for all of them.  The plan is fixed
+  // first; on a capturable stream it is recorded once as a CUDA graph and replayed while it
+  // stays the same, so a batch of any size is one graph launch.
+  std::vector<BatchLaunch> plan(c->ranges.size());
+  std::memset(plan.data(), 0, sizeof(BatchLaunch) * plan.size());
   for (size_t r = 0; r < c->ranges.size(); ++r) {
-    const int K = std::max(1, c->ranges[r].first);
-    fl.item_begin = c->ranges[r].second.first;
-    fl.item_end = c->ranges[r].second.second;
-    fl.queue = c->d_counters + kCounters + 1 + r;
+    BatchLaunch& b = plan[r];
+    b.K = std::max(1, c->ranges[r].first);
+    b.fl = fl;
+    b.fl.item_begin = c->ranges[r].second.first;
+    b.fl.item_end = c->ranges[r].second.second;
+    b.fl.queue = c->d_counters + kCounters + 1 + r;
+    b.stream = (int)(r % c->side.size());
+    const long long groups = b.fl.item_end - b.fl.item_begin;
+    b.warps = ctx_warps(c, groups) ? 1 : 0;
+    c->layout_used |= b.warps ? SSA_LAYOUT_WARPS : SSA_LAYOUT_THREAD;
     int occ = 0;
-    cudaStream_t s = c->side[r % c->side.size()];
-    if (warps) {
-      if (frank_trio_max_active_blocks(K, clock_variant | 1, 0, &occ) != 0 || occ < 1)
+    if (b.warps) {
+      if (frank_trio_max_active_blocks(b.K, clock_variant | 1, 0, &occ) != 0 || occ < 1)
         return fail(c, SSA_ECUDA, "occupancy query failed for the three-warp bit-sliced kernel");
+      b.block = kTrioBlock;
       const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
-      const long long need = (fl.item_end - fl.item_begin + 31) / 32;
-      const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
-      if ((e = (cudaError_t)frank_trio_launcher(K)(fl, grid, 0, (void*)s)) != cudaSuccess)
-        return cuda_fail(c, e, "three-warp bit-sliced kernel launch");
-      continue;
+      b.grid = (int)std::max(1ll, std::min((groups + 31) / 32, (long long)c->sm_count * bpsm));
+    } else {
+      if (frank_max_active_blocks(b.K, clock_variant | 1, block, 0, &occ) != 0 || occ < 1)
+        return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
+      b.block = block;
+      const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+      b.grid = (int)std::max(1ll, std::min((groups + block - 1) / block, (long long)c->sm_count * bpsm));
     }
-    if (frank_max_active_blocks(K, clock_variant | 1, block, 0, &occ) != 0 || occ < 1)
-      return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
-    const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
-    const long long need = (fl.item_end - fl.item_begin + block - 1) / block;
-    const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
-    if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, 0, (void*)s)) != cudaSuccess)
-      return cuda_fail(c, e, "bit-sliced kernel launch");
   }
-  for (size_t i = 0; i < c->side.size(); ++i) {
-    if ((e = cudaEventRecord(c->side_done[i], c->side[i])) != cudaSuccess) return cuda_fail(c, e, "join event");
-    if ((e = cudaStreamWaitEvent(c->stream, c->side_done[i], 0)) != cudaSuccess) return cuda_fail(c, e, "join wait");
+  if (!c->stream) return issue_batch(c, plan);  // the legacy default stream cannot be captured
+  std::vector<unsigned char> key(sizeof(BatchLaunch) * plan.size());
+  std::memcpy(key.data(), plan.data(), key.size());
+  if (!c->batch_graph || key != c->batch_graph_key) {
+    if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
+    c->batch_graph = nullptr;
+    c->batch_graph_key.clear();
+    if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(c, e, "begin capture of the batch launch");
+    const int st = issue_batch(c, plan);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (st != SSA_OK || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return st != SSA_OK ? st : cuda_fail(c, ee, "end capture of the batch launch");
+    }
+    e = cudaGraphInstantiate(&c->batch_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->batch_graph = nullptr;
+      return cuda_fail(c, e, "instantiate the batch graph");
+    }
+    c->batch_graph_key = key;
   }
+  if ((e = cudaGraphLaunch(c->batch_graph, c->stream)) != cudaSuccess) return cuda_fail(c, e, "batch graph launch");
   return SSA_OK;
 }
 
@@ -748,6 +811,71 @@ int ssa_run(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_sn
   return SSA_OK;
 }
 
+int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_snap, int64_t probe_steps,
+             int32_t* choice) {
+  if (!c) return fail(nullptr, SSA_EINVAL, "ctx is NULL");
+  if (probe_steps < 0) return fail(c, SSA_EINVAL, "probe_steps must be >= 0");
+  if (c->opt.engine != SSA_ENGINE_BITSLICED) return fail(c, SSA_EUNSUPPORTED, "the tuner chooses bit-sliced layouts");
+  struct Candidate {
+    int layout, block;
+  };
+  // the rule (per K bucket in a batch), one thread per group at three block sizes, three warps
+  const Candidate cands[] = {{SSA_LAYOUT_AUTO, 64}, {SSA_LAYOUT_THREAD, 32}, {SSA_LAYOUT_THREAD, 64},
+                             {SSA_LAYOUT_THREAD, 128}, {SSA_LAYOUT_WARPS, 64}};
+  DeviceGuard guard(c->device);
+  const long long budget = c->opt.step_budget;
+  const int old_layout = c->tuned_layout, old_block = c->tuned_block;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e;
+  if ((e = cudaEventCreate(&ev[0])) != cudaSuccess || (e = cudaEventCreate(&ev[1])) != cudaSuccess) {
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    return cuda_fail(c, e, "tuner events");
+  }
+  int st = SSA_OK;
+  float best = -1.0f;
+  Candidate win = cands[0];
+  c->opt.step_budget = probe_steps;
+  for (const Candidate& cand : cands) {
+    c->tuned_layout = cand.layout;
+    c->tuned_block = cand.block;
+    float ms = -1.0f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel and records graphs
+      cudaEventRecord(ev[0], c->stream);
+      st = ssa_run(c, t_end, snapshot_times, n_snap);
+      cudaEventRecord(ev[1], c->stream);
+      if (st != SSA_OK && st != SSA_ETIMEOUT) break;
+      st = SSA_OK;
+      float t = 0.0f;
+      if ((e = cudaEventSynchronize(ev[1])) != cudaSuccess || (e = cudaEventElapsedTime(&t, ev[0], ev[1])) != cudaSuccess) {
+        st = cuda_fail(c, e, "tuner timing");
+        break;
+      }
+      if (ms < 0.0f || t < ms) ms = t;
+    }
+    if (st != SSA_OK) break;
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      win = cand;
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  c->opt.step_budget = budget;
+  c->ran = false;  // the probes' outputs are not a run of the caller's
+  if (st != SSA_OK) {
+    c->tuned_layout = old_layout;
+    c->tuned_block = old_block;
+    return st;
+  }
+  c->tuned_layout = win.layout;
+  c->tuned_block = win.block;
+  if (choice) {
+    choice[0] = win.layout;
+    choice[1] = win.block;
+  }
+  return SSA_OK;
+}
+
 int ssa_field_bytes(const ssa_ctx* c, int32_t field, size_t* bytes) {
   if (!c || !bytes) return fail(const_cast<ssa_ctx*>(c), SSA_EINVAL, "null argument");
   *bytes = field_bytes(c, field);
@@ -797,6 +925,7 @@ int ssa_destroy(ssa_ctx* c) {
   {
     DeviceGuard guard(c->device);
     if (c->stream || !c->bufs.empty()) cudaStreamSynchronize(c->stream);
+    if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
     for (auto s : c->side) cudaStreamDestroy(s);
     for (auto ev : c->side_done) cudaEventDestroy(ev);
     if (c->fork) cudaEventDestroy(c->fork);

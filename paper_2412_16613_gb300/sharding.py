@@ -33,25 +33,35 @@ def weak_shard(runs_per_rank: int, rank: int) -> tuple[int, int]:
     return rank * runs_per_rank, runs_per_rank
 
 
-# counter indices whose combination over ranks is a maximum rather than a sum (the longest group,
-# the layout)
-MAX_COUNTERS = (8, 9)
+# counter indices whose combination over ranks is a maximum (the longest group) or a bitwise or
+# (the layouts that ran) rather than a sum
+MAX_COUNTERS = (8,)
+OR_COUNTERS = (9,)
 
 
 def combine(hist: np.ndarray, counters: np.ndarray, dist=None):
     """Sum histograms and counters over the ranks of `dist` (torch.distributed), taking the
-    maximum for the longest-group counter.  Returns numpy arrays (unchanged without dist)."""
+    maximum for the longest-group counter and the bitwise or for the layout counter.  Returns
+    numpy arrays (unchanged without dist)."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
         return hist, counters
     import torch
+    counters = np.asarray(counters, dtype=np.uint64)
     h = torch.from_numpy(np.ascontiguousarray(hist, dtype=np.float64))
     c = torch.from_numpy(np.ascontiguousarray(counters, dtype=np.float64))
     cmax = c.clone()
+    # the or of small bit sets as a maximum per bit
+    bits = torch.tensor([float((int(counters[i]) >> b) & 1) for i in OR_COUNTERS if i < len(counters)
+                         for b in range(8)], dtype=torch.float64)
     dist.all_reduce(h)
     dist.all_reduce(c)
     dist.all_reduce(cmax, op=dist.ReduceOp.MAX)
+    if bits.numel():
+        dist.all_reduce(bits, op=dist.ReduceOp.MAX)
     out_c = c.numpy().copy()
     for i in MAX_COUNTERS:
         if i < len(out_c):
             out_c[i] = cmax[i].item()
+    for j, i in enumerate(k for k in OR_COUNTERS if k < len(out_c)):
+        out_c[i] = sum(int(bits[8 * j + b].item()) << b for b in range(8))
     return h.numpy().astype(np.uint64), out_c.astype(np.uint64)

@@ -36,7 +36,7 @@ def declared_functions():
 def test_headers_declare_the_boundary():
     names = declared_functions()
     for n in ["ssa_create", "ssa_create_batch", "ssa_run", "ssa_fetch", "ssa_destroy", "ssa_last_error",
-              "ssa_set_allocator", "ssa_default_options", "ssa_field_bytes", "ssa_version",
+              "ssa_set_allocator", "ssa_default_options", "ssa_field_bytes", "ssa_version", "ssa_tune",
               "bitssa_test_philox", "bitssa_test_bitslice", "bitssa_bench_alu"]:
         assert n in names, n
 

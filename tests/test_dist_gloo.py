@@ -31,6 +31,7 @@ def _oracle_shard(first, n):
     counters[2] = r["reactions"].sum()
     counters[5] = (r["outcome"] >= 0).sum()
     counters[8] = r["steps"].max() if n else 0
+    counters[9] = 1 if first == 0 else 2  # stands in for the layout each rank ran
     return hist, counters, r
 
 
@@ -67,6 +68,7 @@ def test_two_gloo_ranks_equal_one_process(tmp_path):
     mp.start_processes(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
     whole_hist, whole_counters, whole = _oracle_shard(0, N_RUNS)
     parts = [np.load(os.path.join(tmp_path, f"rank{r}.npz")) for r in range(2)]
+    whole_counters[9] = 3  # rank 0 ran layout bit 0, rank 1 layout bit 1
     for p in parts:
         assert np.array_equal(p["hist"], whole_hist)
         assert np.array_equal(p["counters"], whole_counters)

@@ -91,3 +91,26 @@ def test_batch_equals_separate_contexts(precision, layout):
         assert np.array_equal(g["outcome"][sl], one["outcome"])
         assert np.array_equal(g["t_abs"][sl], one["t_abs"])
         assert np.array_equal(g["ee_hist"][e], one["ee_hist"].reshape(len(snaps), 65))
+
+
+def test_batch_graph_replay_and_recapture():
+    """A batch is one captured graph per launch plan: a second run replays it, a run with other
+    snapshot times records a new one; every output equals a fresh context's."""
+    import torch
+    ens = workloads.batch_ensembles(n_ens=9, runs=64, n_min=8, n_max=3000, seed=5)
+    o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), keep_snap_counts=1)
+    ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, ens["init"], ens["rates"], ens["runs"],
+                               ens["seeds"], o)
+    try:
+        outs = []
+        for snaps in ([0.01, 0.1], [0.01, 0.1], [0.002, 0.02, 0.2]):
+            pkg.ssa_run(ctx, 1.0, snaps)
+            outs.append((snaps, pkg.fetch_all(ctx, snapshots=True)))
+    finally:
+        pkg.ssa_destroy(ctx)
+    for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
+        assert np.array_equal(outs[0][1][k], outs[1][1][k]), k
+    fresh = run_batch(ens, 1.0, outs[2][0])
+    for k in ("final_counts", "outcome", "t_abs"):
+        assert np.array_equal(outs[2][1][k], fresh[k]), k
+    assert np.array_equal(outs[2][1]["ee_hist"].reshape(fresh["ee_hist"].shape), fresh["ee_hist"])

@@ -319,3 +319,30 @@ def test_thread_per_run_baseline_distribution():
     se = math.sqrt(g["t_abs"].var() / n + r["t_abs"].var() / len(r["t_abs"]))
     assert abs(g["t_abs"].mean() - r["t_abs"].mean()) < 5 * se
     assert g["counters"]["reactions"] > 0
+
+
+def test_tuner_keeps_the_runs():
+    """ssa_tune times each configuration and keeps the fastest; the runs after it equal an
+    untuned context's, and the choice is one of the offered configurations."""
+    import torch
+    snaps = [0.01, 0.1]
+    base = gpu_run((64, 64, 128), 3000, seed=8, t_end=1.0, snaps=snaps)
+    o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), keep_snap_counts=1)
+    ctx = pkg.ssa_create(FRANK_R, FRANK_P, [1, 1, 1], (64, 64, 128), 3000, 8, o)
+    try:
+        for probe in (200, 0):
+            layout, block = pkg.ssa_tune(ctx, 1.0, snaps, probe_steps=probe)
+            assert (layout, block) in [(pkg.SSA_LAYOUT_AUTO, 64), (pkg.SSA_LAYOUT_THREAD, 32),
+                                       (pkg.SSA_LAYOUT_THREAD, 64), (pkg.SSA_LAYOUT_THREAD, 128),
+                                       (pkg.SSA_LAYOUT_WARPS, 64)]
+            with pytest.raises(pkg.SSAError) as ei:
+                pkg.ssa_fetch(ctx, pkg.SSA_FIELD_FINAL_COUNTS)
+            assert ei.value.status == pkg.SSA_ESTATE
+            pkg.ssa_run(ctx, 1.0, snaps)
+            g = pkg.fetch_all(ctx, snapshots=True)
+            g["snap_counts"] = g["snap_counts"].reshape(len(snaps), 3000, 3)
+            for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
+                assert np.array_equal(g[k], base[k]), (probe, k)
+            assert same_counters(g, base)
+    finally:
+        pkg.ssa_destroy(ctx)
