@@ -195,6 +195,49 @@ __device__ __forceinline__ bool clock_crosses(const Clock<false>& nx, int precis
   return (precision == kP32Kahan || precision == kP32Plain) ? nx.t_f > nx.th_f : nx.t > nx.th_t;
 }
 
+// Thinning (k_r < k_max, step (4) below): a drawn reaction is kept iff the q-bit uniform U is
+// below T_r.  U is read most significant bit first, from words W0..W1-1 of the step's block
+// (`word_at(k)`) and then from further calls of the same stream from call `next_call` on,
+// stopping once every lane is decided.
+template <int W0, int W1, typename WordAt>
+__device__ __forceinline__ void thin_step(const Ensemble& e, WordAt word_at, uint32_t live, uint32_t sgroup,
+                                          unsigned long long step, uint32_t next_call, PhiloxKey key,
+                                          uint32_t& x1, uint32_t& x2, uint32_t& x3) {
+  const uint32_t alw1 = (e.thin_always & 1u) ? ~0u : 0u;
+  const uint32_t alw2 = (e.thin_always & 2u) ? ~0u : 0u;
+  const uint32_t alw3 = (e.thin_always & 4u) ? ~0u : 0u;
+  const uint32_t tested = (x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3);
+  uint32_t und = tested & live;
+  uint32_t rej = tested & ~live;
+  const int q = e.thin_bits;
+  auto bit = [&](int i, uint32_t word) {
+    const int pos = q - 1 - i;
+    const uint32_t b1 = 0u - (uint32_t)(((unsigned long long)e.thin_T[0] >> pos) & 1ull);
+    const uint32_t b2 = 0u - (uint32_t)(((unsigned long long)e.thin_T[1] >> pos) & 1ull);
+    const uint32_t b3 = 0u - (uint32_t)(((unsigned long long)e.thin_T[2] >> pos) & 1ull);
+    const uint32_t tb = (x1 & b1) | (x2 & b2) | (x3 & b3);
+    const uint32_t lower = und & ~word & tb;   // U < T decided
+    const uint32_t higher = und & word & ~tb;  // U > T decided
+    rej |= higher;
+    und &= ~(lower | higher);
+  };
+#pragma unroll
+  for (int k = W0; k < W1; ++k)
+    if (k - W0 < q) bit(k - W0, word_at(k));
+  int i = W1 - W0;
+  for (uint32_t c = next_call; und != 0u && i < q; ++c) {
+    const uint4 r = philox4x32_10(stream_counter(sgroup, step, 0u, 0u, c), key);
+    const uint32_t wv[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (i < q) bit(i++, wv[j]);
+  }
+  rej |= und;  // U == T: not below
+  x1 &= ~rej;
+  x2 &= ~rej;
+  x3 &= ~rej;
+}
+
 // Everything one thread keeps about its group between steps (all in registers).
 template <int K, bool PROD>
 struct GroupState {
@@ -447,42 +490,9 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   // for every reaction with k_r > 0, so only reactions that thinning rejects can be picked.
   uint32_t x1 = lt1, x2 = lt2 & ~lt1, x3 = lt3 & ~lt2;
 
-  // (4) thinning for k_r < k_max: keep iff U < T_r, U read most significant bit first
-  if (e.thin) {
-    const uint32_t alw1 = (e.thin_always & 1u) ? ~0u : 0u;
-    const uint32_t alw2 = (e.thin_always & 2u) ? ~0u : 0u;
-    const uint32_t alw3 = (e.thin_always & 4u) ? ~0u : 0u;
-    uint32_t und = ((x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3)) & s.live;
-    uint32_t rej = ((x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3)) & ~s.live;
-    const int q = e.thin_bits;
-    int i = 0;
-    auto thin_bit = [&](uint32_t word) {
-      const int pos = q - 1 - i;
-      const uint32_t b1 = 0u - (uint32_t)(((unsigned long long)e.thin_T[0] >> pos) & 1ull);
-      const uint32_t b2 = 0u - (uint32_t)(((unsigned long long)e.thin_T[1] >> pos) & 1ull);
-      const uint32_t b3 = 0u - (uint32_t)(((unsigned long long)e.thin_T[2] >> pos) & 1ull);
-      const uint32_t tb = (x1 & b1) | (x2 & b2) | (x3 & b3);
-      const uint32_t lower = und & ~word & tb;   // U < T decided
-      const uint32_t higher = und & word & ~tb;  // U > T decided
-      rej |= higher;
-      und &= ~(lower | higher);
-      ++i;
-    };
-#pragma unroll
-    for (int k = K + 2; k < 4 * NC0; ++k)
-      if (i < q) thin_bit(w[k]);
-    for (uint32_t c = NC0; und != 0u && i < q; ++c) {
-      const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, c), key);
-      if (i < q) thin_bit(r.x);
-      if (i < q) thin_bit(r.y);
-      if (i < q) thin_bit(r.z);
-      if (i < q) thin_bit(r.w);
-    }
-    rej |= und;  // U == T: not below
-    x1 &= ~rej;
-    x2 &= ~rej;
-    x3 &= ~rej;
-  }
+  // (4) thinning for k_r < k_max
+  if (e.thin)
+    thin_step<K + 2, 4 * NC0>(e, [&](int k) { return w[k]; }, s.live, s.sgroup, s.step, NC0, key, x1, x2, x3);
 
   // (5) updates from the counts before the reaction (App. B).  A step in which no lane
   // fires (frequent once most lanes of a group have absorbed) changes nothing.

@@ -462,41 +462,8 @@ __global__ void __launch_bounds__(kTrioBlock, trio_min_blocks(K))
     if (go) {
       const uint32_t lt1 = sh.lt[0][lane], lt2 = sh.lt[1][lane], lt3 = sh.lt[2][lane];
       uint32_t x1 = lt1, x2 = lt2 & ~lt1, x3 = lt3 & ~lt2;
-      if (e.thin) {  // keep iff U < T_r, U read most significant bit first
-        const uint32_t alw1 = (e.thin_always & 1u) ? ~0u : 0u;
-        const uint32_t alw2 = (e.thin_always & 2u) ? ~0u : 0u;
-        const uint32_t alw3 = (e.thin_always & 4u) ? ~0u : 0u;
-        uint32_t und = ((x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3)) & s.live;
-        uint32_t rej = ((x1 & ~alw1) | (x2 & ~alw2) | (x3 & ~alw3)) & ~s.live;
-        const int q = e.thin_bits;
-        int i = 0;
-        auto thin_bit = [&](uint32_t word) {
-          const int pos = q - 1 - i;
-          const uint32_t b1 = 0u - (uint32_t)(((unsigned long long)e.thin_T[0] >> pos) & 1ull);
-          const uint32_t b2 = 0u - (uint32_t)(((unsigned long long)e.thin_T[1] >> pos) & 1ull);
-          const uint32_t b3 = 0u - (uint32_t)(((unsigned long long)e.thin_T[2] >> pos) & 1ull);
-          const uint32_t tb = (x1 & b1) | (x2 & b2) | (x3 & b3);
-          const uint32_t lower = und & ~word & tb;   // U < T decided
-          const uint32_t higher = und & word & ~tb;  // U > T decided
-          rej |= higher;
-          und &= ~(lower | higher);
-          ++i;
-        };
-#pragma unroll
-        for (int k = K + 2; k < 4 * NC0; ++k)
-          if (i < q) thin_bit(row[k]);
-        for (uint32_t c = NC0; und != 0u && i < q; ++c) {
-          const uint4 r = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, c), key);
-          if (i < q) thin_bit(r.x);
-          if (i < q) thin_bit(r.y);
-          if (i < q) thin_bit(r.z);
-          if (i < q) thin_bit(r.w);
-        }
-        rej |= und;  // U == T: not below
-        x1 &= ~rej;
-        x2 &= ~rej;
-        x3 &= ~rej;
-      }
+      if (e.thin)
+        thin_step<K + 2, 4 * NC0>(e, [&](int k) { return row[k]; }, s.live, s.sgroup, s.step, NC0, key, x1, x2, x3);
       const uint32_t fired = x1 | x2 | x3;
       ++s.step;
       s.buf = s.buf == 2 ? 0 : s.buf + 1;

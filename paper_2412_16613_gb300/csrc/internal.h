@@ -72,6 +72,7 @@ struct Ensemble {
                              // of (n_i | top_mask[i]) is the lanes that pass the pre-check
 };
 
+
 // Fills top_ones and top_mask from lambda_int and K.
 inline void set_precheck(Ensemble& e) {
   e.top_ones = 0u;
