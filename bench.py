@@ -381,6 +381,29 @@ def main():
                      "d2h_bytes_per_step": d2h, "steps": e2e_steps}
     pkg.ssa_destroy(ctx)
 
+    # ---- the per-run snapshot dump (int32[snap][runs][3]) on the same workload: its HBM bytes and
+    # what it adds to the step, outside the timed region
+    if not args.no_baselines and WORKLOAD != "c3":
+        od = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
+                                     keep_snap_counts=1, first_run=first_run, layout=opt.layout,
+                                     block_size=opt.block_size)
+        cd = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
+                            RUNS_PER_GPU, SEED, od)
+        pkg.ssa_run(cd, T_END, SNAPS)
+        torch.cuda.synchronize()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(2)
+        a.record(stream)
+        pkg.ssa_run(cd, T_END, SNAPS)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        msd = a.elapsed_time(b2)
+        dump_bytes = pkg.ssa_field_bytes(cd, pkg.SSA_FIELD_SNAP_COUNTS)
+        pkg.ssa_destroy(cd)
+        result["snapshot_dump"] = {"bytes_per_step": dump_bytes, "ms_per_step": msd,
+                                   "hbm_gbs_over_step": dump_bytes / (msd / 1e3) / 1e9,
+                                   "added_ms": msd - result["ms_per_step"]}
+
     # ---- the one-thread-per-run GPU baseline on the same workload and precision
     if not args.no_baselines and WORKLOAD != "c3":
         o7 = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,

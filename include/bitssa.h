@@ -103,7 +103,13 @@ typedef struct {
   void* cuda_stream;         /* cudaStream_t to use; NULL = the legacy default stream */
   int32_t device;            /* CUDA device ordinal, -1 = the current device */
   int32_t layout;            /* SSA_LAYOUT_AUTO (default) | SSA_LAYOUT_THREAD | SSA_LAYOUT_WARPS */
-  int32_t reserved[6];
+  int32_t shared_n;          /* 0 (default): every run draws its own n.  1: the paper's shared draw
+                                (Sec. 4, step a): all 32 runs of a group use the n of the group's
+                                run 0, drawn and redrawn whether or not that run is still live; with
+                                identical initial states the runs of a group are then identical,
+                                so it is meant for per-run initial states (n0_per_run = 1).
+                                Bit-sliced engine only. */
+  int32_t reserved[5];
 } ssa_options;
 
 /* Fields for ssa_fetch.  n_runs = the context's total number of runs (for a batch,

@@ -287,9 +287,10 @@ int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index, const
      * bit where it differs from lambda_int (all bits when it equals lambda_int), and keeps
      * the bits below p: they are uniform and independent of the rejection, so the new
      * draw is again uniform on [0, 2^K) and the accepted one uniform on [0, lambda_int). */
+    const int n_lane = p->shared_n ? 0 : lane;  /* whose bits make n */
     uint64_t draw = 0;
     for (int i = 0; i < K; i++)
-      draw |= (uint64_t)lane_bit(word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)i), lane) << i;
+      draw |= (uint64_t)lane_bit(word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)i), n_lane) << i;
     uint32_t attempt = 0;
     while (draw >= d->lambda_int) {
       attempt++;
@@ -298,7 +299,7 @@ int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index, const
       draw &= ((uint64_t)1 << from) - 1;
       for (int i = from; i < K; i++)
         draw |= (uint64_t)lane_bit(word_at(&ws, group, (uint64_t)step, attempt, 0, (uint32_t)i),
-                                   lane) << i;
+                                   n_lane) << i;
     }
     out->redraws += attempt;
 

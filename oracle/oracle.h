@@ -71,6 +71,8 @@ typedef struct {
   const double* snap_times; /* [n_snap] ascending, <= t_end (may be NULL if n_snap == 0) */
   int32_t n_snap;
   int64_t step_budget;      /* max steps per run, 0 = unlimited */
+  int32_t shared_n;         /* 1: every run of a group of 32 uses the n of the group's lane 0 (one n
+                               for all copies, Sec. 4 step a), drawn whether or not lane 0 is live */
 } orc_problem;
 
 /* Derived constants of a problem, computed from their definitions. */

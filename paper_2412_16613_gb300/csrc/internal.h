@@ -66,6 +66,7 @@ struct Ensemble {
   unsigned int active;       // bit r: k_r > 0
   int thin;                  // any reaction with k_r < k_max
   int thin_bits;             // q
+  int shared_n;              // 1: every lane of a group uses lane 0's n
   unsigned int top_ones;     // planes of the leading run of ones of lambda_int (bit i = plane i):
                              // n >= lambda_int needs all of them set (0: no pre-check)
   unsigned int top_mask[32]; // per plane: 0 on the run, ~0 elsewhere, so that the AND over planes

@@ -211,6 +211,9 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.precision < 0 || o.precision > 4) return (*why = "unknown precision mode", SSA_EINVAL);
   if (o.engine < 0 || o.engine > 1) return (*why = "unknown engine", SSA_EINVAL);
   if (o.layout < SSA_LAYOUT_AUTO || o.layout > SSA_LAYOUT_WARPS) return (*why = "unknown layout", SSA_EINVAL);
+  if (o.shared_n != 0 && o.shared_n != 1) return (*why = "shared_n must be 0 or 1", SSA_EINVAL);
+  if (o.shared_n && o.engine != SSA_ENGINE_BITSLICED)
+    return (*why = "shared_n is a mode of the bit-sliced engine", SSA_EUNSUPPORTED);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
   if (o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
     return (*why = "block_size must be 0 or a multiple of 32 up to 256", SSA_EINVAL);
@@ -654,6 +657,7 @@ int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_spec
   c->n_runs_total = n_runs;
   c->ens.push_back(make_ensemble(n_tot, shared, canon_rates, c->opt.thin_bits, seed, n_runs, 0,
                                  c->opt.first_run / 32));
+  c->ens.back().shared_n = c->opt.shared_n;
   DeviceGuard guard(c->opt.device);
   if ((st = setup_device(c)) != SSA_OK) return bail(st, c->err);
   if ((st = allocate_common(c, rows)) != SSA_OK) {
@@ -701,6 +705,7 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
     if (tot > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
     const double* k = rates_ens + 3 * e;
     c->ens.push_back(make_ensemble(tot, canon, k, c->opt.thin_bits, seed_ens[e], runs_ens[e], offset, 0));
+    c->ens.back().shared_n = c->opt.shared_n;
     c->rates.insert(c->rates.end(), k, k + 3);
     offset += runs_ens[e];
     order.push_back({std::max(1, c->ens.back().K), e});

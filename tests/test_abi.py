@@ -80,6 +80,9 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
     (dict(reac=F_R, prod=F_P, precision=7), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, block_size=48), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, first_run=16), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, layout=3), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, shared_n=2), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, shared_n=1, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
     (dict(reac=[[1, 0, 1], [0, 1, 1]], prod=[[2, 0, 0], [0, 2, 0]]), pkg.SSA_EUNSUPPORTED),  # not Frank
     (dict(reac=[[1, 1, 0], [0, 1, 1], [1, 0, 1]], prod=[[0, 0, 2], [0, 2, 0], [2, 0, 0]]),
      pkg.SSA_EUNSUPPORTED),                                                           # Frank, wrong order

@@ -346,3 +346,26 @@ def test_tuner_keeps_the_runs():
             assert same_counters(g, base)
     finally:
         pkg.ssa_destroy(ctx)
+
+
+@LAYOUTS
+def test_parity_shared_n(layout):
+    """The paper's shared draw (one n per group, Sec. 4 step a) against the oracle, with
+    multinomial initial states per run (Sec. 5, Fig. 4) and a thinned rate."""
+    rng = np.random.default_rng(31)
+    n = 1024 + 7
+    init = rng.multinomial(512, [0.25, 0.25, 0.5], size=n)
+    snaps = [0.005, 0.05, 0.5]
+    for rates in ((1.0, 1.0, 1.0), (1.0, 0.6, 1.0)):
+        g = gpu_run(init, n, seed=13, t_end=2.0, snaps=snaps, rates=rates, shared_n=1, layout=layout)
+        r = oracle.run(oracle.frank(*rates), init, seed=13, t_end=2.0, snap_times=snaps, shared_n=True,
+                       threads=THREADS)
+        assert_parity(g, r)
+
+
+def test_shared_n_identical_start_gives_identical_lanes():
+    g = gpu_run((64, 64, 128), 128, seed=2, t_end=3.0, snaps=[0.1], shared_n=1)
+    for grp in range(4):
+        sl = slice(32 * grp, 32 * grp + 32)
+        assert np.all(g["final_counts"][sl] == g["final_counts"][32 * grp])
+        assert np.all(g["t_abs"][sl] == g["t_abs"][32 * grp])

@@ -234,15 +234,17 @@ def _frank_me(N, rates=(1.0, 1.0, 1.0)):
     return me.generator(FRANK_REAC, FRANK_PROD, list(rates), N)
 
 
-@pytest.mark.parametrize("lane", [0, 17])
-def test_master_equation_distribution(orc, lane):
+@pytest.mark.parametrize("lane,shared", [(0, False), (17, False), (17, True)])
+def test_master_equation_distribution(orc, lane, shared):
+    """Each lane is an exact sample path, also when it reacts to the n of its group's lane 0
+    (one n for all copies, Sec. 4 step a): n never depends on the state."""
     N, init = 12, (3, 3, 6)
     st, index, Q = _frank_me(N)
     snaps = [0.02, 0.05, 0.1, 0.2, 0.4]
     runs = 40_000
     # one lane per group: groups draw from independent counters
     r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32 + lane, seed=21, t_end=0.5,
-                snap_times=snaps)
+                snap_times=snaps, shared_n=shared)
     p0 = np.zeros(len(st))
     p0[index[init]] = 1.0
     for s, t in enumerate(snaps):
@@ -259,6 +261,27 @@ def test_master_equation_distribution(orc, lane):
             e *= o.sum() / e.sum()
         stat, pval = stats.power_divergence(o, e, lambda_="log-likelihood")
         assert pval > 1e-4, (t, pval)
+
+
+def test_shared_n_lanes_follow_one_draw(orc):
+    """Shared n: from one initial state every lane of a group repeats lane 0's run (the reason
+    the paper's shared draw needs distinct initial states); lane 0 itself is the run it is
+    without sharing; with per-run initial states the lanes differ and each conserves N."""
+    r = orc.run(orc.frank(), (40, 40, 80), 96, seed=3, t_end=5.0, shared_n=True)
+    for g in range(3):
+        sl = slice(32 * g, 32 * g + 32)
+        assert np.all(r["final_counts"][sl] == r["final_counts"][32 * g])
+        assert np.all(r["t_abs"][sl] == r["t_abs"][32 * g]) and np.all(r["steps"][sl] == r["steps"][32 * g])
+    rng = np.random.default_rng(4)
+    init = rng.multinomial(160, [0.25, 0.25, 0.5], size=96)
+    a = orc.run(orc.frank(), init, seed=3, t_end=5.0, shared_n=True)
+    b = orc.run(orc.frank(), init, seed=3, t_end=5.0, shared_n=False)
+    for g in range(3):
+        assert np.array_equal(a["final_counts"][32 * g], b["final_counts"][32 * g])
+        assert a["t_abs"][32 * g] == b["t_abs"][32 * g] or (np.isinf(a["t_abs"][32 * g]) and np.isinf(b["t_abs"][32 * g]))
+        assert a["steps"][32 * g] == b["steps"][32 * g]
+    assert np.all(a["final_counts"].sum(1) == 160)
+    assert len({tuple(x) for x in a["final_counts"][:32]}) > 1
 
 
 def test_master_equation_absorption(orc):
