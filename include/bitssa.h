@@ -108,7 +108,8 @@ typedef struct {
                                 run 0, drawn and redrawn whether or not that run is still live; with
                                 identical initial states the runs of a group are then identical,
                                 so it is meant for per-run initial states (n0_per_run = 1).
-                                Bit-sliced engine only. */
+                                Bit-sliced engine, three-warp layout (SSA_LAYOUT_AUTO takes it;
+                                SSA_LAYOUT_THREAD gives SSA_EUNSUPPORTED). */
   int32_t reserved[5];
 } ssa_options;
 

@@ -272,57 +272,25 @@ __device__ __forceinline__ uint32_t live_lanes(const GroupState<K, PROD>& s, con
   return m;
 }
 
-// One group's lanes into snapshot `snap`: the histogram bin of each valid lane and, when the
-// per-run dump is kept, its counts in the caller's species order.  `counts(l, cl, cd, ca)` reads
-// lane l.  The dump rows of four consecutive runs are 12 ints: written as three 16-byte stores
-// where the destination is 16-byte aligned, else int by int.  (Three species: the runtime
-// accepts Frank's model only.)
-template <typename Counts>
-__device__ __forceinline__ void capture_group(const FrankLaunch& p, int ens, long long row0, int nvalid, int snap,
-                                              unsigned int* s_hist, Counts counts) {
-  // caller's species k holds canonical species inv[k]
-  const int inv0 = p.perm[0] == 0 ? 0 : (p.perm[1] == 0 ? 1 : 2);
-  const int inv1 = p.perm[0] == 1 ? 0 : (p.perm[1] == 1 ? 1 : 2);
-  const int inv2 = p.perm[0] == 2 ? 0 : (p.perm[1] == 2 ? 1 : 2);
-  int* base = p.snap_counts ? p.snap_counts + ((long long)snap * p.n_runs_total + row0) * 3 : nullptr;
-  for (int l0 = 0; l0 < nvalid; l0 += 4) {
-    int v[12];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int c[3] = {0, 0, 0};
-      if (l0 + j < nvalid) {
-        counts(l0 + j, c[0], c[1], c[2]);
-        if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(c[0], c[1])], 1u);
-        else atomicAdd(&p.hist[((long long)ens * p.n_snap + snap) * kHistBins + ee_bin(c[0], c[1])], 1ull);
-      }
-      v[3 * j] = inv0 == 0 ? c[0] : (inv0 == 1 ? c[1] : c[2]);
-      v[3 * j + 1] = inv1 == 0 ? c[0] : (inv1 == 1 ? c[1] : c[2]);
-      v[3 * j + 2] = inv2 == 0 ? c[0] : (inv2 == 1 ? c[1] : c[2]);
-    }
-    if (base) {
-      int* o = base + 3 * l0;
-      if (l0 + 4 <= nvalid && ((uintptr_t)o & 15u) == 0u) {
-        uint4* o4 = reinterpret_cast<uint4*>(o);
-        o4[0] = make_uint4(v[0], v[1], v[2], v[3]);
-        o4[1] = make_uint4(v[4], v[5], v[6], v[7]);
-        o4[2] = make_uint4(v[8], v[9], v[10], v[11]);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 12; ++k)
-          if (l0 + k / 3 < nvalid) o[k] = v[k];
-      }
-    }
-  }
-}
-
-// The current state of every valid lane into snapshot `snap`.
+// The current state of every valid lane into snapshot `snap`: histogram and per-run counts.
+// Lane by lane with plain stores: staging four runs (12 ints) for 16-byte stores was tried and
+// cost the step loop registers it does not have, for a path taken ten times per group.
 template <int K, bool PROD>
 __device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K, PROD>& s, const Ensemble& e,
                                         int snap, unsigned int* s_hist) {
   using Sh = FrankShape<K>;
-  capture_group(p, s.ens, group_row0(s, e), s.nvalid, snap, s_hist, [&](int l, int& cl, int& cd, int& ca) {
+  for (int l = 0; l < s.nvalid; ++l) {
+    int cl, cd, ca;
     lane_counts<Sh::B, Sh::WP>(s.L, s.U, e.n_tot, l, cl, cd, ca);
-  });
+    if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(cl, cd)], 1u);
+    else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + ee_bin(cl, cd)], 1ull);
+    if (p.snap_counts) {
+      int* o = p.snap_counts + ((long long)snap * p.n_runs_total + group_row0(s, e) + l) * p.n_species;
+      o[p.perm[0]] = cl;
+      o[p.perm[1]] = cd;
+      o[p.perm[2]] = ca;
+    }
+  }
 }
 
 // Set up group `group_local` of ensemble `e`: initial planes, cumulative propensities by
@@ -457,8 +425,6 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   // together, and redo the comparators only in the rare step where a lane redraws
   // n >= lambda_int needs every plane of lambda_int's leading run of ones set in n: test that
   // first (a shallow AND tree), and run the full comparison only when some lane passes
-  // the lanes whose n is drawn: the live ones, or lane 0 alone when the group shares one n
-  const uint32_t draw_lanes = e.shared_n ? 1u : s.live;
   uint32_t need = 0u;
   {
     uint32_t a[K];
@@ -471,7 +437,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
         a[j] = a[3 * j] & (3 * j + 1 < width ? a[3 * j + 1] : 0xFFFFFFFFu) &
                (3 * j + 2 < width ? a[3 * j + 2] : 0xFFFFFFFFu);
     }
-    if (a[0] & draw_lanes) need = ~bs::less_than_const(n, e.lambda_int) & draw_lanes;
+    if (a[0] & s.live) need = ~bs::less_than_const(n, e.lambda_int) & s.live;
   }
   uint32_t lt1 = bs::less_than(n, s.S1);
   uint32_t lt2 = bs::less_than(n, s.S2);
@@ -501,13 +467,6 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
       }
       need &= ~bs::less_than_const(n, e.lambda_int);
     }
-    lt1 = bs::less_than(n, s.S1);
-    lt2 = bs::less_than(n, s.S2);
-    lt3 = bs::less_than(n, s.S3);
-  }
-  if (e.shared_n) {  // every lane takes lane 0's n (Sec. 4, step a: one n for all copies)
-#pragma unroll
-    for (int i = 0; i < K; ++i) n[i] = 0u - (n[i] & 1u);
     lt1 = bs::less_than(n, s.S1);
     lt2 = bs::less_than(n, s.S2);
     lt3 = bs::less_than(n, s.S3);

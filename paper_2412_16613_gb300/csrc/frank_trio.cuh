@@ -111,8 +111,19 @@ __device__ __forceinline__ void trio_lane_counts(const TrioState<K>& s, int n_to
 template <int K>
 __device__ __forceinline__ void trio_capture(const FrankLaunch& p, const TrioState<K>& s, const Ensemble& e,
                                              int snap, unsigned int* s_hist) {
-  capture_group(p, s.ens, trio_row0(s, e), s.nvalid, snap, s_hist,
-                [&](int l, int& cl, int& cd, int& ca) { trio_lane_counts(s, e.n_tot, l, cl, cd, ca); });
+  const long long row0 = trio_row0(s, e);
+  for (int l = 0; l < s.nvalid; ++l) {
+    int cl, cd, ca;
+    trio_lane_counts(s, e.n_tot, l, cl, cd, ca);
+    if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(cl, cd)], 1u);
+    else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + ee_bin(cl, cd)], 1ull);
+    if (p.snap_counts) {
+      int* o = p.snap_counts + ((long long)snap * p.n_runs_total + row0 + l) * p.n_species;
+      o[p.perm[0]] = cl;
+      o[p.perm[1]] = cd;
+      o[p.perm[2]] = ca;
+    }
+  }
 }
 
 // out = a + b + cin over W planes, the operands given plane by plane.
@@ -487,10 +498,12 @@ __global__ void __launch_bounds__(kTrioBlock, trio_min_blocks(K))
       }
       if (live_writer) {
         uint32_t fail = 0u;
+        // the paper's shared draw (Sec. 4, step a): lane 0's n, redrawn whether or not lane 0 is
+        // live, then copied to every lane
         if (now_live && !(p.step_budget > 0 && (long long)s.step >= p.step_budget))
           fail = trio_redraw<K>(row_next, e, s.sgroup, s.step, e.shared_n ? 1u : now_live, key, sh.redraws[lane])
                      ? 0u : 1u;
-        if (e.shared_n)  // every lane takes lane 0's n (Sec. 4, step a: one n for all copies)
+        if (e.shared_n)
           for (int i = 0; i < K; ++i) row_next[i] = 0u - (row_next[i] & 1u);
         sh.ahead_fail[lane] = fail;
       }

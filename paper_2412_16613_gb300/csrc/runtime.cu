@@ -214,6 +214,8 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.shared_n != 0 && o.shared_n != 1) return (*why = "shared_n must be 0 or 1", SSA_EINVAL);
   if (o.shared_n && o.engine != SSA_ENGINE_BITSLICED)
     return (*why = "shared_n is a mode of the bit-sliced engine", SSA_EUNSUPPORTED);
+  if (o.shared_n && o.layout == SSA_LAYOUT_THREAD)
+    return (*why = "shared_n runs on the three-warp layout", SSA_EUNSUPPORTED);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
   if (o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
     return (*why = "block_size must be 0 or a multiple of 32 up to 256", SSA_EINVAL);
@@ -414,6 +416,7 @@ bool use_warps_layout(const ssa_options& o, long long groups, int sm_count) {
 // The layout of one launch of a context: a fixed option wins, then the tuner's choice, then the
 // rule above.
 bool ctx_warps(const ssa_ctx* c, long long groups) {
+  if (c->opt.shared_n) return true;  // the shared draw is built into the three-warp layout only
   if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_THREAD) return false;
   if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_WARPS) return true;
   return use_warps_layout(c->opt, groups, c->sm_count);

@@ -348,10 +348,11 @@ def test_tuner_keeps_the_runs():
         pkg.ssa_destroy(ctx)
 
 
-@LAYOUTS
+@pytest.mark.parametrize("layout", [pkg.SSA_LAYOUT_AUTO, pkg.SSA_LAYOUT_WARPS], ids=["auto", "warps"])
 def test_parity_shared_n(layout):
     """The paper's shared draw (one n per group, Sec. 4 step a) against the oracle, with
-    multinomial initial states per run (Sec. 5, Fig. 4) and a thinned rate."""
+    multinomial initial states per run (Sec. 5, Fig. 4) and a thinned rate; it runs on the
+    three-warp layout, which the automatic choice takes for it."""
     rng = np.random.default_rng(31)
     n = 1024 + 7
     init = rng.multinomial(512, [0.25, 0.25, 0.5], size=n)
@@ -365,6 +366,7 @@ def test_parity_shared_n(layout):
 
 def test_shared_n_identical_start_gives_identical_lanes():
     g = gpu_run((64, 64, 128), 128, seed=2, t_end=3.0, snaps=[0.1], shared_n=1)
+    assert g["counters"]["layout"] == pkg.SSA_LAYOUT_WARPS
     for grp in range(4):
         sl = slice(32 * grp, 32 * grp + 32)
         assert np.all(g["final_counts"][sl] == g["final_counts"][32 * grp])
