@@ -114,3 +114,27 @@ def test_batch_graph_replay_and_recapture():
     for k in ("final_counts", "outcome", "t_abs"):
         assert np.array_equal(outs[2][1][k], fresh[k]), k
     assert np.array_equal(outs[2][1]["ee_hist"].reshape(fresh["ee_hist"].shape), fresh["ee_hist"])
+
+
+def test_batch_on_the_legacy_default_stream_and_tuned():
+    """A batch on the legacy default stream (which cannot be captured) launches directly; a tuned
+    batch context keeps its runs."""
+    ens = workloads.batch_ensembles(n_ens=5, runs=96, n_min=10, n_max=4000, seed=8)
+    snaps = [0.01, 0.1]
+    ref = run_batch(ens, 1.0, snaps)
+    o = pkg.ssa_default_options(cuda_stream=None, keep_snap_counts=1)
+    ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, ens["init"], ens["rates"], ens["runs"],
+                               ens["seeds"], o)
+    try:
+        pkg.ssa_run(ctx, 1.0, snaps)
+        a = pkg.fetch_all(ctx, snapshots=True)
+        choice = pkg.ssa_tune(ctx, 1.0, snaps, probe_steps=300)
+        assert choice[0] in (pkg.SSA_LAYOUT_AUTO, pkg.SSA_LAYOUT_THREAD, pkg.SSA_LAYOUT_WARPS)
+        pkg.ssa_run(ctx, 1.0, snaps)
+        b = pkg.fetch_all(ctx, snapshots=True)
+    finally:
+        pkg.ssa_destroy(ctx)
+    for out in (a, b):
+        for k in ("final_counts", "outcome", "t_abs"):
+            assert np.array_equal(out[k], ref[k]), k
+        assert np.array_equal(out["ee_hist"].reshape(ref["ee_hist"].shape), ref["ee_hist"])
