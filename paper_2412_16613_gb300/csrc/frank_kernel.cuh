@@ -456,14 +456,36 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
         return;
       }
       ++s.redraws;
-      uint32_t wr[4 * NCR];  // all calls of the attempt at once: their chains interleave
-      philox4x32_10_block<NCR>(wr, stream_counter(s.sgroup, s.step, attempt, 0u, 0u), 0u, key);
       uint32_t above = 0u;
+      if constexpr (K >= 25) {
+        // wide n: the calls from the top, two at a time, while some lane replaces a lower plane
 #pragma unroll
-      for (int i = K - 1; i >= 0; --i) {
-        const uint32_t m = need & ~above;
-        above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
-        n[i] = (n[i] & ~m) | (wr[i] & m);
+        for (int c = NCR - 1; c >= 0; c -= 2) {
+          if (need & ~above) {
+            constexpr int kPair = 2;
+            const int lo = c > 0 ? c - 1 : 0;
+            uint32_t wr[4 * kPair];
+            philox4x32_10_block<kPair>(wr, stream_counter(s.sgroup, s.step, attempt, 0u, 0u), (uint32_t)lo, key);
+#pragma unroll
+            for (int j = 4 * kPair - 1; j >= 0; --j) {
+              const int i = 4 * lo + j;
+              if (i <= 4 * c + 3 && i < K) {
+                const uint32_t m = need & ~above;
+                above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
+                n[i] = (n[i] & ~m) | (wr[j] & m);
+              }
+            }
+          }
+        }
+      } else {
+        uint32_t wr[4 * NCR];  // all calls of the attempt at once: their chains interleave
+        philox4x32_10_block<NCR>(wr, stream_counter(s.sgroup, s.step, attempt, 0u, 0u), 0u, key);
+#pragma unroll
+        for (int i = K - 1; i >= 0; --i) {
+          const uint32_t m = need & ~above;
+          above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
+          n[i] = (n[i] & ~m) | (wr[i] & m);
+        }
       }
       need &= ~bs::less_than_const(n, e.lambda_int);
     }

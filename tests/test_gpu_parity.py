@@ -371,3 +371,19 @@ def test_shared_n_identical_start_gives_identical_lanes():
         sl = slice(32 * grp, 32 * grp + 32)
         assert np.all(g["final_counts"][sl] == g["final_counts"][32 * grp])
         assert np.all(g["t_abs"][sl] == g["t_abs"][32 * grp])
+
+
+@LAYOUTS
+@pytest.mark.parametrize("N,rates", [(46400, (1.0, 1.0, 1.0)), (10000, (0.7, 1.3, 1.9)), (65536, (1.0, 1.0, 1.0))])
+def test_parity_wide_n(N, rates, layout):
+    """K = 26..31: the wide-n redraw (calls from the top, two at a time), including N_tot = 46 400,
+    where half of all draws are rejected, against the oracle over ~10^4 steps per run."""
+    init = (N // 4, N // 4, N - 2 * (N // 4))
+    lam = N * (N - 1) / 2 * max(rates)
+    t_end = 1.2e4 / lam
+    snaps = [t_end / 3, 2 * t_end / 3]
+    n = 96 + 5
+    g = gpu_run(init, n, seed=17, t_end=t_end, snaps=snaps, rates=rates, layout=layout)
+    r = oracle.run(oracle.frank(*rates), init, n, seed=17, t_end=t_end, snap_times=snaps, threads=THREADS)
+    assert_parity(g, r)
+    assert g["counters"]["redraw_rounds"] > 0
