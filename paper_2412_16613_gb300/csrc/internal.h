@@ -81,6 +81,14 @@ inline void set_precheck(Ensemble& e) {
   for (int i = 0; i < 32; ++i) e.top_mask[i] = ((e.top_ones >> i) & 1u) ? 0u : 0xFFFFFFFFu;
 }
 
+// Per-ensemble constants of Frank's model in the kernel's species order (L, D, A) from their
+// definitions: lambda_int = N (N - 1) / 2, K = its bit length, the pre-check masks, the
+// thinning thresholds T_r = floor(k_r / k_max 2^q).
+Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], int q, unsigned long long seed,
+                       long long n_runs, long long run_offset, long long group_base);
+// The crossing threshold of time t for total rate lambda, in every form a clock compares.
+Threshold make_threshold(double t, double lambda);
+
 // One launch of the bit-sliced kernel for one K.
 struct FrankLaunch {
   Ensemble ens;                   // used when ens_table == nullptr (one ensemble)

@@ -68,43 +68,6 @@ int scratch_for_current_device(NoAllocScratch** out) {
   return SSA_OK;
 }
 
-int bitlen64(unsigned long long v) {
-  int b = 0;
-  while (v) {
-    ++b;
-    v >>= 1;
-  }
-  return b;
-}
-
-// Crossing threshold of time t for total rate lambda (the same forms the kernel reads).
-Threshold threshold_of(double t, double lambda) {
-  Threshold h;
-  std::memset(&h, 0, sizeof h);
-  h.t = t;
-  float f = (float)t;
-  if ((double)f > t) f = std::nextafter(f, -INFINITY);
-  h.t_f = f;
-  if (std::isinf(t) || !(lambda > 0.0)) {
-    h.E = LLONG_MIN;
-    h.M = 1ull << 63;
-    return h;
-  }
-  const double theta = -lambda * t;
-  long long E = (long long)std::floor(theta / M_LN2);
-  double m = std::exp(theta - (double)E * M_LN2);
-  while (m >= 2.0) {
-    m *= 0.5;
-    ++E;
-  }
-  while (m < 1.0) {
-    m *= 2.0;
-    --E;
-  }
-  h.E = E;
-  h.M = (unsigned long long)std::ldexp(m, 63);  // m in [1, 2): exact
-  return h;
-}
 
 }  // namespace
 
@@ -148,31 +111,11 @@ extern "C" int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int
   if (n_snap > 0 && !ee_hist) return noalloc_fail(SSA_EINVAL, "ee_hist is required when n_snap > 0");
 
   // ---- the ensemble (Frank's model in species order L, D, A)
-  Ensemble en;
-  std::memset(&en, 0, sizeof en);
-  en.seed = seed;
-  en.n_runs = n_runs;
-  const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
-  en.lambda_int = (unsigned int)lam;
-  en.K = bitlen64(lam);
-  set_precheck(en);
-  en.n_tot = (int)n_tot;
-  en.lambda = kmax * (double)lam;
-  en.inv_lambda_f = (float)(1.0 / en.lambda);
-  en.thin_bits = thin_bits;
-  for (int r = 0; r < 3; ++r) {
-    en.init[r] = (int)N0[r];
-    if (rates[r] > 0.0) en.active |= 1u << r;
-    if (rates[r] == kmax) {
-      en.thin_always |= 1u << r;
-    } else {
-      en.thin_T[r] = (long long)(unsigned long long)std::floor(std::ldexp(rates[r] / kmax, thin_bits));
-      en.thin = 1;
-    }
-  }
+  const int init[3] = {(int)N0[0], (int)N0[1], (int)N0[2]};
+  const Ensemble en = make_ensemble(n_tot, init, rates, thin_bits, seed, n_runs, 0, 0);
   Threshold thr[kNoAllocMaxSnap + 1];
-  for (int s = 0; s < n_snap; ++s) thr[s] = threshold_of(snapshot_times[s], en.lambda);
-  thr[n_snap] = threshold_of(t_end, en.lambda);
+  for (int s = 0; s < n_snap; ++s) thr[s] = make_threshold(snapshot_times[s], en.lambda);
+  thr[n_snap] = make_threshold(t_end, en.lambda);
 
   // ---- scratch: the library's own device array
   NoAllocScratch* scratch = nullptr;

@@ -20,6 +20,82 @@
 
 using namespace bitssa;
 
+namespace bitssa {
+
+namespace {
+int bits_of(unsigned long long v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+}  // namespace
+
+// Per-ensemble constants from their definitions.
+Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], int q, unsigned long long seed,
+                       long long n_runs, long long run_offset, long long group_base) {
+  Ensemble e;
+  std::memset(&e, 0, sizeof e);
+  e.seed = seed;
+  e.n_runs = n_runs;
+  e.run_offset = run_offset;
+  e.group_base = group_base;
+  e.n_tot = (int)n_tot;
+  const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
+  e.lambda_int = (unsigned int)lam;
+  e.K = bits_of(lam);
+  set_precheck(e);
+  const double kmax = std::max(k[0], std::max(k[1], k[2]));
+  e.lambda = kmax * (double)lam;
+  e.inv_lambda_f = (float)(1.0 / e.lambda);
+  e.thin_bits = q;
+  for (int r = 0; r < 3; ++r) {
+    e.init[r] = init[r];
+    if (k[r] > 0.0) e.active |= 1u << r;
+    if (k[r] == kmax) {
+      e.thin_always |= 1u << r;
+      e.thin_T[r] = 0;
+    } else {
+      e.thin_T[r] = (long long)(unsigned long long)std::floor(std::ldexp(k[r] / kmax, q));
+      e.thin = 1;
+    }
+  }
+  return e;
+}
+
+// The crossing threshold of time t for total rate lambda.
+Threshold make_threshold(double t, double lambda) {
+  Threshold h;
+  std::memset(&h, 0, sizeof h);
+  h.t = t;
+  float f = (float)t;
+  if ((double)f > t) f = std::nextafter(f, -INFINITY);
+  h.t_f = f;
+  if (std::isinf(t) || !(lambda > 0.0)) {
+    h.E = LLONG_MIN;
+    h.M = 1ull << 63;
+    return h;
+  }
+  const double theta = -lambda * t;  // ln exp(-lambda t)
+  long long E = (long long)std::floor(theta / M_LN2);
+  double m = std::exp(theta - (double)E * M_LN2);
+  while (m >= 2.0) {
+    m *= 0.5;
+    ++E;
+  }
+  while (m < 1.0) {
+    m *= 2.0;
+    --E;
+  }
+  h.E = E;
+  h.M = (unsigned long long)std::ldexp(m, 63);  // m in [1, 2): exact
+  return h;
+}
+
+}  // namespace bitssa
+
 namespace {
 
 struct Allocator {
@@ -32,14 +108,6 @@ std::mutex g_alloc_mu;
 Allocator g_alloc;
 thread_local std::string t_err;
 
-int bit_len(unsigned long long v) {
-  int b = 0;
-  while (v) {
-    ++b;
-    v >>= 1;
-  }
-  return b;
-}
 
 }  // namespace
 
@@ -225,66 +293,6 @@ int check_options(const ssa_options& o, std::string* why) {
   return SSA_OK;
 }
 
-// Per-ensemble constants from their definitions.
-Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], int q, unsigned long long seed,
-                       long long n_runs, long long run_offset, long long group_base) {
-  Ensemble e;
-  std::memset(&e, 0, sizeof e);
-  e.seed = seed;
-  e.n_runs = n_runs;
-  e.run_offset = run_offset;
-  e.group_base = group_base;
-  e.n_tot = (int)n_tot;
-  const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
-  e.lambda_int = (unsigned int)lam;
-  e.K = bit_len(lam);
-  set_precheck(e);
-  const double kmax = std::max(k[0], std::max(k[1], k[2]));
-  e.lambda = kmax * (double)lam;
-  e.inv_lambda_f = (float)(1.0 / e.lambda);
-  e.thin_bits = q;
-  for (int r = 0; r < 3; ++r) {
-    e.init[r] = init[r];
-    if (k[r] > 0.0) e.active |= 1u << r;
-    if (k[r] == kmax) {
-      e.thin_always |= 1u << r;
-      e.thin_T[r] = 0;
-    } else {
-      e.thin_T[r] = (long long)(unsigned long long)std::floor(std::ldexp(k[r] / kmax, q));
-      e.thin = 1;
-    }
-  }
-  return e;
-}
-
-// The crossing threshold of time t for total rate lambda.
-Threshold make_threshold(double t, double lambda) {
-  Threshold h;
-  std::memset(&h, 0, sizeof h);
-  h.t = t;
-  float f = (float)t;
-  if ((double)f > t) f = std::nextafter(f, -INFINITY);
-  h.t_f = f;
-  if (std::isinf(t) || !(lambda > 0.0)) {
-    h.E = LLONG_MIN;
-    h.M = 1ull << 63;
-    return h;
-  }
-  const double theta = -lambda * t;  // ln exp(-lambda t)
-  long long E = (long long)std::floor(theta / M_LN2);
-  double m = std::exp(theta - (double)E * M_LN2);
-  while (m >= 2.0) {
-    m *= 0.5;
-    ++E;
-  }
-  while (m < 1.0) {
-    m *= 2.0;
-    --E;
-  }
-  h.E = E;
-  h.M = (unsigned long long)std::ldexp(m, 63);  // m in [1, 2): exact
-  return h;
-}
 
 int grow(ssa_ctx* c, void** p, size_t* cap, size_t need) {
   if (need <= *cap && *p) return SSA_OK;
