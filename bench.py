@@ -48,9 +48,9 @@ L2_BYTES = 129 * 2**20
 SMS = 152
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) of one launch of the one-thread bit-sliced kernel on the default
-# workload: the quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (592 640 B)
+# workload: the quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (694 528 B)
 # scaled x4 by the number of runs.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 4 * 592_640
+TRAFFIC_BYTES_PER_LAUNCH = 4 * 694_528
 
 
 def algorithmic_ops_per_group_step(K: int, b: int) -> int:
