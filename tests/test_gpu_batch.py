@@ -138,3 +138,27 @@ def test_batch_on_the_legacy_default_stream_and_tuned():
         for k in ("final_counts", "outcome", "t_abs"):
             assert np.array_equal(out[k], ref[k]), k
         assert np.array_equal(out["ee_hist"].reshape(ref["ee_hist"].shape), ref["ee_hist"])
+
+
+def test_batch_wide_n_against_the_oracle():
+    """Ensembles from K = 22 to K = 31 in one batch (N_tot up to 65536, one of them where half of
+    all draws are rejected, non-unit rates), each against the oracle."""
+    import torch
+    Ns = np.array([3000, 20000, 46400, 65536])
+    init = np.stack([Ns // 4, Ns // 4, Ns - 2 * (Ns // 4)], 1)
+    rates = np.array([[1.0, 1.0, 1.0], [0.7, 1.3, 1.9], [1.0, 1.0, 1.0], [1.2, 0.8, 1.0]])
+    runs = np.array([40, 33, 64, 40])
+    seeds = np.array([101, 102, 103, 104], dtype=np.uint64)
+    lam = np.sort(Ns * (Ns - 1) / 2 * rates.max(1))[1]
+    t_end = 1.0e4 / lam  # 10^2 .. 7 10^4 steps per run across the four
+    snaps = [t_end / 4, t_end / 2]
+    ens = {"init": init, "rates": rates, "runs": runs, "seeds": seeds}
+    g = run_batch(ens, t_end, snaps)
+    off = np.concatenate([[0], np.cumsum(runs)])
+    for e in range(len(Ns)):
+        sl = slice(off[e], off[e + 1])
+        r = oracle.run(oracle.frank(*rates[e]), init[e], int(runs[e]), seed=int(seeds[e]), t_end=t_end,
+                       snap_times=snaps, threads=THREADS)
+        ge = {"final_counts": g["final_counts"][sl], "outcome": g["outcome"][sl], "t_abs": g["t_abs"][sl],
+              "snap_counts": g["snap_counts"][:, sl]}
+        assert_parity(ge, r)
