@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -78,7 +79,7 @@ class Clocks:
         try:
             self.f = open(path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -275,8 +276,10 @@ def main():
     for _ in range(args.warmup):
         pkg.ssa_run(ctx, T_END, SNAPS)
     barrier()
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv"))
+    # the raw samples go to BENCH_CLOCKS_DIR when it is set (a summary is in the JSON line)
+    clocks_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+    os.makedirs(clocks_dir, exist_ok=True)
+    clocks = Clocks(local, os.path.join(clocks_dir, f"clocks_rank{rank}.csv"))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     reactions = absorbed = lane_steps = group_steps = max_group_steps = layout_used = 0
     barrier()
