@@ -51,7 +51,7 @@ class Problem(C.Structure):
         ("rates", C.POINTER(C.c_double)), ("n_tot", C.c_int64), ("seed", C.c_uint64),
         ("precision", C.c_int32), ("thin_bits", C.c_int32), ("t_end", C.c_double),
         ("snap_times", C.POINTER(C.c_double)), ("n_snap", C.c_int32),
-        ("step_budget", C.c_int64), ("shared_n", C.c_int32),
+        ("step_budget", C.c_int64), ("shared_n", C.c_int32), ("pad_pow2", C.c_int32),
     ]
 
 
@@ -122,13 +122,13 @@ def frank(k1=1.0, k2=1.0, k3=1.0) -> Network:
 
 
 def _problem(net: Network, n_tot, seed, precision=P64, thin_bits=32, t_end=np.inf,
-             snap_times=(), step_budget=0, shared_n=False):
+             snap_times=(), step_budget=0, shared_n=False, pad_pow2=False):
     snaps = np.ascontiguousarray(snap_times, dtype=np.float64)
     p = Problem(net.n_species, net.n_reactions, _ptr(net.reactants, C.c_int32),
                 _ptr(net.products, C.c_int32), _ptr(net.rates, C.c_double), int(n_tot),
                 int(seed) & (2**64 - 1), int(precision), int(thin_bits), float(t_end),
                 _ptr(snaps, C.c_double) if len(snaps) else None, len(snaps), int(step_budget),
-                1 if shared_n else 0)
+                1 if shared_n else 0, 1 if pad_pow2 else 0)
     p._keep = (net, snaps)  # keep the arrays alive as long as the struct
     return p
 
@@ -174,11 +174,12 @@ def ee_bin(L, D):
 
 def run(net: Network, init, n_runs=None, *, seed=0, precision=P64, thin_bits=32, t_end=np.inf,
         snap_times=(), step_budget=0, first_run=0, run_ids=None, threads=None,
-        want_snapshots=True, check=True, shared_n=False):
+        want_snapshots=True, check=True, shared_n=False, pad_pow2=False):
     """Run the oracle on runs first_run .. first_run+n_runs-1 (or on run_ids).
 
     init: [S] shared initial counts or [n_runs][S] per-run counts.
     shared_n: every run of a group of 32 uses the n of the group's lane 0 (Sec. 4, step a).
+    pad_pow2: the uniformisation bound is 2^K (null events fill the gap above lambda_int).
     Returns a dict of numpy arrays indexed by run position.
     """
     init = np.ascontiguousarray(init, dtype=np.int64)
@@ -190,7 +191,8 @@ def run(net: Network, init, n_runs=None, *, seed=0, precision=P64, thin_bits=32,
     if n_runs is None:
         n_runs = init.shape[0] if per_run else 1
     n_tot = int(init.reshape(-1, net.n_species)[0].sum())
-    p = _problem(net, n_tot, seed, precision, thin_bits, t_end, snap_times, step_budget, shared_n)
+    p = _problem(net, n_tot, seed, precision, thin_bits, t_end, snap_times, step_budget, shared_n,
+                 pad_pow2)
     out = (Result * max(n_runs, 1))()
     n_snap = len(snap_times)
     snaps = (np.zeros((n_snap, n_runs, net.n_species), dtype=np.int64)

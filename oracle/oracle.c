@@ -201,6 +201,10 @@ int orc_derive(const orc_problem* p, orc_derived* d) {
   uint64_t N = (uint64_t)p->n_tot;
   d->lambda_int = (uint64_t)m_pair * (N * (N - 1) / 2) + (uint64_t)u_max * N;
   d->K = bit_length(d->lambda_int);
+  /* Uniformisation at any bound at or above the largest total propensity samples the same
+   * process; padding the bound to 2^K with further null events makes every K-bit n valid. */
+  if (p->pad_pow2 != 0 && p->pad_pow2 != 1) return ORC_EINVAL;
+  if (p->pad_pow2) d->lambda_int = (uint64_t)1 << d->K;
   d->k_max = k_max;
   d->lambda = k_max * (double)d->lambda_int;
   for (int r = 0; r < p->n_reactions; r++) {

@@ -19,7 +19,7 @@
  *   n   = sum_{i<K} bit_l(w_i) 2^i; while n >= Lambda_int, its bits from p up (p the
  *         highest bit where n and Lambda_int differ, 0 if equal) are replaced by the
  *         same bits of attempt a+1 (a uniform integer in [0, Lambda_int), Sec. 3 step
- *         5(i) and step a);
+ *         5(i) and step a); with pad_pow2, Lambda_int = 2^K and no draw is rejected;
  *   tau = -log(u) / Lambda from the whole words w_K, w_{K+1} of attempt 0
  *         (Eq. equation-tau, with the uniformisation rate of Eq. equation-z):
  *         fp64 u = (x + 1) 2^-53 with x = w_{K+1} << 21 | w_K >> 11; the fp32
@@ -73,12 +73,15 @@ typedef struct {
   int64_t step_budget;      /* max steps per run, 0 = unlimited */
   int32_t shared_n;         /* 1: every run of a group of 32 uses the n of the group's lane 0 (one n
                                for all copies, Sec. 4 step a), drawn whether or not lane 0 is live */
+  int32_t pad_pow2;         /* 1: the uniformisation bound is raised from lambda_int to 2^K with
+                               further null events, so that every K-bit draw of n is accepted */
 } orc_problem;
 
 /* Derived constants of a problem, computed from their definitions. */
 typedef struct {
-  uint64_t lambda_int;      /* integer uniformisation bound: sum_r h_r <= lambda_int */
-  int32_t K;                /* random planes for n: bit length of lambda_int */
+  uint64_t lambda_int;      /* integer uniformisation bound: sum_r h_r <= lambda_int (2^K when
+                               pad_pow2 is set) */
+  int32_t K;                /* random planes for n: bit length of the unpadded bound */
   double k_max;
   double lambda;            /* k_max * lambda_int */
   int32_t thin_always[ORC_MAX_REACTIONS]; /* 1: T_r = 2^q, always kept */

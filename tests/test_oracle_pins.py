@@ -92,6 +92,14 @@ def test_lambda_frank_is_Z(orc, N, K):
     assert d.lambda_ == float(N * (N - 1) // 2)
 
 
+@pytest.mark.parametrize("N,K", [(12, 7), (64, 11), (1024, 19), (46400, 31), (65536, 31)])
+def test_lambda_padded_to_a_power_of_two(orc, N, K):
+    """Padding keeps K (the bit length of Z) and raises the bound to 2^K > Z."""
+    d = orc.derive(orc.frank(1.0, 0.5, 2.0), N, pad_pow2=True)
+    assert d.K == K and d.lambda_int == 2 ** K > N * (N - 1) // 2
+    assert d.lambda_ == 2.0 * 2 ** K
+
+
 def test_lambda_is_a_bound_by_brute_force(orc):
     """max over all states of sum_r h_r <= lambda_int, with equality for Frank + ghosts."""
     nets = [
@@ -199,6 +207,25 @@ def test_first_step_probabilities_under_heavy_rejection(orc, init):
     assert r["redraws"].sum() > 0.5 * n
 
 
+@pytest.mark.parametrize("init", [(1, 1, 10), (6, 0, 6), (4, 4, 4)])
+def test_first_step_probabilities_padded(orc, init):
+    """With the bound padded to 2^7 = 128 at N_tot = 12, reaction r takes h_r of the 128
+    equally likely draws and nothing is redrawn."""
+    n = 150_000
+    r = orc.run(orc.frank(), init, n, seed=23, step_budget=1, check=False, pad_pow2=True)
+    delta = r["final_counts"] - np.array(init)
+    fired = np.full(n, 3)
+    for k, nu in enumerate(([1, 0, -1], [0, 1, -1], [-1, -1, 2])):
+        fired[(delta == nu).all(1)] = k
+    h = frank_h(*init)
+    p = np.array(h + [128 - sum(h)], dtype=float) / 128
+    obs = np.bincount(fired, minlength=4)
+    keep = p > 0
+    assert np.all(obs[~keep] == 0)
+    assert stats.chisquare(obs[keep], p[keep] * n).pvalue > 1e-4, (obs, p * n)
+    assert r["redraws"].sum() == 0
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_waiting_time_exponential(orc, precision):
     """Eq. equation-tau: tau ~ Exp(Lambda), one clock per 32-lane group."""
@@ -215,6 +242,26 @@ def test_waiting_time_exponential(orc, precision):
     r2 = orc.run(net, (16, 16, 32), run_ids=np.arange(8) * 32 + 5, seed=3, step_budget=1,
                  precision=precision, check=False)
     assert np.array_equal(r2["t_last"], r["t_last"][:8])
+
+
+def test_padded_steps_scale_with_the_bound(orc):
+    """Uniformisation at rate Lambda makes the expected number of steps before absorption
+    Lambda E[T]: padding Z = 2016 to 2048 at N_tot = 64 keeps E[T] and scales the steps by
+    2048 / 2016, with no redraws."""
+    runs = 20_000
+    ids = np.arange(runs) * 32 + 7
+    a = orc.run(orc.frank(), (16, 16, 32), run_ids=ids, seed=8, t_end=np.inf)
+    b = orc.run(orc.frank(), (16, 16, 32), run_ids=ids, seed=8, t_end=np.inf, pad_pow2=True)
+    assert b["redraws"].sum() == 0 and a["redraws"].sum() > 0
+    se_t = math.hypot(a["t_abs"].std(), b["t_abs"].std()) / math.sqrt(runs)
+    assert abs(a["t_abs"].mean() - b["t_abs"].mean()) < 4.5 * se_t
+    ratio = b["steps"].mean() / a["steps"].mean()
+    se_r = ratio * math.hypot(a["steps"].std() / a["steps"].mean(),
+                              b["steps"].std() / b["steps"].mean()) / math.sqrt(runs)
+    assert abs(ratio - 2048 / 2016) < 4.5 * se_r
+    # the real reactions do not depend on the bound: same law of the jump chain
+    se_x = math.hypot(a["reactions"].std(), b["reactions"].std()) / math.sqrt(runs)
+    assert abs(a["reactions"].mean() - b["reactions"].mean()) < 4.5 * se_x
 
 
 def test_redraw_rate(orc):
@@ -234,17 +281,19 @@ def _frank_me(N, rates=(1.0, 1.0, 1.0)):
     return me.generator(FRANK_REAC, FRANK_PROD, list(rates), N)
 
 
-@pytest.mark.parametrize("lane,shared", [(0, False), (17, False), (17, True)])
-def test_master_equation_distribution(orc, lane, shared):
+@pytest.mark.parametrize("lane,shared,pad", [(0, False, False), (17, False, False), (17, True, False),
+                                            (5, False, True), (9, True, True)])
+def test_master_equation_distribution(orc, lane, shared, pad):
     """Each lane is an exact sample path, also when it reacts to the n of its group's lane 0
-    (one n for all copies, Sec. 4 step a): n never depends on the state."""
+    (one n for all copies, Sec. 4 step a): n never depends on the state; and also with the
+    bound padded from Z = 66 to 128 (uniformisation at a larger rate)."""
     N, init = 12, (3, 3, 6)
     st, index, Q = _frank_me(N)
     snaps = [0.02, 0.05, 0.1, 0.2, 0.4]
     runs = 40_000
     # one lane per group: groups draw from independent counters
     r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32 + lane, seed=21, t_end=0.5,
-                snap_times=snaps, shared_n=shared)
+                snap_times=snaps, shared_n=shared, pad_pow2=pad)
     p0 = np.zeros(len(st))
     p0[index[init]] = 1.0
     for s, t in enumerate(snaps):
@@ -284,14 +333,15 @@ def test_shared_n_lanes_follow_one_draw(orc):
     assert len({tuple(x) for x in a["final_counts"][:32]}) > 1
 
 
-def test_master_equation_absorption(orc):
+@pytest.mark.parametrize("pad", [False, True])
+def test_master_equation_absorption(orc, pad):
     """Absorption probabilities and mean absorption time from the fundamental matrix."""
     N, init = 12, (5, 2, 5)
     st, index, Q = _frank_me(N)
     absorbing, B, T, transient = me.absorption(Q)
     i0 = transient.index(index[init])
     runs = 40_000
-    r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32, seed=33, t_end=np.inf)
+    r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32, seed=33, t_end=np.inf, pad_pow2=pad)
     assert np.all(r["outcome"] >= 0)
     for col, a in enumerate(absorbing):
         survivor = int(np.argmax(st[a]))
