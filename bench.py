@@ -51,13 +51,14 @@ MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) of one launch of the one-thread bit-sliced kernel on the default
 # workload: the quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (694 528 B)
 # scaled x4 by the number of runs.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 4 * 694_528
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
-def algorithmic_ops_per_group_step(K: int, b: int) -> int:
+def algorithmic_ops_per_group_step(K: int, b: int, padded: bool = False) -> int:
     """Word operations one group step must do (27K + 6b logic plus 20 LOP3 per Philox call
-    for the ceil((K+2)/4) calls of n and tau)."""
-    return 27 * K + 6 * b + 20 * ((K + 2 + 3) // 4)
+    for the ceil((K+2)/4) calls of n and tau); a bound padded to 2^K has no rejection test
+    (K fewer)."""
+    return (26 if padded else 27) * K + 6 * b + 20 * ((K + 2 + 3) // 4)
 
 
 def bit_length(v: int) -> int:
@@ -119,7 +120,7 @@ def cpu_baseline(sample_runs: int, threads: int):
     oracle.build()
     t0 = time.perf_counter()
     r = oracle.run(oracle.frank(), INIT, sample_runs, seed=SEED, t_end=T_END, snap_times=SNAPS,
-                   threads=threads)
+                   threads=threads, pad_pow2=bool(PAD))
     dt = time.perf_counter() - t0
     reactions = int(r["reactions"].sum())
     return {"value": reactions / dt, "unit": "lane-reactions/s", "cores": threads, "kind": "oracle",
@@ -137,12 +138,13 @@ def run_reference(args, rank, world):
     import oracle
     oracle.build()
     for _ in range(args.warmup):
-        oracle.run(oracle.frank(), INIT, 64, seed=SEED, t_end=T_END, snap_times=SNAPS, threads=threads)
+        oracle.run(oracle.frank(), INIT, 64, seed=SEED, t_end=T_END, snap_times=SNAPS, threads=threads,
+                   pad_pow2=bool(PAD))
     total_react, total_abs, total_t = 0, 0, 0.0
     for k in range(args.steps):
         t0 = time.perf_counter()
         r = oracle.run(oracle.frank(), INIT, per_step, first_run=k * per_step, seed=SEED, t_end=T_END,
-                       snap_times=SNAPS, threads=threads)
+                       snap_times=SNAPS, threads=threads, pad_pow2=bool(PAD))
         total_t += time.perf_counter() - t0
         total_react += int(r["reactions"].sum())
         total_abs += int((r["outcome"] >= 0).sum())
@@ -164,6 +166,7 @@ def run_reference(args, rank, world):
 WORKLOAD = "c2"
 BATCH = None
 PRECISION = 0
+PAD = 1  # 1: uniformisation bound padded to 2^K (no rejected draws of n); --pad 0 for N(N-1)/2
 PRECISION_NAMES = {0: "p64", 1: "p32kahan", 2: "p32d64acc", 3: "p64logsum", 4: "p32plain"}
 
 
@@ -188,8 +191,11 @@ def workload_config(world):
                 "model": "Frank, per-ensemble rates", "ensembles": len(BATCH["runs"]),
                 "runs": RUNS_PER_GPU * world, "runs_per_gpu": RUNS_PER_GPU, "t_end": T_END,
                 "global_batch": RUNS_PER_GPU * world, "parallelism": f"replicas x{world}",
-                "l2": "L2 flushed between timed steps (256 MiB write)"}
+                "bound": BOUND_NAMES[PAD], "l2": "L2 flushed between timed steps (256 MiB write)"}
     return workload_config_single(world)
+
+
+BOUND_NAMES = ["lambda_int = N(N-1)/2, rejected draws redrawn", "lambda_int padded to 2^K with null events"]
 
 
 def workload_config_single(world):
@@ -199,7 +205,7 @@ def workload_config_single(world):
             "runs": RUNS_PER_GPU * world, "runs_per_gpu": RUNS_PER_GPU, "groups_per_gpu": RUNS_PER_GPU // 32,
             "seed": SEED, "t_end": T_END, "snapshots": SNAPS, "precision": PRECISION_NAMES[PRECISION],
             "global_batch": RUNS_PER_GPU * world, "parallelism": f"replicas x{world} (run shards)",
-            "l2": "L2 flushed between timed steps (256 MiB write)"}
+            "bound": BOUND_NAMES[PAD], "l2": "L2 flushed between timed steps (256 MiB write)"}
 
 
 def main():
@@ -219,6 +225,9 @@ def main():
                     help="skip ssa_tune (by default it times every launch configuration on the "
                          "workload during warm-up and keeps the fastest; c3 keeps the per-bucket rule)")
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--pad", type=int, default=1, choices=[0, 1],
+                    help="1: pad the uniformisation bound to 2^K with null events, so that no draw of n "
+                         "is rejected (the same process, sampled through a different draw)")
     ap.add_argument("--runs", type=int, default=0,
                     help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
@@ -228,8 +237,9 @@ def main():
     args = ap.parse_args()
     rank, world, local = env_rank()
     set_workload(args.workload, args.runs)
-    global PRECISION
+    global PRECISION, PAD
     PRECISION = args.precision
+    PAD = args.pad
 
     if args.impl == "reference":
         if world > 1:
@@ -255,7 +265,8 @@ def main():
     from paper_2412_16613_gb300 import sharding
     first_run = sharding.weak_shard(RUNS_PER_GPU, rank)[0] if WORKLOAD != "c3" else 0
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
-                                  block_size=args.block, first_run=first_run, layout=args.layout)
+                                  block_size=args.block, first_run=first_run, layout=args.layout,
+                                  pad_pow2=PAD)
     if WORKLOAD == "c3":
         opt.first_run = 0
         ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],
@@ -316,7 +327,7 @@ def main():
     # ---- roofline of the bit-sliced kernel (one launch per step; a batch runs one launch per
     # number of planes K, so its per-unit count is not a single figure and is not reported)
     K, b = bit_length(N_TOT * (N_TOT - 1) // 2), bit_length(N_TOT)
-    ops_unit = algorithmic_ops_per_group_step(K, b)
+    ops_unit = algorithmic_ops_per_group_step(K, b, bool(PAD))
     gs_per_launch = group_steps / world / args.steps
     achieved = ops_unit * gs_per_launch / (statistics.mean(kernel_ms) / 1e3) / 1e9
     peak_ops_per_clk = float(os.environ.get("BITSSA_ALU_OPS_PER_CLK_PER_SM", "64"))
@@ -389,7 +400,7 @@ def main():
     if not args.no_baselines and WORKLOAD != "c3":
         od = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                      keep_snap_counts=1, first_run=first_run, layout=opt.layout,
-                                     block_size=opt.block_size)
+                                     block_size=opt.block_size, pad_pow2=PAD)
         cd = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
                             RUNS_PER_GPU, SEED, od)
         pkg.ssa_run(cd, T_END, SNAPS)

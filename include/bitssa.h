@@ -110,7 +110,15 @@ typedef struct {
                                 so it is meant for per-run initial states (n0_per_run = 1).
                                 Bit-sliced engine, three-warp layout (SSA_LAYOUT_AUTO takes it;
                                 SSA_LAYOUT_THREAD gives SSA_EUNSUPPORTED). */
-  int32_t reserved[5];
+  int32_t pad_pow2;          /* 0 (default): n is uniform on [0, lambda_int), lambda_int = N (N - 1) / 2
+                                (Eq. equation-z; Sec. 3 step 5), and a draw at or above it is redrawn.
+                                1: the total rate is padded with further null events up to 2^K, K the
+                                bit length of lambda_int, so that every K-bit draw is accepted and
+                                Lambda = k_max 2^K.  Uniformisation at any bound at or above the largest
+                                total propensity samples the same process: the runs are exact either
+                                way, but not draw for draw the same.  Costs 2^K / lambda_int - 1 more
+                                (null) steps, saves every redraw.  Bit-sliced engine only. */
+  int32_t reserved[4];
 } ssa_options;
 
 /* Fields for ssa_fetch.  n_runs = the context's total number of runs (for a batch,

@@ -426,7 +426,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   // n >= lambda_int needs every plane of lambda_int's leading run of ones set in n: test that
   // first (a shallow AND tree), and run the full comparison only when some lane passes
   uint32_t need = 0u;
-  {
+  if (e.reject) {  // (a bound padded to 2^K accepts every draw)
     uint32_t a[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) a[i] = n[i] | e.top_mask[i];

@@ -327,6 +327,7 @@ __device__ __forceinline__ bool trio_redraw(uint32_t* row, const Ensemble& e, ui
                                             unsigned long long step, uint32_t live, PhiloxKey key,
                                             unsigned int& rounds) {
   constexpr int NCR = TrioShape<K>::NCR;
+  if (!e.reject) return true;  // a bound padded to 2^K accepts every draw
   uint32_t pass = 0xFFFFFFFFu;  // n >= lambda_int needs every plane of its leading run of ones set
 #pragma unroll
   for (int i = 0; i < K; ++i) pass &= row[i] | e.top_mask[i];

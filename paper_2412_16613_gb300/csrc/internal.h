@@ -67,6 +67,8 @@ struct Ensemble {
   int thin;                  // any reaction with k_r < k_max
   int thin_bits;             // q
   int shared_n;              // 1: every lane of a group uses lane 0's n
+  int reject;                // 1: lambda_int < 2^K, draws of n at or above it are redrawn;
+                             // 0: the bound is padded to 2^K and every draw is accepted
   unsigned int top_ones;     // planes of the leading run of ones of lambda_int (bit i = plane i):
                              // n >= lambda_int needs all of them set (0: no pre-check)
   unsigned int top_mask[32]; // per plane: 0 on the run, ~0 elsewhere, so that the AND over planes
@@ -82,10 +84,10 @@ inline void set_precheck(Ensemble& e) {
 }
 
 // Per-ensemble constants of Frank's model in the kernel's species order (L, D, A) from their
-// definitions: lambda_int = N (N - 1) / 2, K = its bit length, the pre-check masks, the
-// thinning thresholds T_r = floor(k_r / k_max 2^q).
+// definitions: lambda_int = N (N - 1) / 2 (2^K when pad_pow2), K = the bit length of
+// N (N - 1) / 2, the pre-check masks, the thinning thresholds T_r = floor(k_r / k_max 2^q).
 Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], int q, unsigned long long seed,
-                       long long n_runs, long long run_offset, long long group_base);
+                       long long n_runs, long long run_offset, long long group_base, int pad_pow2);
 // The crossing threshold of time t for total rate lambda, in every form a clock compares.
 Threshold make_threshold(double t, double lambda);
 

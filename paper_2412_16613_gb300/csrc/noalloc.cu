@@ -112,7 +112,7 @@ extern "C" int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int
 
   // ---- the ensemble (Frank's model in species order L, D, A)
   const int init[3] = {(int)N0[0], (int)N0[1], (int)N0[2]};
-  const Ensemble en = make_ensemble(n_tot, init, rates, thin_bits, seed, n_runs, 0, 0);
+  const Ensemble en = make_ensemble(n_tot, init, rates, thin_bits, seed, n_runs, 0, 0, 0);
   Threshold thr[kNoAllocMaxSnap + 1];
   for (int s = 0; s < n_snap; ++s) thr[s] = make_threshold(snapshot_times[s], en.lambda);
   thr[n_snap] = make_threshold(t_end, en.lambda);

@@ -35,7 +35,7 @@ int bits_of(unsigned long long v) {
 
 // Per-ensemble constants from their definitions.
 Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], int q, unsigned long long seed,
-                       long long n_runs, long long run_offset, long long group_base) {
+                       long long n_runs, long long run_offset, long long group_base, int pad_pow2) {
   Ensemble e;
   std::memset(&e, 0, sizeof e);
   e.seed = seed;
@@ -43,9 +43,12 @@ Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], in
   e.run_offset = run_offset;
   e.group_base = group_base;
   e.n_tot = (int)n_tot;
-  const unsigned long long lam = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
+  const unsigned long long z = (unsigned long long)n_tot * (unsigned long long)(n_tot - 1) / 2ull;
+  e.K = bits_of(z);
+  // padded: null events fill [z, 2^K), so that no K-bit draw is rejected
+  const unsigned long long lam = pad_pow2 ? (1ull << e.K) : z;
   e.lambda_int = (unsigned int)lam;
-  e.K = bits_of(lam);
+  e.reject = pad_pow2 ? 0 : 1;
   set_precheck(e);
   const double kmax = std::max(k[0], std::max(k[1], k[2]));
   e.lambda = kmax * (double)lam;
@@ -284,6 +287,9 @@ int check_options(const ssa_options& o, std::string* why) {
     return (*why = "shared_n is a mode of the bit-sliced engine", SSA_EUNSUPPORTED);
   if (o.shared_n && o.layout == SSA_LAYOUT_THREAD)
     return (*why = "shared_n runs on the three-warp layout", SSA_EUNSUPPORTED);
+  if (o.pad_pow2 != 0 && o.pad_pow2 != 1) return (*why = "pad_pow2 must be 0 or 1", SSA_EINVAL);
+  if (o.pad_pow2 && o.engine != SSA_ENGINE_BITSLICED)
+    return (*why = "pad_pow2 is a mode of the bit-sliced engine", SSA_EUNSUPPORTED);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
   if (o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
     return (*why = "block_size must be 0 or a multiple of 32 up to 256", SSA_EINVAL);
@@ -667,7 +673,7 @@ int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_spec
   c->n_ens = 1;
   c->n_runs_total = n_runs;
   c->ens.push_back(make_ensemble(n_tot, shared, canon_rates, c->opt.thin_bits, seed, n_runs, 0,
-                                 c->opt.first_run / 32));
+                                 c->opt.first_run / 32, c->opt.pad_pow2));
   c->ens.back().shared_n = c->opt.shared_n;
   DeviceGuard guard(c->opt.device);
   if ((st = setup_device(c)) != SSA_OK) return bail(st, c->err);
@@ -715,7 +721,8 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
     if (tot < 1) return bail(SSA_EINVAL, "the total count must be >= 1");
     if (tot > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
     const double* k = rates_ens + 3 * e;
-    c->ens.push_back(make_ensemble(tot, canon, k, c->opt.thin_bits, seed_ens[e], runs_ens[e], offset, 0));
+    c->ens.push_back(
+        make_ensemble(tot, canon, k, c->opt.thin_bits, seed_ens[e], runs_ens[e], offset, 0, c->opt.pad_pow2));
     c->ens.back().shared_n = c->opt.shared_n;
     c->rates.insert(c->rates.end(), k, k + 3);
     offset += runs_ens[e];

@@ -84,6 +84,9 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
     (dict(reac=F_R, prod=F_P, shared_n=2), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, shared_n=1, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, shared_n=1, layout=pkg.SSA_LAYOUT_THREAD), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, pad_pow2=2), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, pad_pow2=-1), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, pad_pow2=1, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
     (dict(reac=[[1, 0, 1], [0, 1, 1]], prod=[[2, 0, 0], [0, 2, 0]]), pkg.SSA_EUNSUPPORTED),  # not Frank
     (dict(reac=[[1, 1, 0], [0, 1, 1], [1, 0, 1]], prod=[[0, 0, 2], [0, 2, 0], [2, 0, 0]]),
      pkg.SSA_EUNSUPPORTED),                                                           # Frank, wrong order

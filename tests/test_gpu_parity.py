@@ -387,3 +387,35 @@ def test_parity_wide_n(N, rates, layout):
     r = oracle.run(oracle.frank(*rates), init, n, seed=17, t_end=t_end, snap_times=snaps, threads=THREADS)
     assert_parity(g, r)
     assert g["counters"]["redraw_rounds"] > 0
+
+
+@LAYOUTS
+@pytest.mark.parametrize("N,rates", [(1024, (1.0, 1.0, 1.0)), (46400, (1.0, 1.0, 1.0)), (10000, (0.7, 1.3, 1.9)),
+                                     (12, (1.0, 0.5, 2.0))])
+def test_parity_padded_bound(N, rates, layout):
+    """pad_pow2: the bound raised to 2^K (null events above N (N - 1) / 2), so no draw is
+    rejected; runs, snapshots and counters against the oracle in the same mode."""
+    init = (N // 4, N // 4, N - 2 * (N // 4))
+    lam = 2 ** (N * (N - 1) // 2).bit_length() * max(rates)
+    t_end = 1.2e4 / lam if N > 64 else 50.0
+    snaps = [t_end / 3, 2 * t_end / 3]
+    n = 96 + 5
+    g = gpu_run(init, n, seed=29, t_end=t_end, snaps=snaps, rates=rates, layout=layout, pad_pow2=1)
+    r = oracle.run(oracle.frank(*rates), init, n, seed=29, t_end=t_end, snap_times=snaps, threads=THREADS,
+                   pad_pow2=True)
+    ok = assert_parity(g, r)
+    assert g["counters"]["redraw_rounds"] == 0 and r["redraws"].sum() == 0
+    if ok.all():
+        assert g["counters"]["lane_steps"] == r["steps"].sum()
+        assert g["counters"]["reactions"] == r["reactions"].sum()
+
+
+def test_parity_padded_bound_shared_n():
+    """The paper's shared draw with the padded bound (three-warp layout)."""
+    rng = np.random.default_rng(37)
+    n = 256 + 3
+    init = rng.multinomial(300, [0.25, 0.25, 0.5], size=n)
+    g = gpu_run(init, n, seed=5, t_end=2.0, snaps=[0.01, 0.1], shared_n=1, pad_pow2=1)
+    r = oracle.run(oracle.frank(), init, seed=5, t_end=2.0, snap_times=[0.01, 0.1], shared_n=True,
+                   pad_pow2=True, threads=THREADS)
+    assert_parity(g, r)
