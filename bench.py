@@ -49,9 +49,10 @@ L2_BYTES = 129 * 2**20
 SMS = 152
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) of one launch of the one-thread bit-sliced kernel on the default
-# workload: the quarter-size capture in profiles/frank_kernel_n1024_262144runs_full.md (694 528 B)
-# scaled x4 by the number of runs.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = None
+# workload: the metrics-only capture of the quarter-size case in
+# profiles/frank_kernel_n1024_2p20runs_launches.md (123 136 B), scaled x4 by the number of runs.
+# Set to None whenever the kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_LAUNCH = 4 * 123_136
 
 
 def algorithmic_ops_per_group_step(K: int, b: int, padded: bool = False) -> int:
@@ -340,7 +341,8 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak,
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH if (WORKLOAD == "c2" and RUNS_PER_GPU == 1 << 20
-                                                        and PRECISION == 0 and layout_used == 1) else None,
+                                                        and PRECISION == 0 and PAD == 1 and layout_used == 1)
+                else None,
                 "ops_per_group_step": ops_unit, "group_steps_per_launch": gs_per_launch,
                 "peak_basis": f"{SMS} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {MAX_SM_MHZ:g} MHz",
                 "lop3_microbench_gops": micro}
