@@ -312,6 +312,48 @@ def test_master_equation_distribution(orc, lane, shared, pad):
         assert pval > 1e-4, (t, pval)
 
 
+GENERAL_NETWORKS = [
+    # 2A -> A + B, A + B -> 2A, B -> A: a homodimer, a pair, a first-order reaction, thinning
+    ([[2, 0], [1, 1], [0, 1]], [[1, 1], [2, 0], [1, 0]], [1.0, 0.5, 3.0], (7, 3)),
+    # S + I -> 2I, I -> R (u_max = 1 next to a pair)
+    ([[1, 1, 0], [0, 1, 0]], [[0, 2, 0], [0, 0, 1]], [1.0, 0.7], (8, 2, 0)),
+    # two reactions on one pair (m_pair = 2) and a zero rate
+    ([[1, 1, 0], [1, 1, 0], [0, 0, 1]], [[2, 0, 0], [0, 2, 0], [1, 0, 0]], [1.0, 2.0, 0.0], (4, 4, 2)),
+    # four species
+    ([[1, 1, 0, 0], [0, 0, 1, 1], [0, 1, 0, 0], [0, 0, 2, 0]],
+     [[0, 0, 2, 0], [2, 0, 0, 0], [0, 0, 0, 1], [1, 1, 0, 0]], [1.0, 0.8, 2.0, 0.5], (3, 2, 2, 1)),
+]
+
+
+@pytest.mark.parametrize("net_i", range(len(GENERAL_NETWORKS)))
+@pytest.mark.parametrize("pad", [False, True])
+def test_master_equation_general_networks(orc, net_i, pad):
+    """Networks other than Frank's (order-2 pairs and homodimers, first-order reactions,
+    m_pair = 2, four species, non-unit and zero rates) against the master equation."""
+    reac, prod, rates, init = GENERAL_NETWORKS[net_i]
+    N = sum(init)
+    st, index, Q = me.generator(reac, prod, rates, N)
+    snaps = [0.05, 0.2, 0.6]
+    runs = 30_000
+    r = orc.run(orc.Network(reac, prod, rates), init, run_ids=np.arange(runs) * 32 + 11, seed=77 + net_i,
+                t_end=0.6, snap_times=snaps, pad_pow2=pad)
+    p0 = np.zeros(len(st))
+    p0[index[init]] = 1.0
+    for s, t in enumerate(snaps):
+        p = me.distribution(Q, p0, t)
+        obs = np.zeros(len(st))
+        for c in r["snap_counts"][s]:
+            obs[index[tuple(int(x) for x in c)]] += 1
+        exp = p * runs
+        big = exp >= 5
+        o = np.append(obs[big], obs[~big].sum())
+        e = np.append(exp[big], exp[~big].sum())
+        if e[-1] < 5:
+            o, e = o[:-1], e[:-1]
+            e *= o.sum() / e.sum()
+        assert stats.power_divergence(o, e, lambda_="log-likelihood")[1] > 1e-4, (t, net_i)
+
+
 def test_shared_n_lanes_follow_one_draw(orc):
     """Shared n: from one initial state every lane of a group repeats lane 0's run (the reason
     the paper's shared draw needs distinct initial states); lane 0 itself is the run it is
