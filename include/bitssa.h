@@ -71,10 +71,18 @@ enum {
 
 /* Simulation engine. */
 enum {
-  SSA_ENGINE_BITSLICED = 0,     /* the method of the paper: 32 runs per word */
-  SSA_ENGINE_THREAD_PER_RUN = 1 /* comparison baseline: one GPU thread per run, direct
-                                   method with integer propensities (Sec. 3, steps 1-7
-                                   without ghosts) and its own per-run Philox stream */
+  SSA_ENGINE_BITSLICED = 0,      /* the method of the paper: 32 runs per word.  Frank's model
+                                    (below) runs on kernels that keep the cumulative
+                                    propensities and update them with App. A's increments; any
+                                    other network on the general kernel */
+  SSA_ENGINE_THREAD_PER_RUN = 1, /* comparison baseline: one GPU thread per run, direct
+                                    method with integer propensities (Sec. 3, steps 1-7
+                                    without ghosts) and its own per-run Philox stream;
+                                    Frank's model only */
+  SSA_ENGINE_GENERAL = 2         /* the method on the general kernel for every network, Frank's
+                                    included: each step recomputes every propensity from the
+                                    count planes with bit-sliced products (Sec. 4.1); same
+                                    streams and runs as SSA_ENGINE_BITSLICED */
 };
 
 /* How the bit-sliced engine maps a group of 32 runs onto the GPU. */
@@ -91,7 +99,8 @@ enum {
 typedef struct {
   int32_t precision;         /* SSA_P64 (default) | SSA_P32_KAHAN | SSA_P32_D64ACC | SSA_P64_LOGSUM |
                                 SSA_P32_PLAIN */
-  int32_t engine;            /* SSA_ENGINE_BITSLICED (default) | SSA_ENGINE_THREAD_PER_RUN */
+  int32_t engine;            /* SSA_ENGINE_BITSLICED (default) | SSA_ENGINE_THREAD_PER_RUN |
+                                SSA_ENGINE_GENERAL */
   int32_t block_size;        /* threads per block, 0 = default (SSA_LAYOUT_WARPS always uses 96) */
   int32_t blocks_per_sm;     /* resident blocks per SM to launch, 0 = occupancy limit */
   int32_t thin_bits;         /* q in [1, 64], bits of the thinning threshold (default 32) */
@@ -108,8 +117,9 @@ typedef struct {
                                 run 0, drawn and redrawn whether or not that run is still live; with
                                 identical initial states the runs of a group are then identical,
                                 so it is meant for per-run initial states (n0_per_run = 1).
-                                Bit-sliced engine, three-warp layout (SSA_LAYOUT_AUTO takes it;
-                                SSA_LAYOUT_THREAD gives SSA_EUNSUPPORTED). */
+                                Bit-sliced engines; Frank's model runs it on the three-warp layout
+                                (SSA_LAYOUT_AUTO takes it; SSA_LAYOUT_THREAD gives
+                                SSA_EUNSUPPORTED), a general network on its one kernel. */
   int32_t pad_pow2;          /* 0 (default): n is uniform on [0, lambda_int), lambda_int = N (N - 1) / 2
                                 (Eq. equation-z; Sec. 3 step 5), and a draw at or above it is redrawn.
                                 1: the total rate is padded with further null events up to 2^K, K the
@@ -117,7 +127,7 @@ typedef struct {
                                 Lambda = k_max 2^K.  Uniformisation at any bound at or above the largest
                                 total propensity samples the same process: the runs are exact either
                                 way, but not draw for draw the same.  Costs 2^K / lambda_int - 1 more
-                                (null) steps, saves every redraw.  Bit-sliced engine only. */
+                                (null) steps, saves every redraw.  Bit-sliced engines only. */
   int32_t reserved[4];
 } ssa_options;
 
@@ -133,7 +143,9 @@ enum {
   SSA_FIELD_EE_HIST = 3,        /* uint64[n_ens][n_snap][65]: enantiomeric-excess histogram of
                                    (L, D) at each snapshot, L the species X of reaction 0
                                    (A + X -> 2X) and D the species Y of reaction 1 (A + Y -> 2Y):
-                                   bin min(63, floor(64 L / (L + D))), bin 64 = L + D == 0 */
+                                   bin min(63, floor(64 L / (L + D))), bin 64 = L + D == 0.
+                                   For a network that is not Frank's, L and D are species 0
+                                   and 1 (D = 0 with a single species) */
   SSA_FIELD_SNAP_COUNTS = 4,    /* int32[n_snap][n_runs][S] (needs keep_snap_counts = 1) */
   SSA_FIELD_COUNTERS = 5,       /* uint64[10]: group steps, lane steps of live runs, real
                                    reactions, null lane steps, redraw rounds, absorbed runs,
@@ -142,7 +154,8 @@ enum {
                                    SSA_LAYOUT_WARPS: 1, 2, or 3 for a batch that used both;
                                    0 no bit-sliced launch) */
   SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,
-                                   and runs not absorbed, per ensemble */
+                                   and [3] the others: not absorbed, absorbed with several
+                                   species left, or with one species of index 3 or above */
 };
 #define SSA_N_COUNTERS 10
 
@@ -161,10 +174,16 @@ void ssa_default_options(ssa_options* opt);
  *     int64[n_runs][n_species] (n0_per_run = 1); every run must have the same total
  *     (Sec. 4: the copies share N_tot).
  *   seed: the Philox key.
- * SSA_EUNSUPPORTED unless the network is Frank's model (Eqs. 1-3) up to a
- * relabelling of species: three species X, Y, A and, in this order,
- * A + X -> 2X, A + Y -> 2Y, X + Y -> 2A; and unless N_tot(N_tot - 1)/2 < 2^31
- * (N_tot <= 65536).  n_runs may be 0.  On success *out owns device memory until
+ * Frank's model (Eqs. 1-3) up to a relabelling of species -- three species X, Y, A
+ * and, in this order, A + X -> 2X, A + Y -> 2Y, X + Y -> 2A -- runs on its own
+ * kernels.  Any other network of at most 8 species and 8 reactions runs on the
+ * general kernel: the uniformisation bound is lambda_int = m_pair C(N_tot, 2) +
+ * u_max N_tot, with m_pair the most reactions on one unordered reactant pair and
+ * u_max the most first-order reactions of one species, and reaction r takes the
+ * integers [S_{r-1}, S_r) of the draw in the order given.  SSA_EUNSUPPORTED beyond
+ * 8 species or reactions, for N_tot > 65536, and when lambda_int >= 2^31;
+ * SSA_EUNSUPPORTED also for a general network with the thread-per-run engine or
+ * SSA_LAYOUT_WARPS.  n_runs may be 0.  On success *out owns device memory until
  * ssa_destroy.
  */
 int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_species,

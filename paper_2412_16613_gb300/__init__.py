@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libbitssa.so")
 SSA_OK, SSA_EINVAL, SSA_EUNSUPPORTED, SSA_ENOMEM = 0, -1, -2, -3
 SSA_ECUDA, SSA_ETIMEOUT, SSA_EOVERFLOW, SSA_ESTATE = -4, -5, -6, -7
 SSA_P64, SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P64_LOGSUM, SSA_P32_PLAIN = 0, 1, 2, 3, 4
-SSA_ENGINE_BITSLICED, SSA_ENGINE_THREAD_PER_RUN = 0, 1
+SSA_ENGINE_BITSLICED, SSA_ENGINE_THREAD_PER_RUN, SSA_ENGINE_GENERAL = 0, 1, 2
 SSA_LAYOUT_AUTO, SSA_LAYOUT_THREAD, SSA_LAYOUT_WARPS = 0, 1, 2
 SSA_FIELD_FINAL_COUNTS, SSA_FIELD_ABSORB_TIME, SSA_FIELD_ABSORB_OUTCOME = 0, 1, 2
 SSA_FIELD_EE_HIST, SSA_FIELD_SNAP_COUNTS, SSA_FIELD_COUNTERS, SSA_FIELD_ENS_ABSORBED = 3, 4, 5, 6

@@ -47,6 +47,8 @@ def _jobs():
                      [f"-DBITSSA_K={k}"]))
         jobs.append((os.path.join(CSRC, "frank_trio_instance.cu"), os.path.join(BUILD, f"frank_trio_k{k:02d}.o"),
                      [f"-DBITSSA_K={k}"]))
+        jobs.append((os.path.join(CSRC, "general_instance.cu"), os.path.join(BUILD, f"general_k{k:02d}.o"),
+                     [f"-DBITSSA_K={k}"]))
     for name in ("frank_dispatch", "thread_per_run", "runtime", "selftest", "noalloc"):
         jobs.append((os.path.join(CSRC, name + ".cu"), os.path.join(BUILD, name + ".o"), []))
     return jobs

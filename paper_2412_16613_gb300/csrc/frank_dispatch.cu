@@ -1,5 +1,6 @@
-// frank_dispatch.cu -- table of the per-K instantiations of the bit-sliced kernel
-// (each built from frank_instance.cu with -DBITSSA_K=<K>).
+// frank_dispatch.cu -- tables of the per-K instantiations of the bit-sliced kernels
+// (each built from frank_instance.cu, frank_trio_instance.cu or general_instance.cu with
+// -DBITSSA_K=<K>).
 #include "internal.h"
 
 namespace bitssa {
@@ -14,7 +15,10 @@ namespace bitssa {
   int frank_regs_k##k(int);                                                                    \
   int frank_trio_launch_k##k(const FrankLaunch&, int, int, void*);                             \
   int frank_trio_occupancy_k##k(int, int, int*);                                               \
-  int frank_trio_regs_k##k(int);
+  int frank_trio_regs_k##k(int);                                                               \
+  int general_launch_k##k(const FrankLaunch&, int, int, int, void*);                           \
+  int general_occupancy_k##k(int, int, int, int*);                                             \
+  int general_regs_k##k(int);
 BITSSA_FOR_EACH_K(BITSSA_DECLARE)
 
 FrankLauncher frank_launcher(int K) {
@@ -82,6 +86,42 @@ int frank_trio_registers(int K, int variant) {
 #define BITSSA_CASE(k) \
   case k:              \
     return frank_trio_regs_k##k(variant);
+    BITSSA_FOR_EACH_K(BITSSA_CASE)
+#undef BITSSA_CASE
+    default:
+      return -1;
+  }
+}
+
+FrankLauncher general_launcher(int K) {
+  switch (K) {
+#define BITSSA_CASE(k) \
+  case k:              \
+    return &general_launch_k##k;
+    BITSSA_FOR_EACH_K(BITSSA_CASE)
+#undef BITSSA_CASE
+    default:
+      return nullptr;
+  }
+}
+
+int general_max_active_blocks(int K, int variant, int block, int smem, int* blocks) {
+  switch (K) {
+#define BITSSA_CASE(k) \
+  case k:              \
+    return general_occupancy_k##k(variant, block, smem, blocks);
+    BITSSA_FOR_EACH_K(BITSSA_CASE)
+#undef BITSSA_CASE
+    default:
+      return -1;
+  }
+}
+
+int general_registers(int K, int variant) {
+  switch (K) {
+#define BITSSA_CASE(k) \
+  case k:              \
+    return general_regs_k##k(variant);
     BITSSA_FOR_EACH_K(BITSSA_CASE)
 #undef BITSSA_CASE
     default:

@@ -41,25 +41,6 @@
 
 namespace bitssa {
 
-// Largest N with N (N - 1) / 2 < 2^K, i.e. the largest Frank system whose
-// lambda_int fits in K planes.
-__host__ __device__ constexpr long long frank_nmax(int K) {
-  long long lo = 1, hi = 1ll << 17;
-  while (lo < hi) {
-    const long long mid = (lo + hi + 1) / 2;
-    if (mid * (mid - 1) / 2 < (1ll << K)) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-__host__ __device__ constexpr int bit_length(long long v) {
-  int b = 0;
-  while (v) {
-    ++b;
-    v >>= 1;
-  }
-  return b;
-}
 
 template <int K>
 struct FrankShape {
@@ -238,6 +219,76 @@ __device__ __forceinline__ void thin_step(const Ensemble& e, WordAt word_at, uin
   x3 &= ~rej;
 }
 
+// The redraw of the lanes in `need` (those with n >= lambda_int).  A lane replaces its planes
+// from p up, p the highest plane where n and lambda_int differ (every plane when they are
+// equal), with the same planes of the next attempt; the planes below p are independent of the
+// rejection and stay.  Planes are visited from the top: `above` collects the lanes that differ
+// above the current plane.  Every call of an attempt is made: a warp takes this path whenever
+// one of its runs is rejected, and the interleaved calls cost little more than one.  Returns
+// false after 64 attempts.
+template <int K>
+__device__ __forceinline__ bool redraw_n(uint32_t (&n)[K], const Ensemble& e, uint32_t sgroup,
+                                         unsigned long long step, uint32_t need, PhiloxKey key,
+                                         unsigned int& redraws) {
+  constexpr int NCR = FrankShape<K>::NCR;
+  for (uint32_t attempt = 1u; need; ++attempt) {
+    if (attempt >= 64u) return false;
+    ++redraws;
+    uint32_t above = 0u;
+    if constexpr (K >= 25) {
+      // wide n: the calls from the top, two at a time, while some lane replaces a lower plane
+#pragma unroll
+      for (int c = NCR - 1; c >= 0; c -= 2) {
+        if (need & ~above) {
+          constexpr int kPair = 2;
+          const int lo = c > 0 ? c - 1 : 0;
+          uint32_t wr[4 * kPair];
+          philox4x32_10_block<kPair>(wr, stream_counter(sgroup, step, attempt, 0u, 0u), (uint32_t)lo, key);
+#pragma unroll
+          for (int j = 4 * kPair - 1; j >= 0; --j) {
+            const int i = 4 * lo + j;
+            if (i <= 4 * c + 3 && i < K) {
+              const uint32_t m = need & ~above;
+              above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
+              n[i] = (n[i] & ~m) | (wr[j] & m);
+            }
+          }
+        }
+      }
+    } else {
+      uint32_t wr[4 * NCR];  // all calls of the attempt at once: their chains interleave
+      philox4x32_10_block<NCR>(wr, stream_counter(sgroup, step, attempt, 0u, 0u), 0u, key);
+#pragma unroll
+      for (int i = K - 1; i >= 0; --i) {
+        const uint32_t m = need & ~above;
+        above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
+        n[i] = (n[i] & ~m) | (wr[i] & m);
+      }
+    }
+    need &= ~bs::less_than_const(n, e.lambda_int);
+  }
+  return true;
+}
+
+// Lanes (among `live`) whose n is at or above lambda_int.  n >= lambda_int needs every plane of
+// lambda_int's leading run of ones set in n: that is tested first (a shallow AND tree), and the
+// full comparison runs only when some lane passes.  A bound padded to 2^K rejects nothing.
+template <int K>
+__device__ __forceinline__ uint32_t rejected_lanes(const uint32_t (&n)[K], const Ensemble& e, uint32_t live) {
+  if (!e.reject) return 0u;
+  uint32_t a[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) a[i] = n[i] | e.top_mask[i];
+#pragma unroll
+  for (int width = K; width > 1; width = (width + 2) / 3) {
+#pragma unroll
+    for (int j = 0; j < (width + 2) / 3; ++j)
+      a[j] = a[3 * j] & (3 * j + 1 < width ? a[3 * j + 1] : 0xFFFFFFFFu) &
+             (3 * j + 2 < width ? a[3 * j + 2] : 0xFFFFFFFFu);
+  }
+  return (a[0] & live) ? ~bs::less_than_const(n, e.lambda_int) & live : 0u;
+}
+
 // Everything one thread keeps about its group between steps (all in registers).
 template <int K, bool PROD>
 struct GroupState {
@@ -406,7 +457,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
                                            const Threshold* thr, unsigned int* s_hist, unsigned int& errors) {
   using Sh = FrankShape<K>;
   constexpr int WP = Sh::WP, WU3 = Sh::WU3, WR1 = Sh::WR1, WR3 = Sh::WR3;
-  constexpr int NC0 = Sh::NC0, NCR = Sh::NCR;
+  constexpr int NC0 = Sh::NC0;
   const PhiloxKey key{(uint32_t)e.seed, (uint32_t)(e.seed >> 32)};
   const int precision = p.precision;
 
@@ -423,71 +474,15 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   for (int i = 0; i < K; ++i) n[i] = w[i];
   // the rejection test and the three comparators are independent borrow chains: run them
   // together, and redo the comparators only in the rare step where a lane redraws
-  // n >= lambda_int needs every plane of lambda_int's leading run of ones set in n: test that
-  // first (a shallow AND tree), and run the full comparison only when some lane passes
-  uint32_t need = 0u;
-  if (e.reject) {  // (a bound padded to 2^K accepts every draw)
-    uint32_t a[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) a[i] = n[i] | e.top_mask[i];
-#pragma unroll
-    for (int width = K; width > 1; width = (width + 2) / 3) {
-#pragma unroll
-      for (int j = 0; j < (width + 2) / 3; ++j)
-        a[j] = a[3 * j] & (3 * j + 1 < width ? a[3 * j + 1] : 0xFFFFFFFFu) &
-               (3 * j + 2 < width ? a[3 * j + 2] : 0xFFFFFFFFu);
-    }
-    if (a[0] & s.live) need = ~bs::less_than_const(n, e.lambda_int) & s.live;
-  }
+  const uint32_t need = rejected_lanes<K>(n, e, s.live);
   uint32_t lt1 = bs::less_than(n, s.S1);
   uint32_t lt2 = bs::less_than(n, s.S2);
   uint32_t lt3 = bs::less_than(n, s.S3);
   if (need) {
-    // A lane with n >= lambda_int replaces its planes from p up, p the highest plane where
-    // n and lambda_int differ (every plane when they are equal), with the same planes of the
-    // next attempt; the planes below p are independent of the rejection and stay.  Planes are
-    // visited from the top: `above` collects the lanes that differ above the current plane.
-    // Every call of the attempt is made: a warp takes this branch whenever one of its 1024
-    // runs is rejected, and the interleaved calls cost little more than one.
-    for (uint32_t attempt = 1u; need; ++attempt) {
-      if (attempt >= 64u) {
-        errors |= kErrRedraw;
-        s.done = true;
-        return;
-      }
-      ++s.redraws;
-      uint32_t above = 0u;
-      if constexpr (K >= 25) {
-        // wide n: the calls from the top, two at a time, while some lane replaces a lower plane
-#pragma unroll
-        for (int c = NCR - 1; c >= 0; c -= 2) {
-          if (need & ~above) {
-            constexpr int kPair = 2;
-            const int lo = c > 0 ? c - 1 : 0;
-            uint32_t wr[4 * kPair];
-            philox4x32_10_block<kPair>(wr, stream_counter(s.sgroup, s.step, attempt, 0u, 0u), (uint32_t)lo, key);
-#pragma unroll
-            for (int j = 4 * kPair - 1; j >= 0; --j) {
-              const int i = 4 * lo + j;
-              if (i <= 4 * c + 3 && i < K) {
-                const uint32_t m = need & ~above;
-                above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
-                n[i] = (n[i] & ~m) | (wr[j] & m);
-              }
-            }
-          }
-        }
-      } else {
-        uint32_t wr[4 * NCR];  // all calls of the attempt at once: their chains interleave
-        philox4x32_10_block<NCR>(wr, stream_counter(s.sgroup, s.step, attempt, 0u, 0u), 0u, key);
-#pragma unroll
-        for (int i = K - 1; i >= 0; --i) {
-          const uint32_t m = need & ~above;
-          above |= n[i] ^ (0u - ((e.lambda_int >> i) & 1u));
-          n[i] = (n[i] & ~m) | (wr[i] & m);
-        }
-      }
-      need &= ~bs::less_than_const(n, e.lambda_int);
+    if (!redraw_n<K>(n, e, s.sgroup, s.step, need, key, s.redraws)) {
+      errors |= kErrRedraw;
+      s.done = true;
+      return;
     }
     lt1 = bs::less_than(n, s.S1);
     lt2 = bs::less_than(n, s.S2);

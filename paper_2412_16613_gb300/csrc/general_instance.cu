@@ -1,0 +1,62 @@
+// general_instance.cu -- one instantiation of the general-network bit-sliced kernel;
+// compiled once per K (number of propensity planes) with -DBITSSA_K=<K>.
+#include <cuda_runtime.h>
+
+#include "general_kernel.cuh"
+
+#ifndef BITSSA_K
+#error "compile with -DBITSSA_K=<planes>"
+#endif
+
+#define BITSSA_CAT2(a, b) a##b
+#define BITSSA_CAT(a, b) BITSSA_CAT2(a, b)
+
+namespace bitssa {
+
+// variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64)
+int BITSSA_CAT(general_launch_k, BITSSA_K)(const FrankLaunch& p, int grid, int block, int smem,
+                                            void* stream) {
+  const cudaStream_t st = (cudaStream_t)stream;
+  const bool prod = p.precision == kP64;
+  if (p.ens_table) {
+    if (prod) general_kernel<BITSSA_K, true, true><<<grid, block, smem, st>>>(p);
+    else general_kernel<BITSSA_K, true, false><<<grid, block, smem, st>>>(p);
+  } else {
+    if (prod) general_kernel<BITSSA_K, false, true><<<grid, block, smem, st>>>(p);
+    else general_kernel<BITSSA_K, false, false><<<grid, block, smem, st>>>(p);
+  }
+  return (int)cudaGetLastError();
+}
+
+namespace {
+template <typename F>
+int with_kernel(int variant, F f) {
+  switch (variant & 3) {
+    case 0: return f(general_kernel<BITSSA_K, false, false>);
+    case 1: return f(general_kernel<BITSSA_K, true, false>);
+    case 2: return f(general_kernel<BITSSA_K, false, true>);
+    default: return f(general_kernel<BITSSA_K, true, true>);
+  }
+}
+}  // namespace
+
+// Occupancy at `smem` bytes of dynamic shared memory; lifts the kernel's dynamic shared-memory
+// limit first when the request exceeds the default 48 KB.
+int BITSSA_CAT(general_occupancy_k, BITSSA_K)(int variant, int block, int smem, int* blocks) {
+  return with_kernel(variant, [&](auto kern) {
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return (int)e;
+    }
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, block, (size_t)smem);
+  });
+}
+
+int BITSSA_CAT(general_regs_k, BITSSA_K)(int variant) {
+  return with_kernel(variant, [&](auto kern) {
+    cudaFuncAttributes a;
+    return cudaFuncGetAttributes(&a, kern) == cudaSuccess ? a.numRegs : -1;
+  });
+}
+
+}  // namespace bitssa

@@ -1,0 +1,501 @@
+// general_kernel.cuh -- the bit-sliced Gillespie step loop for any conserved mass-action
+// network of order 1 or 2 (Sec. 2) on sm_103a.
+//
+// One thread owns one group of 32 runs (lane l of every plane is run 32 g + l).  The
+// Frank kernel keeps cumulative propensities and their linear increments; this one
+// recomputes every propensity at every step from the count planes, with the bit-sliced
+// schoolbook product of Sec. 4.1:
+//   h_r = x_a x_b            (A + B -> ...)
+//   h_r = x_a (x_a - 1) / 2  (2A -> ...)
+//   h_r = x_a                (A -> ...)
+// The count planes live in shared memory as [species][plane][thread] words, so that a
+// reaction's reactants are found by index at run time and one kernel serves every network
+// of up to 8 species and 8 reactions; the per-step values (n, the running sum S, one
+// product) stay in registers.
+//
+// One group step (Sec. 3, steps 1-7, the draw done by Sec. 4's steps a-d), in the order of
+// the Frank kernel and the oracle:
+//   1. Philox words of attempt 0: the K planes of n (rejection and partial redraw above
+//      lambda_int unless the bound is padded to 2^K) and the clock's two words.
+//   2. Clock, snapshots (state before the event), t_end.
+//   3. For r = 0..R-1: h_r, S += h_r, lt_r = [n < S], xi_r = lt_r & ~lt_{r-1}
+//      (Eq. equation-changer); a lane with n >= S_R fires nothing (a ghost or null event).
+//   4. Thinning of reactions with k_r < k_max.
+//   5. x_i += sum_r xi_r nu_ri for every species (Eq. equation-v), two's complement.
+//   6. Absorption: a lane none of whose reactions with k_r > 0 has a nonzero propensity.
+#pragma once
+
+#include <cstdint>
+
+#include "bitslice.cuh"
+#include "frank_kernel.cuh"
+#include "internal.h"
+#include "philox.cuh"
+
+namespace bitssa {
+
+// Count planes a general network may need at K propensity planes when it has a reaction of
+// order 2: lambda_int >= N (N - 1) / 2, so N is at most Frank's largest N for K planes.
+template <int K>
+struct GeneralShape {
+  static constexpr int BM = FrankShape<K>::B;     // count planes read by the products
+  static constexpr int NC0 = (K + 2 + 3) / 4;     // Philox calls for n and tau
+  static constexpr int B1 = K < kMaxCountPlanes ? K : kMaxCountPlanes;  // first-order reads
+};
+
+// The state one thread keeps in registers; the counts are in shared memory.
+template <bool PROD>
+struct GeneralState {
+  uint32_t live;     // lanes that can still react
+  uint32_t valid;    // lanes holding a run
+  uint32_t sgroup;   // stream group index
+  int nvalid;
+  int ens;
+  int snap;
+  unsigned long long step;
+  Clock<PROD> clk;
+  unsigned long long reactions, lane_steps;
+  unsigned int redraws;
+  bool done;
+};
+
+// Shared-memory view of one thread's count planes: plane i of species s at x[(s PL + i) T].
+struct CountPlanes {
+  uint32_t* base;  // this thread's word of plane 0 of species 0
+  int stride;      // threads per block
+  int PL;          // planes stored per species
+  __device__ __forceinline__ uint32_t& at(int s, int i) const { return base[(s * PL + i) * stride]; }
+};
+
+template <int W>
+__device__ __forceinline__ void load_planes(uint32_t (&x)[W], const CountPlanes& c, int s) {
+#pragma unroll
+  for (int i = 0; i < W; ++i) x[i] = c.at(s, i);
+}
+
+// Lanes with a nonzero count of species s, and with at least two.
+__device__ __forceinline__ void count_masks(const CountPlanes& c, int s, int B, uint32_t& nz, uint32_t& two) {
+  nz = c.at(s, 0);
+  two = 0u;
+  for (int i = 1; i < B; ++i) two |= c.at(s, i);
+  nz |= two;
+}
+
+// Count planes of an ensemble: the bit length of its N_tot.
+__device__ __forceinline__ int count_planes(const Ensemble& e) { return 32 - __clz(e.n_tot); }
+
+// Lanes where some reaction with k_r > 0 has h_r > 0: h = x_a x_b > 0 iff both are nonzero,
+// x_a (x_a - 1) / 2 > 0 iff x_a >= 2, x_a > 0 iff it is nonzero.
+__device__ __forceinline__ uint32_t general_live(const Network& net, const Ensemble& e, const CountPlanes& c) {
+  const int B = count_planes(e);
+  uint32_t nz[kMaxSpecies], two[kMaxSpecies];
+#pragma unroll
+  for (int s = 0; s < kMaxSpecies; ++s) {
+    nz[s] = two[s] = 0u;
+    if (s < net.S) count_masks(c, s, B, nz[s], two[s]);
+  }
+  uint32_t m = 0u;
+#pragma unroll
+  for (int r = 0; r < kMaxReactions; ++r) {
+    if (r >= net.R || !((e.active >> r) & 1u)) continue;
+    uint32_t h = 0u;
+    // (the species indices are run-time values: pick the masks by an unrolled compare)
+#pragma unroll
+    for (int s = 0; s < kMaxSpecies; ++s) {
+      if (s >= net.S) continue;
+      if (net.order[r] == 1 && s == net.a[r]) h = nz[s];
+      if (net.order[r] == 2 && net.a[r] == net.b[r] && s == net.a[r]) h = two[s];
+    }
+    if (net.order[r] == 2 && net.a[r] != net.b[r]) {
+      uint32_t ha = 0u, hb = 0u;
+#pragma unroll
+      for (int s = 0; s < kMaxSpecies; ++s) {
+        if (s == net.a[r]) ha = nz[s];
+        if (s == net.b[r]) hb = nz[s];
+      }
+      h = ha & hb;
+    }
+    m |= h;
+  }
+  return m;
+}
+
+// h (K planes) = the propensity of reaction r in every lane, from the count planes.
+template <int K>
+__device__ __forceinline__ void general_propensity(uint32_t (&h)[K], const Network& net, int r,
+                                                   const CountPlanes& c, int B) {
+  using Sh = GeneralShape<K>;
+  constexpr int BM = Sh::BM;
+  const int a = net.a[r];
+  if (net.order[r] == 1) {  // h = x_a, zero-extended
+#pragma unroll
+    for (int i = 0; i < K; ++i) h[i] = (i < Sh::B1 && i < B) ? c.at(a, i) : 0u;
+    return;
+  }
+  uint32_t xa[BM];
+  load_planes(xa, c, a);
+  if (net.b[r] != a) {  // h = x_a x_b
+    uint32_t xb[BM];
+    load_planes(xb, c, net.b[r]);
+    bs::multiply(h, xa, xb);
+    return;
+  }
+  // h = x_a (x_a - 1) / 2: the product is even and below 2^(K+1); drop its plane 0
+  uint32_t xm[BM];
+  uint32_t borrow = 0xFFFFFFFFu;  // x_a - 1
+#pragma unroll
+  for (int i = 0; i < BM; ++i) {
+    xm[i] = xa[i] ^ borrow;
+    borrow &= ~xa[i];
+  }
+  uint32_t p[K + 1];
+  bs::multiply(p, xa, xm);
+#pragma unroll
+  for (int i = 0; i < K; ++i) h[i] = p[i + 1];
+}
+
+// Set up a group: counts into shared memory (padding lanes hold zero counts and never react),
+// the live lanes, the clock.
+template <int K, bool PROD>
+__device__ __forceinline__ void general_init(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                             const Threshold* thr, long long group_local, int ens_index,
+                                             const CountPlanes& c, unsigned int* s_hist);
+
+template <int K, bool PROD>
+__device__ __forceinline__ void general_capture(const FrankLaunch& p, const GeneralState<PROD>& s,
+                                                const Ensemble& e, int snap, const CountPlanes& c,
+                                                unsigned int* s_hist);
+
+// Counts of lane l: species s from its planes.
+__device__ __forceinline__ int lane_count(const CountPlanes& c, int s, int B, int l) {
+  int v = 0;
+  for (int i = 0; i < B; ++i) v |= (int)((c.at(s, i) >> l) & 1u) << i;
+  return v;
+}
+
+__device__ __forceinline__ long long general_row0(uint32_t sgroup, const Ensemble& e) {
+  return e.run_offset + ((long long)sgroup - e.group_base) * 32;
+}
+
+template <int K, bool PROD>
+__device__ __forceinline__ void general_capture(const FrankLaunch& p, const GeneralState<PROD>& s,
+                                                const Ensemble& e, int snap, const CountPlanes& c,
+                                                unsigned int* s_hist) {
+  const Network& net = p.net;
+  const int B = count_planes(e);
+  for (int l = 0; l < s.nvalid; ++l) {
+    const int cx = net.hist_x >= 0 ? lane_count(c, net.hist_x, B, l) : 0;
+    const int cy = net.hist_y >= 0 ? lane_count(c, net.hist_y, B, l) : 0;
+    const int bin = ee_bin(cx, cy);
+    if (s_hist) atomicAdd(&s_hist[snap * kHistBins + bin], 1u);
+    else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + bin], 1ull);
+    if (p.snap_counts) {
+      int* o = p.snap_counts + ((long long)snap * p.n_runs_total + general_row0(s.sgroup, e) + l) * net.S;
+      for (int sp = 0; sp < net.S; ++sp) o[sp] = lane_count(c, sp, B, l);
+    }
+  }
+}
+
+template <int K, bool PROD>
+__device__ __forceinline__ void general_init(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                             const Threshold* thr, long long group_local, int ens_index,
+                                             const CountPlanes& c, unsigned int* s_hist) {
+  const Network& net = p.net;
+  const long long run0 = group_local * 32;
+  const long long left = e.n_runs - run0;
+  s.nvalid = left >= 32 ? 32 : (int)left;
+  s.valid = s.nvalid >= 32 ? 0xFFFFFFFFu : ((1u << s.nvalid) - 1u);
+  s.sgroup = (uint32_t)(e.group_base + group_local);
+  s.ens = ens_index;
+  const long long row0 = e.run_offset + run0;
+  for (int sp = 0; sp < net.S; ++sp) {
+    for (int i = 0; i < c.PL; ++i) {
+      uint32_t w = 0u;
+      if (p.init_counts) {
+        for (int l = 0; l < s.nvalid; ++l) w |= (uint32_t)((p.init_counts[(row0 + l) * net.S + sp] >> i) & 1) << l;
+      } else if ((e.init[sp] >> i) & 1) {
+        w = s.valid;
+      }
+      c.at(sp, i) = w;
+    }
+  }
+  s.live = general_live(net, e, c) & s.valid;
+  uint32_t at0 = s.valid & ~s.live;  // runs that start absorbed are absorbed at t = 0
+  while (at0) {
+    const int l = __ffs(at0) - 1;
+    at0 &= at0 - 1;
+    p.t_abs[row0 + l] = 0.0;
+  }
+  s.step = 0;
+  s.clk.reset();
+  s.snap = 0;
+  s.clk.aim(thr[0]);
+  s.reactions = s.lane_steps = 0;
+  s.redraws = 0;
+  s.done = s.live == 0u;
+  if (s.done)
+    for (; s.snap < p.n_snap; ++s.snap) general_capture<K, PROD>(p, s, e, s.snap, c, s_hist);
+}
+
+// One group step (see the file header).
+template <int K, bool PROD>
+__device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                             const Threshold* thr, const CountPlanes& c, unsigned int* s_hist,
+                                             unsigned int& errors) {
+  using Sh = GeneralShape<K>;
+  constexpr int NC0 = Sh::NC0;
+  const Network& net = p.net;
+  const int B = count_planes(e);
+  const PhiloxKey key{(uint32_t)e.seed, (uint32_t)(e.seed >> 32)};
+  const int precision = p.precision;
+
+  if (p.step_budget > 0 && (long long)s.step >= p.step_budget) {
+    errors |= kErrTimeout;
+    s.done = true;
+    return;
+  }
+  // (1) the random words of attempt 0; n, redrawn where it is at or above lambda_int
+  uint32_t w[4 * NC0];
+  philox4x32_10_block<NC0>(w, stream_counter(s.sgroup, s.step, 0u, 0u, 0u), 0u, key);
+  uint32_t n[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) n[i] = w[i];
+  // the paper's shared draw (Sec. 4, step a): lane 0's n, redrawn whether or not it is live
+  const uint32_t need = rejected_lanes<K>(n, e, e.shared_n ? 1u : s.live);
+  if (need && !redraw_n<K>(n, e, s.sgroup, s.step, need, key, s.redraws)) {
+    errors |= kErrRedraw;
+    s.done = true;
+    return;
+  }
+  if (e.shared_n) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) n[i] = 0u - (n[i] & 1u);
+  }
+
+  // (2) the clock: the candidate time of this step's event, snapshots, t_end
+  Clock<PROD> nx;
+  bool crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision);
+  while (crossed) {
+    if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
+      s.done = true;
+      return;
+    }
+    general_capture<K, PROD>(p, s, e, s.snap, c, s_hist);
+    ++s.snap;
+    nx.aim(thr[s.snap]);
+    if constexpr (PROD) crossed = clock_crosses(nx);
+    else crossed = clock_crosses(nx, precision);
+  }
+  s.clk = nx;
+
+  // (3) the CDF walk over the reactions in order: S = sum_{p<=r} h_p, xi_r = [S_{r-1} <= n < S_r]
+  uint32_t xi[kMaxReactions];
+  {
+    uint32_t S[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) S[i] = 0u;
+    uint32_t lt_prev = 0u;
+#pragma unroll 1
+    for (int r = 0; r < net.R; ++r) {
+      uint32_t h[K];
+      general_propensity<K>(h, net, r, c, B);
+      bs::add_signed(S, h, 0u);
+      const uint32_t lt = bs::less_than(n, S);
+      const uint32_t x = lt & ~lt_prev;
+      lt_prev = lt;
+      // (a run-time r cannot index a register array: place x by an unrolled compare)
+#pragma unroll
+      for (int q = 0; q < kMaxReactions; ++q)
+        if (q == r) xi[q] = x;
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxReactions; ++q)
+      if (q >= net.R) xi[q] = 0u;
+  }
+
+  // (4) thinning for k_r < k_max: U (q bits, most significant first, from word K+2 on) < T_r
+  if (e.thin) {
+    uint32_t tested = 0u;
+#pragma unroll
+    for (int r = 0; r < kMaxReactions; ++r)
+      if (!((e.thin_always >> r) & 1u)) tested |= xi[r];
+    uint32_t und = tested & s.live, rej = tested & ~s.live;
+    const int q = e.thin_bits;
+    auto bit = [&](int i, uint32_t word) {
+      const int pos = q - 1 - i;
+      uint32_t tb = 0u;
+#pragma unroll
+      for (int r = 0; r < kMaxReactions; ++r)
+        if ((((unsigned long long)e.thin_T[r] >> pos) & 1ull) != 0ull) tb |= xi[r];
+      const uint32_t lower = und & ~word & tb;
+      const uint32_t higher = und & word & ~tb;
+      rej |= higher;
+      und &= ~(lower | higher);
+    };
+    int i = 0;
+#pragma unroll
+    for (int k = K + 2; k < 4 * NC0; ++k)
+      if (k - (K + 2) < q) bit(i++, w[k]);
+    for (uint32_t call = NC0; und != 0u && i < q; ++call) {
+      const uint4 rw = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, call), key);
+      const uint32_t wv[4] = {rw.x, rw.y, rw.z, rw.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i < q) bit(i++, wv[j]);
+    }
+    rej |= und;  // U == T: not below
+#pragma unroll
+    for (int r = 0; r < kMaxReactions; ++r) xi[r] &= ~rej;
+  }
+
+  // (5) the counts: x_s += sum_r xi_r nu_rs (nu in [-2, 2]: three two's-complement planes)
+  uint32_t fired = 0u;
+#pragma unroll
+  for (int r = 0; r < kMaxReactions; ++r) fired |= xi[r];
+  ++s.step;
+  if (!fired) return;
+  for (int sp = 0; sp < net.S; ++sp) {
+    uint32_t d0 = 0u, d1 = 0u, d2 = 0u;
+#pragma unroll
+    for (int r = 0; r < kMaxReactions; ++r) {
+      if (r >= net.R) continue;
+      const int v = net.nu[r][sp];
+      if (v & 1) d0 |= xi[r];
+      if (v & 2) d1 |= xi[r];
+      if (v & 4) d2 |= xi[r];
+    }
+    if (!(d0 | d1 | d2)) continue;
+    uint32_t carry = 0u;
+    for (int i = 0; i < B; ++i) {
+      const uint32_t d = i == 0 ? d0 : (i == 1 ? d1 : d2);
+      const uint32_t x = c.at(sp, i);
+      c.at(sp, i) = bs::xor3(x, d, carry);
+      carry = bs::maj(x, d, carry);
+    }
+  }
+  s.reactions += (unsigned)__popc(fired);
+
+  // (6) absorption
+  const uint32_t now_live = general_live(net, e, c) & s.live;
+  uint32_t newly = s.live & ~now_live;
+  if (newly) {
+    const double tn = s.clk.time(e, precision);
+    s.lane_steps += (unsigned long long)__popc(newly) * s.step;
+    const long long row0 = general_row0(s.sgroup, e);
+    while (newly) {
+      const int l = __ffs(newly) - 1;
+      newly &= newly - 1;
+      p.t_abs[row0 + l] = tn;
+    }
+    s.live = now_live;
+    if (!s.live) {
+      s.done = true;
+      for (; s.snap < p.n_snap; ++s.snap) general_capture<K, PROD>(p, s, e, s.snap, c, s_hist);
+    }
+  }
+}
+
+// Outputs of a finished group: final counts, outcomes, per-ensemble tallies, counters.
+template <int K, bool PROD>
+__device__ __forceinline__ void general_finish(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                               const CountPlanes& c) {
+  const Network& net = p.net;
+  const int B = count_planes(e);
+  unsigned long long outc[4] = {0, 0, 0, 0};
+  const long long row0 = general_row0(s.sgroup, e);
+  for (int l = 0; l < s.nvalid; ++l) {
+    int* o = p.final_counts + (row0 + l) * net.S;
+    int nz = 0, who = -1;
+    for (int sp = 0; sp < net.S; ++sp) {
+      const int v = lane_count(c, sp, B, l);
+      o[sp] = v;
+      if (v) {
+        ++nz;
+        who = sp;
+      }
+    }
+    signed char oc = -1;
+    if (!((s.live >> l) & 1u)) {
+      oc = nz == 1 ? (signed char)who : (signed char)-2;
+      outc[(nz == 1 && who < 3) ? who : 3] += 1;  // [3]: another species, or several left
+    } else {
+      p.t_abs[row0 + l] = __longlong_as_double(0x7FF0000000000000ll);
+      outc[3] += 1;
+    }
+    p.outcome[row0 + l] = oc;
+  }
+  if (p.ens_absorbed) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (outc[k]) atomicAdd(&p.ens_absorbed[(long long)s.ens * 4 + k], outc[k]);
+  }
+  s.lane_steps += (unsigned long long)__popc(s.live) * s.step;  // lanes that never absorbed
+  atomicAdd(&p.counters[kGroupSteps], s.step);
+  atomicAdd(&p.counters[kLaneSteps], s.lane_steps);
+  atomicAdd(&p.counters[kReactions], s.reactions);
+  atomicAdd(&p.counters[kNullLaneSteps], s.lane_steps - s.reactions);
+  if (s.redraws) atomicAdd(&p.counters[kRedrawRounds], (unsigned long long)s.redraws);
+  atomicAdd(&p.counters[kAbsorbed], (unsigned long long)__popc(s.valid & ~s.live));
+  atomicAdd(&p.counters[kGroupsDone], 1ull);
+  atomicMax(&p.counters[kMaxGroupSteps], s.step);
+}
+
+// Planes stored per species: enough for the products' reads and for the counts themselves.
+__host__ __device__ constexpr int general_planes(int BM, int B) { return BM > B ? BM : B; }
+
+// The persistent kernel: the queue, warp-synchronous loop and histogram handling of the
+// Frank kernel.  Dynamic shared memory: the histogram (single ensemble), then the count
+// planes of every thread of the block.
+template <int K, bool BATCH, bool PROD>
+__global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ FrankLaunch p) {
+  extern __shared__ unsigned int s_mem[];
+  const bool smem_hist = !BATCH && p.n_snap > 0;
+  unsigned int* s_hist = smem_hist ? s_mem : nullptr;
+  const int hist_words = smem_hist ? p.n_snap * kHistBins : 0;
+  if (smem_hist) {
+    for (int i = threadIdx.x; i < hist_words; i += blockDim.x) s_mem[i] = 0u;
+    __syncthreads();
+  }
+  const CountPlanes c{s_mem + hist_words + threadIdx.x, (int)blockDim.x,
+                      general_planes(GeneralShape<K>::BM, p.net.B)};
+  unsigned int errors = 0u;
+  GeneralState<PROD> s;
+  s.done = true;
+  bool active = false, exhausted = false;
+  const Threshold* thr = p.thr;
+  for (;;) {
+    if (!active && !exhausted) {
+      const long long item = (long long)atomicAdd(p.queue, 1ull) + p.item_begin;
+      if (item >= p.item_end) {
+        exhausted = true;
+      } else if (!BATCH) {
+        general_init<K, PROD>(p, s, p.ens, thr, item, 0, c, s_hist);
+        active = true;
+      } else {
+        const int ei = p.item_ens[item];
+        thr = p.thr + (long long)ei * (p.n_snap + 1);
+        general_init<K, PROD>(p, s, p.ens_table[ei], thr, p.item_group[item], ei, c, nullptr);
+        active = true;
+      }
+    }
+    if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
+    if (active) {
+      const Ensemble& e = BATCH ? p.ens_table[s.ens] : p.ens;
+      if (!s.done) general_step<K, PROD>(p, s, e, thr, c, s_hist, errors);
+      if (s.done) {
+        general_finish<K, PROD>(p, s, e, c);
+        active = false;
+      }
+    }
+    __syncwarp();
+  }
+  const unsigned int err = __reduce_or_sync(0xFFFFFFFFu, errors);
+  if ((threadIdx.x & 31) == 0 && err) atomicOr(p.status, err);
+  if (smem_hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < hist_words; i += blockDim.x)
+      if (s_mem[i]) atomicAdd(&p.hist[i], (unsigned long long)s_mem[i]);
+  }
+}
+
+}  // namespace bitssa

@@ -7,11 +7,34 @@
 
 namespace bitssa {
 
+// Largest N with N (N - 1) / 2 < 2^K, i.e. the largest Frank system whose
+// lambda_int fits in K planes.
+__host__ __device__ constexpr long long frank_nmax(int K) {
+  long long lo = 1, hi = 1ll << 17;
+  while (lo < hi) {
+    const long long mid = (lo + hi + 1) / 2;
+    if (mid * (mid - 1) / 2 < (1ll << K)) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__host__ __device__ constexpr int bit_length(long long v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
+}
+
 constexpr int kMaxSnap = 64;
 constexpr int kHistBins = 65;  // 64 enantiomeric-excess bins + one for L + D == 0
 constexpr int kCounters = 10;
 constexpr int kMaxK = 31;      // random / propensity planes: N_tot (N_tot - 1) / 2 < 2^31
 constexpr int kTrioBlock = 96; // threads of a block of the three-warp layout (32 groups)
+constexpr int kMaxSpecies = 8;   // general networks: species
+constexpr int kMaxReactions = 8; // general networks: reactions
+constexpr int kMaxCountPlanes = 17;  // counts up to N_tot = 65536
 
 // Clock precision modes (same values as SSA_P64 ... in bitssa.h).
 enum Precision { kP64 = 0, kP32Kahan = 1, kP32D64Acc = 2, kP64LogSum = 3, kP32Plain = 4 };
@@ -48,20 +71,21 @@ struct Threshold {
   int pad;
 };
 
-// Per-ensemble constants.  Species are in the kernel's canonical Frank order
-// (L, D, A): reactions A+L->2L, A+D->2D, L+D->2A.
+// Per-ensemble constants.  For Frank's model species are in the kernel's canonical
+// order (L, D, A): reactions A+L->2L, A+D->2D, L+D->2A; for a general network they
+// are the caller's species and reactions.
 struct Ensemble {
   unsigned long long seed;
   long long n_runs;        // runs of this ensemble in this context
   long long run_offset;    // row of the ensemble's first run in the output fields
   long long group_base;    // stream group index of the context's first group (first_run / 32)
-  long long thin_T[3];     // thinning thresholds T_r (bit patterns of uint64)
+  long long thin_T[kMaxReactions];  // thinning thresholds T_r (bit patterns of uint64)
   double lambda;           // k_max * lambda_int
   float inv_lambda_f;      // (float)(1 / lambda)
-  unsigned int lambda_int; // N (N - 1) / 2
+  unsigned int lambda_int; // N (N - 1) / 2 for Frank; m_pair C(N, 2) + u_max N in general
   int n_tot;
   int K;                   // bit length of lambda_int
-  int init[3];             // shared initial counts (canonical order)
+  int init[kMaxSpecies];   // shared initial counts (canonical order for Frank)
   unsigned int thin_always;  // bit r: k_r == k_max
   unsigned int active;       // bit r: k_r > 0
   int thin;                  // any reaction with k_r < k_max
@@ -91,6 +115,25 @@ Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], in
 // The crossing threshold of time t for total rate lambda, in every form a clock compares.
 Threshold make_threshold(double t, double lambda);
 
+// A conserved mass-action network of order 1 or 2 (Sec. 2), in the caller's species and
+// reaction order, for the general bit-sliced kernel.
+struct Network {
+  int S, R;
+  int B;                             // count planes: bit length of N_tot
+  int order[kMaxReactions];          // 1 or 2
+  int a[kMaxReactions];              // first reactant
+  int b[kMaxReactions];              // second reactant (a for 2X); -1 for first order
+  int nu[kMaxReactions][kMaxSpecies];  // products - reactants, in [-2, 2]
+  int hist_x, hist_y;                // species binned by the ee histogram (x: "L", y: "D")
+};
+
+// Per-ensemble constants of a general network from their definitions: lambda_int =
+// m_pair C(N, 2) + u_max N (2^K when pad_pow2), K = the bit length of the unpadded bound,
+// the thinning thresholds T_r = floor(k_r / k_max 2^q).
+Ensemble make_general_ensemble(const Network& net, long long n_tot, const int* init, const double* k, int q,
+                               unsigned long long seed, long long n_runs, long long run_offset,
+                               long long group_base, int pad_pow2, unsigned long long* lambda_unpadded);
+
 // One launch of the bit-sliced kernel for one K.
 struct FrankLaunch {
   Ensemble ens;                   // used when ens_table == nullptr (one ensemble)
@@ -117,6 +160,7 @@ struct FrankLaunch {
   unsigned long long* counters;   // [kCounters]
   unsigned int* status;           // error flags
   unsigned long long* queue;      // work-item counter of this launch
+  Network net;                    // general kernel only
 };
 
 // One launch of the one-thread-per-run baseline.
@@ -150,6 +194,12 @@ int frank_max_active_blocks(int K, int variant, int block, int smem, int* blocks
 int frank_registers(int K, int variant);
 // The three-warp layout (block of kTrioBlock threads serving 32 groups).
 using FrankTrioLauncher = int (*)(const FrankLaunch&, int grid, int smem, void* stream);
+// The general-network kernel (one thread per group; counts in shared memory).
+FrankLauncher general_launcher(int K);
+int general_max_active_blocks(int K, int variant, int block, int smem, int* blocks);
+int general_registers(int K, int variant);
+// Shared memory of the general kernel per block of `block` threads, histogram excluded.
+int general_smem_bytes(const Network& net, int K, int block);
 FrankTrioLauncher frank_trio_launcher(int K);
 int frank_trio_max_active_blocks(int K, int variant, int smem, int* blocks);
 int frank_trio_registers(int K, int variant);

@@ -68,6 +68,57 @@ Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], in
   return e;
 }
 
+// Per-ensemble constants of a general network.  lambda_int = m_pair C(N, 2) + u_max N bounds
+// sum_r h_r over every state with N molecules: the pairs {i, j} (i < j) and {i, i} carry
+// n_i n_j and C(n_i, 2), which sum to C(N, 2) (Eq. equation-z), and each carries at most m_pair
+// reactions; each species carries at most u_max first-order reactions of propensity n_i <= N.
+Ensemble make_general_ensemble(const Network& net, long long n_tot, const int* init, const double* k, int q,
+                               unsigned long long seed, long long n_runs, long long run_offset,
+                               long long group_base, int pad_pow2, unsigned long long* lambda_unpadded) {
+  Ensemble e;
+  std::memset(&e, 0, sizeof e);
+  e.seed = seed;
+  e.n_runs = n_runs;
+  e.run_offset = run_offset;
+  e.group_base = group_base;
+  e.n_tot = (int)n_tot;
+  int pair[kMaxSpecies][kMaxSpecies] = {{0}}, uni[kMaxSpecies] = {0};
+  for (int r = 0; r < net.R; ++r) {
+    if (net.order[r] == 2) ++pair[std::min(net.a[r], net.b[r])][std::max(net.a[r], net.b[r])];
+    else ++uni[net.a[r]];
+  }
+  int m_pair = 0, u_max = 0;
+  for (int i = 0; i < net.S; ++i) {
+    u_max = std::max(u_max, uni[i]);
+    for (int j = 0; j < net.S; ++j) m_pair = std::max(m_pair, pair[i][j]);
+  }
+  const unsigned long long N = (unsigned long long)n_tot;
+  const unsigned long long z = (unsigned long long)m_pair * (N * (N - 1) / 2ull) + (unsigned long long)u_max * N;
+  if (lambda_unpadded) *lambda_unpadded = z;
+  e.K = bits_of(z);
+  const unsigned long long lam = pad_pow2 ? (1ull << std::min(e.K, 31)) : z;
+  e.lambda_int = (unsigned int)lam;
+  e.reject = pad_pow2 ? 0 : 1;
+  set_precheck(e);
+  double kmax = 0.0;
+  for (int r = 0; r < net.R; ++r) kmax = std::max(kmax, k[r]);
+  e.lambda = kmax * (double)lam;
+  e.inv_lambda_f = (float)(1.0 / e.lambda);
+  e.thin_bits = q;
+  for (int i = 0; i < net.S; ++i) e.init[i] = init ? init[i] : 0;
+  for (int r = 0; r < net.R; ++r) {
+    if (k[r] > 0.0) e.active |= 1u << r;
+    if (k[r] == kmax) {
+      e.thin_always |= 1u << r;
+      e.thin_T[r] = 0;
+    } else {
+      e.thin_T[r] = (long long)(unsigned long long)std::floor(std::ldexp(k[r] / kmax, q));
+      e.thin = 1;
+    }
+  }
+  return e;
+}
+
 // The crossing threshold of time t for total rate lambda.
 Threshold make_threshold(double t, double lambda) {
   Threshold h;
@@ -121,7 +172,10 @@ struct ssa_ctx {
   Allocator alloc;
   std::string err;
   int S = 3;
+  int R = 3;
   int perm[3] = {0, 1, 2};  // canonical species (L, D, A) -> caller's species index
+  bool general = false;     // the general-network kernel runs this context
+  Network net{};            // the network, for the general kernel
   bool batch = false;
   int n_ens = 0;
   long long n_runs_total = 0;
@@ -229,7 +283,9 @@ void dev_free_all(ssa_ctx* c) {
 // Validation of the network: order 1 or 2, conservation of the total count
 // (Sec. 2), and recognition of Frank's model (Eqs. 1-3) up to relabelling.
 // ---------------------------------------------------------------------------
-int check_network(const int32_t* reac, const int32_t* prod, int S, int R, int perm[3], std::string* why) {
+int check_network(const int32_t* reac, const int32_t* prod, int S, int R, int perm[3], bool* frank,
+                  std::string* why) {
+  *frank = false;
   if (!reac || !prod) return (*why = "null stoichiometry", SSA_EINVAL);
   if (S < 1 || R < 1 || S > 64 || R > 64) return (*why = "n_species / n_reactions out of range", SSA_EINVAL);
   for (int r = 0; r < R; ++r) {
@@ -245,7 +301,9 @@ int check_network(const int32_t* reac, const int32_t* prod, int S, int R, int pe
     if (made != order)
       return (*why = "reaction " + std::to_string(r) + " does not conserve the total count", SSA_EINVAL);
   }
-  if (S != 3 || R != 3) return (*why = "only Frank's model (3 species, 3 reactions) is supported", SSA_EUNSUPPORTED);
+  if (S > kMaxSpecies || R > kMaxReactions)
+    return (*why = "at most 8 species and 8 reactions", SSA_EUNSUPPORTED);
+  if (S != 3 || R != 3) return SSA_OK;  // a general network
   // reaction 2: X + Y -> 2A
   int A = -1;
   for (int i = 0; i < 3; ++i)
@@ -259,18 +317,45 @@ int check_network(const int32_t* reac, const int32_t* prod, int S, int R, int pe
   int X = -1, Y = -1;
   const bool ok = A >= 0 && is_auto(0, X) && is_auto(1, Y) && X != Y && reac[2 * 3 + X] == 1 &&
                   reac[2 * 3 + Y] == 1 && reac[2 * 3 + A] == 0 && prod[2 * 3 + X] == 0 && prod[2 * 3 + Y] == 0;
-  if (!ok)
-    return (*why = "network is not Frank's model A+X->2X, A+Y->2Y, X+Y->2A (in this reaction order)",
-            SSA_EUNSUPPORTED);
+  if (!ok) return SSA_OK;  // a general network
   perm[0] = X;
   perm[1] = Y;
   perm[2] = A;
+  *frank = true;
   return SSA_OK;
 }
 
-int check_rates(const double* k, std::string* why) {
+// The network in the form the general kernel reads.  The ee histogram bins Frank's X and Y when
+// the network is Frank's model, else species 0 and 1.
+Network make_network(const int32_t* reac, const int32_t* prod, int S, int R, bool frank, const int perm[3]) {
+  Network net;
+  std::memset(&net, 0, sizeof net);
+  net.S = S;
+  net.R = R;
+  for (int r = 0; r < R; ++r) {
+    int first = -1, second = -1, order = 0;
+    for (int i = 0; i < S; ++i) {
+      const int m = reac[r * S + i];
+      order += m;
+      if (m == 2) first = second = i;
+      if (m == 1) {
+        if (first < 0) first = i;
+        else second = i;
+      }
+      net.nu[r][i] = prod[r * S + i] - m;
+    }
+    net.order[r] = order;
+    net.a[r] = first;
+    net.b[r] = order == 2 ? second : -1;
+  }
+  net.hist_x = frank ? perm[0] : 0;
+  net.hist_y = frank ? perm[1] : (S > 1 ? 1 : -1);
+  return net;
+}
+
+int check_rates(const double* k, std::string* why, int R = 3) {
   double kmax = 0.0;
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < R; ++r) {
     if (!(k[r] >= 0.0) || std::isinf(k[r])) return (*why = "rates must be finite and >= 0", SSA_EINVAL);
     kmax = std::max(kmax, k[r]);
   }
@@ -280,16 +365,16 @@ int check_rates(const double* k, std::string* why) {
 
 int check_options(const ssa_options& o, std::string* why) {
   if (o.precision < 0 || o.precision > 4) return (*why = "unknown precision mode", SSA_EINVAL);
-  if (o.engine < 0 || o.engine > 1) return (*why = "unknown engine", SSA_EINVAL);
+  if (o.engine < 0 || o.engine > 2) return (*why = "unknown engine", SSA_EINVAL);
+  if (o.engine == SSA_ENGINE_GENERAL && o.layout == SSA_LAYOUT_WARPS)
+    return (*why = "the general engine runs one thread per group", SSA_EUNSUPPORTED);
   if (o.layout < SSA_LAYOUT_AUTO || o.layout > SSA_LAYOUT_WARPS) return (*why = "unknown layout", SSA_EINVAL);
   if (o.shared_n != 0 && o.shared_n != 1) return (*why = "shared_n must be 0 or 1", SSA_EINVAL);
-  if (o.shared_n && o.engine != SSA_ENGINE_BITSLICED)
-    return (*why = "shared_n is a mode of the bit-sliced engine", SSA_EUNSUPPORTED);
-  if (o.shared_n && o.layout == SSA_LAYOUT_THREAD)
-    return (*why = "shared_n runs on the three-warp layout", SSA_EUNSUPPORTED);
+  if (o.shared_n && o.engine == SSA_ENGINE_THREAD_PER_RUN)
+    return (*why = "shared_n is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
   if (o.pad_pow2 != 0 && o.pad_pow2 != 1) return (*why = "pad_pow2 must be 0 or 1", SSA_EINVAL);
-  if (o.pad_pow2 && o.engine != SSA_ENGINE_BITSLICED)
-    return (*why = "pad_pow2 is a mode of the bit-sliced engine", SSA_EUNSUPPORTED);
+  if (o.pad_pow2 && o.engine == SSA_ENGINE_THREAD_PER_RUN)
+    return (*why = "pad_pow2 is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
   if (o.block_size < 0 || o.block_size > 256 || (o.block_size % 32) != 0)
     return (*why = "block_size must be 0 or a multiple of 32 up to 256", SSA_EINVAL);
@@ -363,6 +448,7 @@ int allocate_common(ssa_ctx* c, const std::vector<int>& init_rows) {
 
 int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R, const ssa_options* opt,
                   ssa_ctx** out, ssa_ctx** made, int perm[3]) {
+  for (int i = 0; i < 3; ++i) perm[i] = i;
   if (!out) return fail(nullptr, SSA_EINVAL, "out is NULL");
   *out = nullptr;
   ssa_options o;
@@ -371,11 +457,23 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
   std::string why;
   int st = check_options(o, &why);
   if (st != SSA_OK) return fail(nullptr, st, why);
-  st = check_network(reac, prod, S, R, perm, &why);
+  bool frank = false;
+  st = check_network(reac, prod, S, R, perm, &frank, &why);
   if (st != SSA_OK) return fail(nullptr, st, why);
+  const bool general = !frank || o.engine == SSA_ENGINE_GENERAL;
+  if (general && o.engine == SSA_ENGINE_THREAD_PER_RUN)
+    return fail(nullptr, SSA_EUNSUPPORTED, "the thread-per-run engine runs Frank's model (A+X->2X, A+Y->2Y, "
+                                           "X+Y->2A in this order) only");
+  if (frank && !general && o.shared_n && o.layout == SSA_LAYOUT_THREAD)
+    return fail(nullptr, SSA_EUNSUPPORTED, "shared_n runs Frank's model on the three-warp layout");
+  if (general && o.layout == SSA_LAYOUT_WARPS)
+    return fail(nullptr, SSA_EUNSUPPORTED, "a general network runs one thread per group");
   ssa_ctx* c = new ssa_ctx();
   c->opt = o;
   c->S = S;
+  c->R = R;
+  c->general = general;
+  if (general) c->net = make_network(reac, prod, S, R, frank, perm);
   for (int i = 0; i < 3; ++i) c->perm[i] = perm[i];
   {
     std::lock_guard<std::mutex> lock(g_alloc_mu);
@@ -430,10 +528,60 @@ bool use_warps_layout(const ssa_options& o, long long groups, int sm_count) {
 // The layout of one launch of a context: a fixed option wins, then the tuner's choice, then the
 // rule above.
 bool ctx_warps(const ssa_ctx* c, long long groups) {
-  if (c->opt.shared_n) return true;  // the shared draw is built into the three-warp layout only
+  if (c->general) return false;      // the general kernel has one layout
+  if (c->opt.shared_n) return true;  // Frank's kernels: the shared draw is built into three warps only
   if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_THREAD) return false;
   if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_WARPS) return true;
   return use_warps_layout(c->opt, groups, c->sm_count);
+}
+
+// Shared memory of the general kernel per block, histogram excluded: the count planes of every
+// thread ([species][plane][thread] words; enough planes for the products at K).
+int general_smem(const ssa_ctx* c, int K, int block) {
+  const int BM = bit_length(frank_nmax(K));
+  return c->net.S * std::max(BM, c->net.B) * block * (int)sizeof(uint32_t);
+}
+
+// Launches of the general-network kernel: one for a single ensemble, one per K bucket (on the
+// caller's stream, one after another) for a batch.
+int launch_general(ssa_ctx* c, FrankLaunch fl, int block, int clock_variant) {
+  cudaError_t e;
+  fl.net = c->net;
+  const int hist_smem = c->batch ? 0 : c->n_snap * kHistBins * (int)sizeof(unsigned int);
+  c->layout_used = SSA_LAYOUT_THREAD;
+  struct Range {
+    int K;
+    long long begin, end;
+  };
+  std::vector<Range> ranges;
+  if (!c->batch) {
+    ranges.push_back({std::max(1, c->ens[0].K), 0, (c->ens[0].n_runs + 31) / 32});
+    fl.ens = c->ens[0];
+    fl.ens_table = nullptr;
+  } else {
+    for (size_t r = 0; r < c->ranges.size(); ++r)
+      ranges.push_back({std::max(1, c->ranges[r].first), c->ranges[r].second.first, c->ranges[r].second.second});
+    fl.ens_table = c->d_ens;
+    fl.item_ens = c->d_item_ens;
+    fl.item_group = c->d_item_group;
+  }
+  for (size_t r = 0; r < ranges.size(); ++r) {
+    const int K = ranges[r].K;
+    const int smem = hist_smem + general_smem(c, K, block);
+    int occ = 0;
+    if (general_max_active_blocks(K, clock_variant | (c->batch ? 1 : 0), block, smem, &occ) != 0 || occ < 1)
+      return fail(c, SSA_ECUDA, "occupancy query failed for the general bit-sliced kernel (shared memory " +
+                                    std::to_string(smem) + " bytes per block)");
+    const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+    const long long groups = ranges[r].end - ranges[r].begin;
+    const int grid = (int)std::max(1ll, std::min((groups + block - 1) / block, (long long)c->sm_count * bpsm));
+    fl.item_begin = ranges[r].begin;
+    fl.item_end = ranges[r].end;
+    fl.queue = c->d_counters + kCounters + (c->batch ? 1 + r : 0);
+    if ((e = (cudaError_t)general_launcher(K)(fl, grid, block, smem, (void*)c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "general bit-sliced kernel launch");
+  }
+  return SSA_OK;
 }
 
 int launch_runs(ssa_ctx* c) {
@@ -497,6 +645,7 @@ int launch_runs(ssa_ctx* c) {
   }
 
   const int clock_variant = c->opt.precision == SSA_P64 ? 2 : 0;
+  if (c->general) return launch_general(c, fl, block, clock_variant);
   if (!c->batch) {
     const Ensemble& en = c->ens[0];
     const long long groups = (en.n_runs + 31) / 32;
@@ -639,11 +788,55 @@ int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_spec
     return fail(nullptr, code, msg);
   };
   if (!rates) return bail(SSA_EINVAL, "rates is NULL");
-  if ((st = check_rates(rates, &why)) != SSA_OK) return bail(st, why);
+  if ((st = check_rates(rates, &why, c->R)) != SSA_OK) return bail(st, why);
   if (!N0) return bail(SSA_EINVAL, "N0 is NULL");
   if (n_runs < 0) return bail(SSA_EINVAL, "n_runs must be >= 0");
   if (n0_per_run != 0 && n0_per_run != 1) return bail(SSA_EINVAL, "n0_per_run must be 0 or 1");
   if (c->opt.first_run + n_runs > (1ll << 37)) return bail(SSA_EINVAL, "run index beyond 2^37");
+  if (c->general) {
+    // counts in the caller's species order, one total for every run
+    const int S = c->S;
+    long long n_tot = -1;
+    std::vector<int> rows;
+    const long long nrows = n0_per_run ? n_runs : 1;
+    if (n0_per_run) rows.resize((size_t)n_runs * S);
+    int shared[kMaxSpecies] = {0};
+    for (long long j = 0; j < nrows; ++j) {
+      long long tot = 0;
+      for (int i = 0; i < S; ++i) {
+        const long long v = N0[j * S + i];
+        if (v < 0) return bail(SSA_EINVAL, "initial counts must be >= 0");
+        if (v > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
+        tot += v;
+        if (n0_per_run) rows[(size_t)j * S + i] = (int)v;
+        else shared[i] = (int)v;
+      }
+      if (n_tot < 0) n_tot = tot;
+      if (tot != n_tot) return bail(SSA_EINVAL, "every run must have the same total count");
+    }
+    if (nrows == 0) n_tot = 1;
+    if (n_tot < 1) return bail(SSA_EINVAL, "the total count must be >= 1");
+    if (n_tot > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
+    c->rates.assign(rates, rates + c->R);
+    c->n_ens = 1;
+    c->n_runs_total = n_runs;
+    unsigned long long lam = 0;
+    c->ens.push_back(make_general_ensemble(c->net, n_tot, shared, rates, c->opt.thin_bits, seed, n_runs, 0,
+                                           c->opt.first_run / 32, c->opt.pad_pow2, &lam));
+    if (lam >= (1ull << 31))
+      return bail(SSA_EUNSUPPORTED, "the uniformisation bound m_pair C(N,2) + u_max N must stay below 2^31");
+    c->ens.back().shared_n = c->opt.shared_n;
+    c->net.B = bits_of((unsigned long long)n_tot);
+    DeviceGuard guard(c->opt.device);
+    if ((st = setup_device(c)) != SSA_OK) return bail(st, c->err);
+    if ((st = allocate_common(c, rows)) != SSA_OK) {
+      std::string msg = c->err;
+      dev_free_all(c);
+      return bail(st, msg);
+    }
+    *out = c;
+    return SSA_OK;
+  }
   // total count, identical for every run (Sec. 4)
   long long n_tot = -1;
   std::vector<int> rows;
@@ -701,14 +894,40 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
   if (n_ens < 1) return bail(SSA_EINVAL, "n_ens must be >= 1");
   if (!N0_ens || !rates_ens || !runs_ens || !seed_ens) return bail(SSA_EINVAL, "null batch array");
   if (c->opt.first_run != 0) return bail(SSA_EINVAL, "first_run must be 0 for a batch");
-  if (c->opt.engine != SSA_ENGINE_BITSLICED) return bail(SSA_EUNSUPPORTED, "batches run on the bit-sliced engine");
+  if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN) return bail(SSA_EUNSUPPORTED, "batches run on the bit-sliced engines");
   c->batch = true;
   c->n_ens = n_ens;
   long long offset = 0;
   std::vector<std::pair<int, int>> order;  // (K, e)
   for (int e = 0; e < n_ens; ++e) {
-    if ((st = check_rates(rates_ens + 3 * e, &why)) != SSA_OK) return bail(st, why);
+    if ((st = check_rates(rates_ens + (size_t)c->R * e, &why, c->R)) != SSA_OK) return bail(st, why);
     if (runs_ens[e] < 0) return bail(SSA_EINVAL, "runs_ens must be >= 0");
+    if (c->general) {
+      const int S = c->S;
+      int init[kMaxSpecies] = {0};
+      long long tot = 0;
+      for (int i = 0; i < S; ++i) {
+        const long long v = N0_ens[(size_t)e * S + i];
+        if (v < 0) return bail(SSA_EINVAL, "initial counts must be >= 0");
+        if (v > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
+        init[i] = (int)v;
+        tot += v;
+      }
+      if (tot < 1) return bail(SSA_EINVAL, "the total count must be >= 1");
+      if (tot > 65536) return bail(SSA_EUNSUPPORTED, "N_tot above 65536");
+      const double* k = rates_ens + (size_t)c->R * e;
+      unsigned long long lam = 0;
+      c->ens.push_back(make_general_ensemble(c->net, tot, init, k, c->opt.thin_bits, seed_ens[e], runs_ens[e],
+                                             offset, 0, c->opt.pad_pow2, &lam));
+      if (lam >= (1ull << 31))
+        return bail(SSA_EUNSUPPORTED, "the uniformisation bound m_pair C(N,2) + u_max N must stay below 2^31");
+      c->ens.back().shared_n = c->opt.shared_n;
+      c->rates.insert(c->rates.end(), k, k + c->R);
+      c->net.B = std::max(c->net.B, bits_of((unsigned long long)tot));
+      offset += runs_ens[e];
+      order.push_back({std::max(1, c->ens.back().K), e});
+      continue;
+    }
     int canon[3];
     long long tot = 0;
     for (int ci = 0; ci < 3; ++ci) {
@@ -838,7 +1057,8 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
              int32_t* choice) {
   if (!c) return fail(nullptr, SSA_EINVAL, "ctx is NULL");
   if (probe_steps < 0) return fail(c, SSA_EINVAL, "probe_steps must be >= 0");
-  if (c->opt.engine != SSA_ENGINE_BITSLICED) return fail(c, SSA_EUNSUPPORTED, "the tuner chooses bit-sliced layouts");
+  if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN)
+    return fail(c, SSA_EUNSUPPORTED, "the tuner chooses bit-sliced layouts");
   struct Candidate {
     int layout, block;
   };
@@ -859,6 +1079,7 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
   Candidate win = cands[0];
   c->opt.step_budget = probe_steps;
   for (const Candidate& cand : cands) {
+    if (c->general && cand.layout == SSA_LAYOUT_WARPS) continue;  // one layout for general networks
     c->tuned_layout = cand.layout;
     c->tuned_block = cand.block;
     float ms = -1.0f;

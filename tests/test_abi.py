@@ -87,9 +87,16 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
     (dict(reac=F_R, prod=F_P, pad_pow2=2), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, pad_pow2=-1), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, pad_pow2=1, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
-    (dict(reac=[[1, 0, 1], [0, 1, 1]], prod=[[2, 0, 0], [0, 2, 0]]), pkg.SSA_EUNSUPPORTED),  # not Frank
-    (dict(reac=[[1, 1, 0], [0, 1, 1], [1, 0, 1]], prod=[[0, 0, 2], [0, 2, 0], [2, 0, 0]]),
-     pkg.SSA_EUNSUPPORTED),                                                           # Frank, wrong order
+    (dict(reac=[[1] + [0] * 8], prod=[[0, 1] + [0] * 7]), pkg.SSA_EUNSUPPORTED),    # 9 species
+    (dict(reac=[[1, 0]] * 9, prod=[[0, 1]] * 9, rates=[1.0] * 9, N0=(3, 3)), pkg.SSA_EUNSUPPORTED),  # 9 reactions
+    (dict(reac=[[1, 1], [1, 1]], prod=[[2, 0], [0, 2]], N0=(32768, 32768)), pkg.SSA_EUNSUPPORTED),  # bound >= 2^31
+    (dict(reac=[[1, 1], [1, 1]], prod=[[2, 0], [0, 2]], N0=(3, 3), rates=(1.0, -1.0)), pkg.SSA_EINVAL),
+    (dict(reac=[[1, 1], [1, 1]], prod=[[2, 0], [0, 2]], N0=(3, 3), engine=pkg.SSA_ENGINE_THREAD_PER_RUN),
+     pkg.SSA_EUNSUPPORTED),                                                           # baseline: Frank only
+    (dict(reac=[[1, 1], [1, 1]], prod=[[2, 0], [0, 2]], N0=(3, 3), layout=pkg.SSA_LAYOUT_WARPS),
+     pkg.SSA_EUNSUPPORTED),                                                           # general: one layout
+    (dict(reac=F_R, prod=F_P, engine=pkg.SSA_ENGINE_GENERAL, layout=pkg.SSA_LAYOUT_WARPS), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, engine=3), pkg.SSA_EINVAL),
 ])
 def test_validation_before_any_cuda_call(lib, kw, status):
     with pytest.raises(pkg.SSAError) as ei:
@@ -113,6 +120,23 @@ def test_null_and_order_errors(lib):
     ctx = C.c_void_p()
     assert L.ssa_create(None, None, 3, 3, None, None, 0, 1, 0, None, C.byref(ctx)) == pkg.SSA_EINVAL
     assert not ctx.value
+
+
+@pytest.mark.parametrize("reac,prod,N0", [
+    ([[1, 0, 1], [0, 1, 1]], [[2, 0, 0], [0, 2, 0]], (3, 3, 3)),                          # not Frank
+    ([[1, 1, 0], [0, 1, 1], [1, 0, 1]], [[0, 0, 2], [0, 2, 0], [2, 0, 0]], (3, 3, 3)),     # Frank, other order
+    ([[1, 1, 0], [0, 1, 0]], [[0, 2, 0], [0, 0, 1]], (9, 1, 0)),                          # S + I -> 2I, I -> R
+    ([[2]], [[2]], (5,)),                                                                 # one species
+])
+def test_general_networks_pass_validation(lib, reac, prod, N0):
+    """Networks that are not Frank's model go to the general kernel: validation accepts them
+    and, without a GPU, the call stops at the device."""
+    try:
+        ctx = _create(reac, prod, rates=[1.0] * len(reac), N0=N0)
+    except pkg.SSAError as e:
+        assert e.status == pkg.SSA_ECUDA  # no device here
+    else:
+        pkg.ssa_destroy(ctx)
 
 
 def test_frank_relabelled_passes_validation(lib):
