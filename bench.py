@@ -55,6 +55,13 @@ MAX_SM_MHZ = 2070.0
 TRAFFIC_BYTES_PER_LAUNCH = 4 * 123_136
 
 
+def general_ops_per_group_step(K: int, b: int) -> int:
+    """Word operations of one group step of Frank's model on the general kernel: per reaction a
+    b x b schoolbook product (3 b^2: AND, sum, carry), the running-sum add and the comparison
+    (3K); per species the masked add of the change (2b); the Philox calls (20 LOP3 each)."""
+    return 3 * (3 * b * b + 3 * K) + 3 * 2 * b + 20 * ((K + 2 + 3) // 4)
+
+
 def algorithmic_ops_per_group_step(K: int, b: int, padded: bool = False) -> int:
     """Word operations one group step must do (27K + 6b logic plus 20 LOP3 per Philox call
     for the ceil((K+2)/4) calls of n and tau); a bound padded to 2^K has no rejection test
@@ -168,6 +175,7 @@ WORKLOAD = "c2"
 BATCH = None
 PRECISION = 0
 PAD = 1  # 1: uniformisation bound padded to 2^K (no rejected draws of n); --pad 0 for N(N-1)/2
+ENGINE = 0  # 0: Frank's kernels; 2: the general-network kernel
 PRECISION_NAMES = {0: "p64", 1: "p32kahan", 2: "p32d64acc", 3: "p64logsum", 4: "p32plain"}
 
 
@@ -206,7 +214,12 @@ def workload_config_single(world):
             "runs": RUNS_PER_GPU * world, "runs_per_gpu": RUNS_PER_GPU, "groups_per_gpu": RUNS_PER_GPU // 32,
             "seed": SEED, "t_end": T_END, "snapshots": SNAPS, "precision": PRECISION_NAMES[PRECISION],
             "global_batch": RUNS_PER_GPU * world, "parallelism": f"replicas x{world} (run shards)",
-            "bound": BOUND_NAMES[PAD], "l2": "L2 flushed between timed steps (256 MiB write)"}
+            "bound": BOUND_NAMES[PAD], "engine": ENGINE_NAMES[ENGINE],
+            "l2": "L2 flushed between timed steps (256 MiB write)"}
+
+
+ENGINE_NAMES = {0: "Frank kernels (cumulative propensities, App. A increments)",
+                2: "general kernel (propensities by bit-sliced products every step)"}
 
 
 def main():
@@ -229,6 +242,8 @@ def main():
     ap.add_argument("--pad", type=int, default=1, choices=[0, 1],
                     help="1: pad the uniformisation bound to 2^K with null events, so that no draw of n "
                          "is rejected (the same process, sampled through a different draw)")
+    ap.add_argument("--engine", type=int, default=0, choices=[0, 2],
+                    help="0: Frank's kernels; 2: the general-network kernel on the same workload")
     ap.add_argument("--runs", type=int, default=0,
                     help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
@@ -238,9 +253,10 @@ def main():
     args = ap.parse_args()
     rank, world, local = env_rank()
     set_workload(args.workload, args.runs)
-    global PRECISION, PAD
+    global PRECISION, PAD, ENGINE
     PRECISION = args.precision
     PAD = args.pad
+    ENGINE = args.engine
 
     if args.impl == "reference":
         if world > 1:
@@ -267,7 +283,7 @@ def main():
     first_run = sharding.weak_shard(RUNS_PER_GPU, rank)[0] if WORKLOAD != "c3" else 0
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                   block_size=args.block, first_run=first_run, layout=args.layout,
-                                  pad_pow2=PAD)
+                                  pad_pow2=PAD, engine=ENGINE)
     if WORKLOAD == "c3":
         opt.first_run = 0
         ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],
@@ -328,7 +344,8 @@ def main():
     # ---- roofline of the bit-sliced kernel (one launch per step; a batch runs one launch per
     # number of planes K, so its per-unit count is not a single figure and is not reported)
     K, b = bit_length(N_TOT * (N_TOT - 1) // 2), bit_length(N_TOT)
-    ops_unit = algorithmic_ops_per_group_step(K, b, bool(PAD))
+    ops_unit = (general_ops_per_group_step(K, b) if ENGINE == 2
+                else algorithmic_ops_per_group_step(K, b, bool(PAD)))
     gs_per_launch = group_steps / world / args.steps
     achieved = ops_unit * gs_per_launch / (statistics.mean(kernel_ms) / 1e3) / 1e9
     peak_ops_per_clk = float(os.environ.get("BITSSA_ALU_OPS_PER_CLK_PER_SM", "64"))
@@ -341,7 +358,8 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
                 "frac": achieved / peak,
                 "traffic": TRAFFIC_BYTES_PER_LAUNCH if (WORKLOAD == "c2" and RUNS_PER_GPU == 1 << 20
-                                                        and PRECISION == 0 and PAD == 1 and layout_used == 1)
+                                                        and PRECISION == 0 and PAD == 1 and ENGINE == 0
+                                                        and layout_used == 1)
                 else None,
                 "ops_per_group_step": ops_unit, "group_steps_per_launch": gs_per_launch,
                 "peak_basis": f"{SMS} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {MAX_SM_MHZ:g} MHz",
@@ -402,7 +420,7 @@ def main():
     if not args.no_baselines and WORKLOAD != "c3":
         od = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                      keep_snap_counts=1, first_run=first_run, layout=opt.layout,
-                                     block_size=opt.block_size, pad_pow2=PAD)
+                                     block_size=opt.block_size, pad_pow2=PAD, engine=ENGINE)
         cd = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
                             RUNS_PER_GPU, SEED, od)
         pkg.ssa_run(cd, T_END, SNAPS)

@@ -59,12 +59,16 @@ struct GeneralState {
   bool done;
 };
 
-// Shared-memory view of one thread's count planes: plane i of species s at x[(s PL + i) T].
+// Shared-memory view of one thread's count planes, plane i of species s at x[(s PL + i) T], and
+// of its scratch words (two per species: the lanes with a nonzero count, with at least two).
 struct CountPlanes {
-  uint32_t* base;  // this thread's word of plane 0 of species 0
-  int stride;      // threads per block
-  int PL;          // planes stored per species
+  uint32_t* base;     // this thread's word of plane 0 of species 0
+  uint32_t* scratch;  // this thread's word of scratch 0
+  int stride;         // threads per block
+  int PL;             // planes stored per species
   __device__ __forceinline__ uint32_t& at(int s, int i) const { return base[(s * PL + i) * stride]; }
+  __device__ __forceinline__ uint32_t& nonzero(int s) const { return scratch[s * stride]; }
+  __device__ __forceinline__ uint32_t& two(int s) const { return scratch[(kMaxSpecies + s) * stride]; }
 };
 
 template <int W>
@@ -73,49 +77,32 @@ __device__ __forceinline__ void load_planes(uint32_t (&x)[W], const CountPlanes&
   for (int i = 0; i < W; ++i) x[i] = c.at(s, i);
 }
 
-// Lanes with a nonzero count of species s, and with at least two.
-__device__ __forceinline__ void count_masks(const CountPlanes& c, int s, int B, uint32_t& nz, uint32_t& two) {
-  nz = c.at(s, 0);
-  two = 0u;
-  for (int i = 1; i < B; ++i) two |= c.at(s, i);
-  nz |= two;
-}
-
 // Count planes of an ensemble: the bit length of its N_tot.
 __device__ __forceinline__ int count_planes(const Ensemble& e) { return 32 - __clz(e.n_tot); }
 
 // Lanes where some reaction with k_r > 0 has h_r > 0: h = x_a x_b > 0 iff both are nonzero,
-// x_a (x_a - 1) / 2 > 0 iff x_a >= 2, x_a > 0 iff it is nonzero.
+// x_a (x_a - 1) / 2 > 0 iff x_a >= 2, x_a > 0 iff it is nonzero.  The planes at and above the
+// ensemble's B are zero, so the first BM planes are read unrolled and only counts wider than
+// that (first-order networks) take the loop.
+template <int K>
 __device__ __forceinline__ uint32_t general_live(const Network& net, const Ensemble& e, const CountPlanes& c) {
+  constexpr int BM = GeneralShape<K>::BM;
   const int B = count_planes(e);
-  uint32_t nz[kMaxSpecies], two[kMaxSpecies];
+  for (int s = 0; s < net.S; ++s) {
+    uint32_t x[BM];
+    load_planes(x, c, s);
+    uint32_t two = 0u;
 #pragma unroll
-  for (int s = 0; s < kMaxSpecies; ++s) {
-    nz[s] = two[s] = 0u;
-    if (s < net.S) count_masks(c, s, B, nz[s], two[s]);
+    for (int i = 1; i < BM; ++i) two |= x[i];
+    for (int i = BM; i < B; ++i) two |= c.at(s, i);
+    c.nonzero(s) = x[0] | two;
+    c.two(s) = two;
   }
   uint32_t m = 0u;
-#pragma unroll
-  for (int r = 0; r < kMaxReactions; ++r) {
-    if (r >= net.R || !((e.active >> r) & 1u)) continue;
-    uint32_t h = 0u;
-    // (the species indices are run-time values: pick the masks by an unrolled compare)
-#pragma unroll
-    for (int s = 0; s < kMaxSpecies; ++s) {
-      if (s >= net.S) continue;
-      if (net.order[r] == 1 && s == net.a[r]) h = nz[s];
-      if (net.order[r] == 2 && net.a[r] == net.b[r] && s == net.a[r]) h = two[s];
-    }
-    if (net.order[r] == 2 && net.a[r] != net.b[r]) {
-      uint32_t ha = 0u, hb = 0u;
-#pragma unroll
-      for (int s = 0; s < kMaxSpecies; ++s) {
-        if (s == net.a[r]) ha = nz[s];
-        if (s == net.b[r]) hb = nz[s];
-      }
-      h = ha & hb;
-    }
-    m |= h;
+  for (int r = 0; r < net.R; ++r) {
+    if (!((e.active >> r) & 1u)) continue;
+    const int a = net.a[r], b = net.b[r];
+    m |= net.order[r] == 1 ? c.nonzero(a) : (b == a ? c.two(a) : (c.nonzero(a) & c.nonzero(b)));
   }
   return m;
 }
@@ -219,7 +206,7 @@ __device__ __forceinline__ void general_init(const FrankLaunch& p, GeneralState<
       c.at(sp, i) = w;
     }
   }
-  s.live = general_live(net, e, c) & s.valid;
+  s.live = general_live<K>(net, e, c) & s.valid;
   uint32_t at0 = s.valid & ~s.live;  // runs that start absorbed are absorbed at t = 0
   while (at0) {
     const int l = __ffs(at0) - 1;
@@ -355,28 +342,37 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
   ++s.step;
   if (!fired) return;
   for (int sp = 0; sp < net.S; ++sp) {
-    uint32_t d0 = 0u, d1 = 0u, d2 = 0u;
+    if (!((net.changes >> sp) & 1u)) continue;
+    uint32_t d[3];
 #pragma unroll
-    for (int r = 0; r < kMaxReactions; ++r) {
-      if (r >= net.R) continue;
-      const int v = net.nu[r][sp];
-      if (v & 1) d0 |= xi[r];
-      if (v & 2) d1 |= xi[r];
-      if (v & 4) d2 |= xi[r];
+    for (int b = 0; b < 3; ++b) {
+      const unsigned int sel = net.nu_bits[sp][b];
+      d[b] = 0u;
+#pragma unroll
+      for (int r = 0; r < kMaxReactions; ++r)
+        if ((sel >> r) & 1u) d[b] |= xi[r];
     }
-    if (!(d0 | d1 | d2)) continue;
+    if (!(d[0] | d[1] | d[2])) continue;
+    constexpr int BM = Sh::BM;
+    uint32_t x[BM];
+    load_planes(x, c, sp);
     uint32_t carry = 0u;
-    for (int i = 0; i < B; ++i) {
-      const uint32_t d = i == 0 ? d0 : (i == 1 ? d1 : d2);
-      const uint32_t x = c.at(sp, i);
-      c.at(sp, i) = bs::xor3(x, d, carry);
-      carry = bs::maj(x, d, carry);
+#pragma unroll
+    for (int i = 0; i < BM; ++i) {
+      const uint32_t di = d[i < 2 ? i : 2];
+      c.at(sp, i) = bs::xor3(x[i], di, carry);
+      carry = bs::maj(x[i], di, carry);
+    }
+    for (int i = BM; i < B; ++i) {  // counts wider than the products read (first-order networks)
+      const uint32_t xi_ = c.at(sp, i);
+      c.at(sp, i) = bs::xor3(xi_, d[2], carry);
+      carry = bs::maj(xi_, d[2], carry);
     }
   }
   s.reactions += (unsigned)__popc(fired);
 
   // (6) absorption
-  const uint32_t now_live = general_live(net, e, c) & s.live;
+  const uint32_t now_live = general_live<K>(net, e, c) & s.live;
   uint32_t newly = s.live & ~now_live;
   if (newly) {
     const double tn = s.clk.time(e, precision);
@@ -444,8 +440,8 @@ __device__ __forceinline__ void general_finish(const FrankLaunch& p, GeneralStat
 __host__ __device__ constexpr int general_planes(int BM, int B) { return BM > B ? BM : B; }
 
 // The persistent kernel: the queue, warp-synchronous loop and histogram handling of the
-// Frank kernel.  Dynamic shared memory: the histogram (single ensemble), then the count
-// planes of every thread of the block.
+// Frank kernel.  Dynamic shared memory: the histogram (single ensemble), the count planes of
+// every thread of the block, then the scratch words of every thread.
 template <int K, bool BATCH, bool PROD>
 __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ FrankLaunch p) {
   extern __shared__ unsigned int s_mem[];
@@ -456,8 +452,9 @@ __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ Fr
     for (int i = threadIdx.x; i < hist_words; i += blockDim.x) s_mem[i] = 0u;
     __syncthreads();
   }
-  const CountPlanes c{s_mem + hist_words + threadIdx.x, (int)blockDim.x,
-                      general_planes(GeneralShape<K>::BM, p.net.B)};
+  const int planes = general_planes(GeneralShape<K>::BM, p.net.B);
+  const CountPlanes c{s_mem + hist_words + threadIdx.x,
+                      s_mem + hist_words + p.net.S * planes * blockDim.x + threadIdx.x, (int)blockDim.x, planes};
   unsigned int errors = 0u;
   GeneralState<PROD> s;
   s.done = true;

@@ -124,6 +124,8 @@ struct Network {
   int a[kMaxReactions];              // first reactant
   int b[kMaxReactions];              // second reactant (a for 2X); -1 for first order
   int nu[kMaxReactions][kMaxSpecies];  // products - reactants, in [-2, 2]
+  unsigned int nu_bits[kMaxSpecies][3];  // bit r of [s][p]: bit p of nu[r][s] in 3-bit two's complement
+  unsigned int changes;              // bit s: some reaction changes species s
   int hist_x, hist_y;                // species binned by the ee histogram (x: "L", y: "D")
 };
 

@@ -348,6 +348,13 @@ Network make_network(const int32_t* reac, const int32_t* prod, int S, int R, boo
     net.a[r] = first;
     net.b[r] = order == 2 ? second : -1;
   }
+  for (int r = 0; r < R; ++r)
+    for (int i = 0; i < S; ++i) {
+      const unsigned int v = (unsigned int)net.nu[r][i] & 7u;  // three-bit two's complement
+      for (int b = 0; b < 3; ++b)
+        if ((v >> b) & 1u) net.nu_bits[i][b] |= 1u << r;
+      if (v) net.changes |= 1u << i;
+    }
   net.hist_x = frank ? perm[0] : 0;
   net.hist_y = frank ? perm[1] : (S > 1 ? 1 : -1);
   return net;
@@ -536,10 +543,11 @@ bool ctx_warps(const ssa_ctx* c, long long groups) {
 }
 
 // Shared memory of the general kernel per block, histogram excluded: the count planes of every
-// thread ([species][plane][thread] words; enough planes for the products at K).
+// thread ([species][plane][thread] words; enough planes for the products at K), then two scratch
+// words per species and thread.
 int general_smem(const ssa_ctx* c, int K, int block) {
   const int BM = bit_length(frank_nmax(K));
-  return c->net.S * std::max(BM, c->net.B) * block * (int)sizeof(uint32_t);
+  return (c->net.S * std::max(BM, c->net.B) + 2 * kMaxSpecies) * block * (int)sizeof(uint32_t);
 }
 
 // Launches of the general-network kernel: one for a single ensemble, one per K bucket (on the
