@@ -128,7 +128,12 @@ typedef struct {
                                 total propensity samples the same process: the runs are exact either
                                 way, but not draw for draw the same.  Costs 2^K / lambda_int - 1 more
                                 (null) steps, saves every redraw.  Bit-sliced engines only. */
-  int32_t reserved[4];
+  int32_t recompute;         /* general kernel (networks other than Frank's, SSA_ENGINE_GENERAL):
+                                0 (default) keeps every propensity h_r and adds its change after
+                                each event, linear in the counts before it (App. A generalised to
+                                any mass-action network); 1 recomputes every h_r by bit-sliced
+                                products at every step (Sec. 4.1).  Same runs either way. */
+  int32_t reserved[3];
 } ssa_options;
 
 /* Fields for ssa_fetch.  n_runs = the context's total number of runs (for a batch,

@@ -53,7 +53,7 @@ class ssa_options(C.Structure):
         ("blocks_per_sm", C.c_int32), ("thin_bits", C.c_int32), ("keep_snap_counts", C.c_int32),
         ("step_budget", C.c_int64), ("first_run", C.c_int64), ("cuda_stream", C.c_void_p),
         ("device", C.c_int32), ("layout", C.c_int32), ("shared_n", C.c_int32), ("pad_pow2", C.c_int32),
-        ("reserved", C.c_int32 * 4),
+        ("recompute", C.c_int32), ("reserved", C.c_int32 * 3),
     ]
 
 

@@ -13,6 +13,14 @@
 // of up to 8 species and 8 reactions; the per-step values (n, the running sum S, one
 // product) stay in registers.
 //
+// Incremental mode (the default) keeps every h_r in shared memory as well and, after each
+// event, adds its change, which for mass action is linear in the counts before the event
+// (App. A generalised): with d_s in [-2, 2] the change of species s in a lane,
+//   d(x_a x_b)            = d_b x_a + d_a x_b + d_a d_b
+//   d(x_a (x_a - 1) / 2)  = d_a x_a + d_a (d_a - 1) / 2
+//   d(x_a)                = d_a
+// Each term is a masked, shifted, conditionally negated copy of a count: no product per step.
+//
 // One group step (Sec. 3, steps 1-7, the draw done by Sec. 4's steps a-d), in the order of
 // the Frank kernel and the oracle:
 //   1. Philox words of attempt 0: the K planes of n (rejection and partial redraw above
@@ -64,12 +72,20 @@ struct GeneralState {
 struct CountPlanes {
   uint32_t* base;     // this thread's word of plane 0 of species 0
   uint32_t* scratch;  // this thread's word of scratch 0
+  uint32_t* hp;       // incremental mode: this thread's word of plane 0 of h_0
   int stride;         // threads per block
   int PL;             // planes stored per species
+  int K;              // planes of each h_r
   __device__ __forceinline__ uint32_t& at(int s, int i) const { return base[(s * PL + i) * stride]; }
   __device__ __forceinline__ uint32_t& nonzero(int s) const { return scratch[s * stride]; }
   __device__ __forceinline__ uint32_t& two(int s) const { return scratch[(kMaxSpecies + s) * stride]; }
+  // the change of species s in this step, plane b of three (two's complement)
+  __device__ __forceinline__ uint32_t& change(int s, int b) const {
+    return scratch[(2 * kMaxSpecies + 3 * s + b) * stride];
+  }
+  __device__ __forceinline__ uint32_t& h(int r, int i) const { return hp[(r * K + i) * stride]; }
 };
+
 
 template <int W>
 __device__ __forceinline__ void load_planes(uint32_t (&x)[W], const CountPlanes& c, int s) {
@@ -141,6 +157,80 @@ __device__ __forceinline__ void general_propensity(uint32_t (&h)[K], const Netwo
   for (int i = 0; i < K; ++i) h[i] = p[i + 1];
 }
 
+// h (K planes) += d x for a lane-wise d in [-2, 2] (three two's-complement planes) and an
+// unsigned x (W planes): the lanes with |d| = 1 add x, with |d| = 2 add 2x, negated where d < 0
+// (complemented, plus one at the carry-in).
+template <int K, int W>
+__device__ __forceinline__ void add_scaled(uint32_t (&h)[K], const uint32_t (&x)[W], const uint32_t (&d)[3]) {
+  const uint32_t one = d[0], two = d[1] & ~d[0], neg = d[2];
+  uint32_t carry = neg;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const uint32_t xi = i < W ? x[i] : 0u, xm = (i >= 1 && i - 1 < W) ? x[i - 1] : 0u;
+    const uint32_t t = ((one & xi) | (two & xm)) ^ neg;
+    const uint32_t s = bs::xor3(h[i], t, carry);
+    carry = bs::maj(h[i], t, carry);
+    h[i] = s;
+  }
+}
+
+// h (K planes) += a small signed lane-wise constant given by its low planes c[0..2] and its
+// sign plane c[3] (two's complement, sign-extended).
+template <int K>
+__device__ __forceinline__ void add_small(uint32_t (&h)[K], const uint32_t (&c)[4]) {
+  uint32_t carry = 0u;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const uint32_t t = c[i < 3 ? i : 3];
+    const uint32_t s = bs::xor3(h[i], t, carry);
+    carry = bs::maj(h[i], t, carry);
+    h[i] = s;
+  }
+}
+
+// h_r += its change in this step (see the file header), from the counts before the event and
+// the change planes of every species.
+template <int K>
+__device__ __forceinline__ void general_increment(const Network& net, int r, const CountPlanes& c) {
+  using Sh = GeneralShape<K>;
+  constexpr int BM = Sh::BM;
+  const int a = net.a[r], b = net.b[r];
+  const bool moves = ((net.changes >> a) & 1u) || (b >= 0 && ((net.changes >> b) & 1u));
+  if (!moves) return;
+  const uint32_t da[3] = {c.change(a, 0), c.change(a, 1), c.change(a, 2)};
+  uint32_t h[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) h[i] = c.h(r, i);
+  if (net.order[r] == 1) {  // + d_a
+    const uint32_t cst[4] = {da[0], da[1], da[2], da[2]};
+    add_small(h, cst);
+  } else if (b == a) {  // + d_a x_a + d_a (d_a - 1) / 2, the last in {3, 1, 0, 0, 1} for d_a = -2..2
+    uint32_t xa[BM];
+    load_planes(xa, c, a);
+    add_scaled(h, xa, da);
+    const uint32_t m2 = da[1] & ~da[0];               // |d| = 2
+    const uint32_t cst[4] = {da[1] & (da[2] | ~da[0]),  // d = -2, -1 or 2
+                             m2 & da[2], 0u, 0u};       // d = -2
+    add_small(h, cst);
+  } else {  // + d_b x_a + d_a x_b + d_a d_b
+    const uint32_t db[3] = {c.change(b, 0), c.change(b, 1), c.change(b, 2)};
+    uint32_t xa[BM], xb[BM];
+    load_planes(xa, c, a);
+    load_planes(xb, c, b);
+    add_scaled(h, xa, db);
+    add_scaled(h, xb, da);
+    // d_a d_b: magnitude 1, 2 or 4, negative when exactly one of them is
+    const uint32_t a1 = da[0], a2 = da[1] & ~da[0], b1 = db[0], b2 = db[1] & ~db[0];
+    const uint32_t m1 = a1 & b1, m2 = (a1 & b2) | (a2 & b1), m4 = a2 & b2;
+    const uint32_t neg = (da[2] ^ db[2]) & (m1 | m2 | m4);
+    // two's complement of -m: m1 -> ...1111, m2 -> ...1110, m4 -> ...1100
+    const uint32_t cst[4] = {m1, (m2 & ~neg) | (neg & (m1 | m2)), (m4 & ~neg) | (neg & (m1 | m2 | m4)), neg};
+    add_small(h, cst);
+  }
+#pragma unroll
+  for (int i = 0; i < K; ++i) c.h(r, i) = h[i];
+}
+
 // Set up a group: counts into shared memory (padding lanes hold zero counts and never react),
 // the live lanes, the clock.
 template <int K, bool PROD>
@@ -204,6 +294,15 @@ __device__ __forceinline__ void general_init(const FrankLaunch& p, GeneralState<
         w = s.valid;
       }
       c.at(sp, i) = w;
+    }
+  }
+  if (net.incremental) {
+    const int B = count_planes(e);
+    for (int r = 0; r < net.R; ++r) {
+      uint32_t h[K];
+      general_propensity<K>(h, net, r, c, B);
+#pragma unroll
+      for (int i = 0; i < K; ++i) c.h(r, i) = h[i];
     }
   }
   s.live = general_live<K>(net, e, c) & s.valid;
@@ -285,7 +384,12 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
 #pragma unroll 1
     for (int r = 0; r < net.R; ++r) {
       uint32_t h[K];
-      general_propensity<K>(h, net, r, c, B);
+      if (net.incremental) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) h[i] = c.h(r, i);
+      } else {
+        general_propensity<K>(h, net, r, c, B);
+      }
       bs::add_signed(S, h, 0u);
       const uint32_t lt = bs::less_than(n, S);
       const uint32_t x = lt & ~lt_prev;
@@ -341,17 +445,27 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
   for (int r = 0; r < kMaxReactions; ++r) fired |= xi[r];
   ++s.step;
   if (!fired) return;
+  // the change of every species in every lane
   for (int sp = 0; sp < net.S; ++sp) {
-    if (!((net.changes >> sp) & 1u)) continue;
-    uint32_t d[3];
+    uint32_t d[3] = {0u, 0u, 0u};
+    if ((net.changes >> sp) & 1u) {
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const unsigned int sel = net.nu_bits[sp][b];
-      d[b] = 0u;
+      for (int b = 0; b < 3; ++b) {
+        const unsigned int sel = net.nu_bits[sp][b];
 #pragma unroll
-      for (int r = 0; r < kMaxReactions; ++r)
-        if ((sel >> r) & 1u) d[b] |= xi[r];
+        for (int r = 0; r < kMaxReactions; ++r)
+          if ((sel >> r) & 1u) d[b] |= xi[r];
+      }
     }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) c.change(sp, b) = d[b];
+  }
+  // incremental mode: h_r += its change, from the counts before the event
+  if (net.incremental)
+    for (int r = 0; r < net.R; ++r) general_increment<K>(net, r, c);
+  // the counts: x_s += d_s
+  for (int sp = 0; sp < net.S; ++sp) {
+    const uint32_t d[3] = {c.change(sp, 0), c.change(sp, 1), c.change(sp, 2)};
     if (!(d[0] | d[1] | d[2])) continue;
     constexpr int BM = Sh::BM;
     uint32_t x[BM];
@@ -364,9 +478,9 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
       carry = bs::maj(x[i], di, carry);
     }
     for (int i = BM; i < B; ++i) {  // counts wider than the products read (first-order networks)
-      const uint32_t xi_ = c.at(sp, i);
-      c.at(sp, i) = bs::xor3(xi_, d[2], carry);
-      carry = bs::maj(xi_, d[2], carry);
+      const uint32_t xv = c.at(sp, i);
+      c.at(sp, i) = bs::xor3(xv, d[2], carry);
+      carry = bs::maj(xv, d[2], carry);
     }
   }
   s.reactions += (unsigned)__popc(fired);
@@ -441,7 +555,8 @@ __host__ __device__ constexpr int general_planes(int BM, int B) { return BM > B 
 
 // The persistent kernel: the queue, warp-synchronous loop and histogram handling of the
 // Frank kernel.  Dynamic shared memory: the histogram (single ensemble), the count planes of
-// every thread of the block, then the scratch words of every thread.
+// every thread of the block, the scratch words of every thread, and in incremental mode the K
+// planes of every h_r of every thread.
 template <int K, bool BATCH, bool PROD>
 __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ FrankLaunch p) {
   extern __shared__ unsigned int s_mem[];
@@ -453,8 +568,10 @@ __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ Fr
     __syncthreads();
   }
   const int planes = general_planes(GeneralShape<K>::BM, p.net.B);
-  const CountPlanes c{s_mem + hist_words + threadIdx.x,
-                      s_mem + hist_words + p.net.S * planes * blockDim.x + threadIdx.x, (int)blockDim.x, planes};
+  uint32_t* const counts = s_mem + hist_words;
+  uint32_t* const scratch = counts + p.net.S * planes * blockDim.x;
+  uint32_t* const hplanes = scratch + kGeneralScratch * blockDim.x;
+  const CountPlanes c{counts + threadIdx.x, scratch + threadIdx.x, hplanes + threadIdx.x, (int)blockDim.x, planes, K};
   unsigned int errors = 0u;
   GeneralState<PROD> s;
   s.done = true;

@@ -35,6 +35,7 @@ constexpr int kTrioBlock = 96; // threads of a block of the three-warp layout (3
 constexpr int kMaxSpecies = 8;   // general networks: species
 constexpr int kMaxReactions = 8; // general networks: reactions
 constexpr int kMaxCountPlanes = 17;  // counts up to N_tot = 65536
+constexpr int kGeneralScratch = 5 * kMaxSpecies;  // general kernel: scratch words per thread
 
 // Clock precision modes (same values as SSA_P64 ... in bitssa.h).
 enum Precision { kP64 = 0, kP32Kahan = 1, kP32D64Acc = 2, kP64LogSum = 3, kP32Plain = 4 };
@@ -127,6 +128,7 @@ struct Network {
   unsigned int nu_bits[kMaxSpecies][3];  // bit r of [s][p]: bit p of nu[r][s] in 3-bit two's complement
   unsigned int changes;              // bit s: some reaction changes species s
   int hist_x, hist_y;                // species binned by the ee histogram (x: "L", y: "D")
+  int incremental;                   // 1: keep h_r and add its change every step; 0: products every step
 };
 
 // Per-ensemble constants of a general network from their definitions: lambda_int =

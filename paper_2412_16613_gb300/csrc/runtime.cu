@@ -380,6 +380,7 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.shared_n && o.engine == SSA_ENGINE_THREAD_PER_RUN)
     return (*why = "shared_n is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
   if (o.pad_pow2 != 0 && o.pad_pow2 != 1) return (*why = "pad_pow2 must be 0 or 1", SSA_EINVAL);
+  if (o.recompute != 0 && o.recompute != 1) return (*why = "recompute must be 0 or 1", SSA_EINVAL);
   if (o.pad_pow2 && o.engine == SSA_ENGINE_THREAD_PER_RUN)
     return (*why = "pad_pow2 is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
@@ -480,7 +481,10 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
   c->S = S;
   c->R = R;
   c->general = general;
-  if (general) c->net = make_network(reac, prod, S, R, frank, perm);
+  if (general) {
+    c->net = make_network(reac, prod, S, R, frank, perm);
+    c->net.incremental = o.recompute ? 0 : 1;
+  }
   for (int i = 0; i < 3; ++i) c->perm[i] = perm[i];
   {
     std::lock_guard<std::mutex> lock(g_alloc_mu);
@@ -543,11 +547,12 @@ bool ctx_warps(const ssa_ctx* c, long long groups) {
 }
 
 // Shared memory of the general kernel per block, histogram excluded: the count planes of every
-// thread ([species][plane][thread] words; enough planes for the products at K), then two scratch
-// words per species and thread.
+// thread ([species][plane][thread] words; enough planes for the products at K), the scratch
+// words, and in incremental mode the K planes of every propensity.
 int general_smem(const ssa_ctx* c, int K, int block) {
   const int BM = bit_length(frank_nmax(K));
-  return (c->net.S * std::max(BM, c->net.B) + 2 * kMaxSpecies) * block * (int)sizeof(uint32_t);
+  const int words = c->net.S * std::max(BM, c->net.B) + kGeneralScratch + (c->net.incremental ? c->net.R * K : 0);
+  return words * block * (int)sizeof(uint32_t);
 }
 
 // Launches of the general-network kernel: one for a single ensemble, one per K bucket (on the

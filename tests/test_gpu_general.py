@@ -65,14 +65,16 @@ def _check(g, r, S, snaps):
 
 
 @pytest.mark.parametrize("name", sorted(NETWORKS))
-@pytest.mark.parametrize("pad", [0, 1])
-def test_general_network_parity(name, pad):
-    """Every run, snapshot and histogram, 3 groups and a ragged tail, against the oracle."""
+@pytest.mark.parametrize("pad,recompute", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_general_network_parity(name, pad, recompute):
+    """Every run, snapshot and histogram, 3 groups and a ragged tail, against the oracle, with the
+    propensities kept and incremented (default) or recomputed by products every step."""
     reac, prod, rates, init, t_end = NETWORKS[name]
     S = len(init)
     snaps = [t_end / 10, t_end / 3, t_end / 2]
     n = 96 + 7
-    g = gpu_run(init, n, seed=41, t_end=t_end, snaps=snaps, rates=rates, reac=reac, prod=prod, pad_pow2=pad)
+    g = gpu_run(init, n, seed=41, t_end=t_end, snaps=snaps, rates=rates, reac=reac, prod=prod, pad_pow2=pad,
+                recompute=recompute)
     r = oracle.run(_oracle_net(reac, prod, rates), init, n, seed=41, t_end=t_end, snap_times=snaps,
                    threads=THREADS, pad_pow2=bool(pad))
     _check(g, r, S, snaps)
@@ -152,19 +154,22 @@ def test_general_batch_against_oracle():
         off += runs[e]
 
 
+@pytest.mark.parametrize("recompute", [0, 1])
 @pytest.mark.parametrize("init,n,rates,pad", [((16, 16, 32), 64, (1.0, 1.0, 1.0), 0),
                                               ((256, 256, 512), 4096 + 17, (1.0, 1.0, 1.0), 1),
                                               ((256, 256, 512), 2048, (0.7, 1.0, 1.6), 0),
                                               ((2500, 2500, 5000), 256, (1.0, 1.0, 1.0), 0)])
-def test_frank_on_general_kernel_equals_frank_kernel(init, n, rates, pad):
+def test_frank_on_general_kernel_equals_frank_kernel(init, n, rates, pad, recompute):
     """Frank's model through the general kernel gives Frank's kernel's runs bit for bit: the
-    same stream and rule, with the propensities recomputed instead of updated."""
+    same stream and rule, with the propensities incremented by the general rule or recomputed
+    by products instead of Frank's hand-derived increments."""
     N = sum(init)
     t_end = 50.0 if N <= 1024 else 3e-4
     snaps = log_snapshots(t_end, 6)
     a = gpu_run(init, n, seed=7, t_end=t_end, snaps=snaps, rates=rates, pad_pow2=pad,
                 layout=pkg.SSA_LAYOUT_THREAD)
-    b = gpu_run(init, n, seed=7, t_end=t_end, snaps=snaps, rates=rates, pad_pow2=pad, engine=GENERAL)
+    b = gpu_run(init, n, seed=7, t_end=t_end, snaps=snaps, rates=rates, pad_pow2=pad, engine=GENERAL,
+                recompute=recompute)
     for k in ("final_counts", "outcome", "ee_hist", "snap_counts", "ens_absorbed"):
         assert np.array_equal(a[k], b[k]), k
     assert np.array_equal(a["t_abs"], b["t_abs"])
