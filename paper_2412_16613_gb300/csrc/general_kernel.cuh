@@ -67,23 +67,26 @@ struct GeneralState {
   bool done;
 };
 
-// Shared-memory view of one thread's count planes, plane i of species s at x[(s PL + i) T], and
-// of its scratch words (two per species: the lanes with a nonzero count, with at least two).
+// Shared-memory view of one thread's words.  Each warp has its own region, laid out
+// [word][lane] with a stride of 32, so that a plane's offset is a compile-time immediate and
+// the 32 lanes of a warp touch 32 banks: plane i of species s at [(s PL + i) 32], the scratch
+// words (per species: the lanes with a nonzero count, with at least two, and the three planes
+// of its change in this step), and in incremental mode plane i of h_r.
 struct CountPlanes {
+  static constexpr int kStride = 32;
   uint32_t* base;     // this thread's word of plane 0 of species 0
   uint32_t* scratch;  // this thread's word of scratch 0
   uint32_t* hp;       // incremental mode: this thread's word of plane 0 of h_0
-  int stride;         // threads per block
   int PL;             // planes stored per species
   int K;              // planes of each h_r
-  __device__ __forceinline__ uint32_t& at(int s, int i) const { return base[(s * PL + i) * stride]; }
-  __device__ __forceinline__ uint32_t& nonzero(int s) const { return scratch[s * stride]; }
-  __device__ __forceinline__ uint32_t& two(int s) const { return scratch[(kMaxSpecies + s) * stride]; }
+  __device__ __forceinline__ uint32_t& at(int s, int i) const { return base[(s * PL + i) * kStride]; }
+  __device__ __forceinline__ uint32_t& nonzero(int s) const { return scratch[s * kStride]; }
+  __device__ __forceinline__ uint32_t& two(int s) const { return scratch[(kMaxSpecies + s) * kStride]; }
   // the change of species s in this step, plane b of three (two's complement)
   __device__ __forceinline__ uint32_t& change(int s, int b) const {
-    return scratch[(2 * kMaxSpecies + 3 * s + b) * stride];
+    return scratch[(2 * kMaxSpecies + 3 * s + b) * kStride];
   }
-  __device__ __forceinline__ uint32_t& h(int r, int i) const { return hp[(r * K + i) * stride]; }
+  __device__ __forceinline__ uint32_t& h(int r, int i) const { return hp[(r * K + i) * kStride]; }
 };
 
 
@@ -568,10 +571,11 @@ __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ Fr
     __syncthreads();
   }
   const int planes = general_planes(GeneralShape<K>::BM, p.net.B);
-  uint32_t* const counts = s_mem + hist_words;
-  uint32_t* const scratch = counts + p.net.S * planes * blockDim.x;
-  uint32_t* const hplanes = scratch + kGeneralScratch * blockDim.x;
-  const CountPlanes c{counts + threadIdx.x, scratch + threadIdx.x, hplanes + threadIdx.x, (int)blockDim.x, planes, K};
+  const int count_words = p.net.S * planes, h_words = p.net.incremental ? p.net.R * K : 0;
+  uint32_t* const warp_base = s_mem + hist_words + (threadIdx.x >> 5) * 32 * (count_words + kGeneralScratch + h_words) +
+                              (threadIdx.x & 31);
+  const CountPlanes c{warp_base, warp_base + 32 * count_words, warp_base + 32 * (count_words + kGeneralScratch),
+                      planes, K};
   unsigned int errors = 0u;
   GeneralState<PROD> s;
   s.done = true;
