@@ -41,8 +41,14 @@ int with_kernel(int variant, F f) {
 }
 }  // namespace
 
+// Occupancy at `smem` bytes of dynamic shared memory; lifts the kernel's dynamic shared-memory
+// limit first when the request exceeds the default 48 KB (the staging rows of a snapshot dump).
 int BITSSA_CAT(frank_occupancy_k, BITSSA_K)(int variant, int block, int smem, int* blocks) {
   return with_kernel(variant, [&](auto kern) {
+    if (smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return (int)e;
+    }
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, block, (size_t)smem);
   });
 }

@@ -323,24 +323,43 @@ __device__ __forceinline__ uint32_t live_lanes(const GroupState<K, PROD>& s, con
   return m;
 }
 
+// Dynamic shared memory of the one-thread kernel: the histogram of a single ensemble, then the
+// per-thread staging rows of the snapshot dump.
+extern __shared__ unsigned int frank_dyn_smem[];
+
 // The current state of every valid lane into snapshot `snap`: histogram and per-run counts.
-// Lane by lane with plain stores: staging four runs (12 ints) for 16-byte stores was tried and
-// cost the step loop registers it does not have, for a path taken ten times per group.
+// With the dump on, a full group's 32 rows of 3 counts (384 contiguous bytes of the output) are
+// staged in this thread's shared-memory rows and written with 24 16-byte stores; a partial group,
+// or an output not 16-byte aligned, is written count by count.
 template <int K, bool PROD>
 __device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K, PROD>& s, const Ensemble& e,
                                         int snap, unsigned int* s_hist) {
   using Sh = FrankShape<K>;
+  int* const rows = p.snap_counts ? p.snap_counts + ((long long)snap * p.n_runs_total + group_row0(s, e)) * 3 : nullptr;
+  const bool staged = rows && p.stage_offset >= 0 && s.nvalid == 32 && p.n_species == 3 &&
+                      (reinterpret_cast<uintptr_t>(rows) & 15u) == 0u;
+  unsigned int* const buf = frank_dyn_smem + p.stage_offset + threadIdx.x * kStageStride;
   for (int l = 0; l < s.nvalid; ++l) {
     int cl, cd, ca;
     lane_counts<Sh::B, Sh::WP>(s.L, s.U, e.n_tot, l, cl, cd, ca);
     if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(cl, cd)], 1u);
     else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + ee_bin(cl, cd)], 1ull);
-    if (p.snap_counts) {
-      int* o = p.snap_counts + ((long long)snap * p.n_runs_total + group_row0(s, e) + l) * p.n_species;
+    if (staged) {
+      buf[3 * l + p.perm[0]] = (unsigned int)cl;
+      buf[3 * l + p.perm[1]] = (unsigned int)cd;
+      buf[3 * l + p.perm[2]] = (unsigned int)ca;
+    } else if (rows) {
+      int* o = rows + l * p.n_species;
       o[p.perm[0]] = cl;
       o[p.perm[1]] = cd;
       o[p.perm[2]] = ca;
     }
+  }
+  if (staged) {
+    const uint4* src = reinterpret_cast<const uint4*>(buf);
+    uint4* dst = reinterpret_cast<uint4*>(rows);
+#pragma unroll 4
+    for (int k = 0; k < 24; ++k) dst[k] = src[k];
   }
 }
 
@@ -627,7 +646,7 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
 // kernel parameters (warp-uniform); batches from a table.
 template <int K, bool BATCH, bool PROD>
 __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ FrankLaunch p) {
-  extern __shared__ unsigned int s_hist_mem[];
+  unsigned int* const s_hist_mem = frank_dyn_smem;
   const bool smem_hist = !BATCH && p.n_snap > 0;
   unsigned int* s_hist = smem_hist ? s_hist_mem : nullptr;
   if (smem_hist) {

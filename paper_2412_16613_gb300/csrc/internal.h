@@ -164,8 +164,14 @@ struct FrankLaunch {
   unsigned long long* counters;   // [kCounters]
   unsigned int* status;           // error flags
   unsigned long long* queue;      // work-item counter of this launch
+  int stage_offset;               // one-thread Frank kernel with a snapshot dump: the word of dynamic
+                                  // shared memory where the per-thread staging rows start; -1: none
   Network net;                    // general kernel only
 };
+
+// Words of shared memory per thread for staging a group's snapshot rows (32 runs x 3 counts,
+// padded so that rows start 16-byte aligned and neighbouring threads fall in different banks).
+constexpr int kStageStride = 100;
 
 // One launch of the one-thread-per-run baseline.
 struct ThreadLaunch {

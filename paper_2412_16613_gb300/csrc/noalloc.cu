@@ -154,6 +154,7 @@ extern "C" int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int
     fl.counters = scratch->counters;
     fl.status = scratch->status;
     fl.queue = &scratch->queue;
+    fl.stage_offset = -1;
     const int K = std::max(1, en.K);
     const int block = 64, smem = n_snap * kHistBins * (int)sizeof(unsigned int);
     int dev = 0, sms = 0, occ = 0;

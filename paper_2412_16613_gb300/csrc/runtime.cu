@@ -615,6 +615,7 @@ int launch_runs(ssa_ctx* c) {
   fl.hist = c->d_hist;
   fl.ens_absorbed = c->d_ens_abs;
   fl.snap_counts = c->opt.keep_snap_counts ? c->d_snap : nullptr;
+  fl.stage_offset = -1;
   fl.n_runs_total = c->n_runs_total;
   fl.counters = c->d_counters;
   fl.status = c->d_status;
@@ -682,12 +683,18 @@ int launch_runs(ssa_ctx* c) {
         return cuda_fail(c, e, "three-warp bit-sliced kernel launch");
       return SSA_OK;
     }
-    if (frank_max_active_blocks(K, clock_variant, block, smem, &occ) != 0 || occ < 1)
+    // with the dump on, each thread stages a group's rows after the histogram (16-byte aligned)
+    int tsmem = smem;
+    if (fl.snap_counts) {
+      fl.stage_offset = ((smem / (int)sizeof(unsigned int)) + 3) & ~3;
+      tsmem = (fl.stage_offset + block * kStageStride) * (int)sizeof(unsigned int);
+    }
+    if (frank_max_active_blocks(K, clock_variant, block, tsmem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (groups + block - 1) / block;
     const int grid = (int)std::max(1ll, std::min(need, (long long)c->sm_count * bpsm));
-    if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, smem, (void*)c->stream)) != cudaSuccess)
+    if ((e = (cudaError_t)frank_launcher(K)(fl, grid, block, tsmem, (void*)c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "bit-sliced kernel launch");
     return SSA_OK;
   }
