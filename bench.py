@@ -55,11 +55,21 @@ MAX_SM_MHZ = 2070.0
 TRAFFIC_BYTES_PER_LAUNCH = 4 * 274_688
 
 
-def general_ops_per_group_step(K: int, b: int) -> int:
-    """Word operations of one group step of Frank's model on the general kernel: per reaction a
-    b x b schoolbook product (3 b^2: AND, sum, carry), the running-sum add and the comparison
-    (3K); per species the masked add of the change (2b); the Philox calls (20 LOP3 each)."""
-    return 3 * (3 * b * b + 3 * K) + 3 * 2 * b + 20 * ((K + 2 + 3) // 4)
+def layout_name(bits: int) -> str:
+    """The layouts counter 9 reports: one thread / three warps, and the general kernel's mode."""
+    names = [n for bit, n in ((1, "thread"), (2, "warps"), (4, "general incremental"), (8, "general products"))
+             if bits & bit]
+    return "+".join(names) or "none"
+
+
+def general_ops_per_group_step(K: int, b: int, products: bool) -> int:
+    """Word operations of one group step of Frank's model on the general kernel.  Per reaction:
+    the running-sum add and the comparison (3K), and either a b x b schoolbook product (3 b^2:
+    AND, sum, carry) or the change of h_r (two scaled counts, 4 ops a plane, and a small constant,
+    2 ops a plane: 10K).  Per species the change planes (3R) and the masked add (2b).  The Philox
+    calls (20 LOP3 each)."""
+    per_reaction = 3 * K + (3 * b * b if products else 10 * K)
+    return 3 * per_reaction + 3 * (2 * b + 3 * 3) + 20 * ((K + 2 + 3) // 4)
 
 
 def algorithmic_ops_per_group_step(K: int, b: int, padded: bool = False) -> int:
@@ -344,7 +354,7 @@ def main():
     # ---- roofline of the bit-sliced kernel (one launch per step; a batch runs one launch per
     # number of planes K, so its per-unit count is not a single figure and is not reported)
     K, b = bit_length(N_TOT * (N_TOT - 1) // 2), bit_length(N_TOT)
-    ops_unit = (general_ops_per_group_step(K, b) if ENGINE == 2
+    ops_unit = (general_ops_per_group_step(K, b, bool(layout_used & 8)) if ENGINE == 2
                 else algorithmic_ops_per_group_step(K, b, bool(PAD)))
     gs_per_launch = group_steps / world / args.steps
     achieved = ops_unit * gs_per_launch / (statistics.mean(kernel_ms) / 1e3) / 1e9
@@ -376,7 +386,7 @@ def main():
               "group_steps_per_step": group_steps / args.steps, "max_group_steps": max_group_steps,
               "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
               "hist_checksum": float(htot.sum().item()),
-              "layout": {0: "none", 1: "thread", 2: "warps", 3: "thread+warps"}[layout_used],
+              "layout": layout_name(layout_used),
               "tuned": None if tuned is None else {"layout": {0: "rule", 1: "thread", 2: "warps"}[tuned[0]],
                                                    "block": tuned[1]}}
 

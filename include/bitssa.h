@@ -129,10 +129,12 @@ typedef struct {
                                 way, but not draw for draw the same.  Costs 2^K / lambda_int - 1 more
                                 (null) steps, saves every redraw.  Bit-sliced engines only. */
   int32_t recompute;         /* general kernel (networks other than Frank's, SSA_ENGINE_GENERAL):
-                                0 (default) keeps every propensity h_r and adds its change after
-                                each event, linear in the counts before it (App. A generalised to
-                                any mass-action network); 1 recomputes every h_r by bit-sliced
-                                products at every step (Sec. 4.1).  Same runs either way. */
+                                2 keeps every propensity h_r and adds its change after each event,
+                                linear in the counts before it (App. A generalised to any
+                                mass-action network); 1 recomputes every h_r by bit-sliced products
+                                at every step (Sec. 4.1); 0 (default) incremental unless ssa_tune
+                                found products faster on the caller's workload.  Same runs in
+                                every mode. */
   int32_t reserved[3];
 } ssa_options;
 
@@ -157,7 +159,8 @@ enum {
                                    groups finished, error flags, steps of the longest group,
                                    the layouts that ran (bit 0 SSA_LAYOUT_THREAD, bit 1
                                    SSA_LAYOUT_WARPS: 1, 2, or 3 for a batch that used both;
-                                   0 no bit-sliced launch) */
+                                   0 no bit-sliced launch; on the general kernel also bit 2
+                                   with propensities incremented, bit 3 recomputed by products) */
   SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,
                                    and [3] the others: not absorbed, absorbed with several
                                    species left, or with one species of index 3 or above */
@@ -218,11 +221,13 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
 int ssa_run(ssa_ctx* ctx, double t_end, const double* snapshot_times, int32_t n_snap);
 
 /*
- * Autotuner: time the context's work under each launch configuration the library has (the
- * automatic layout rule, one thread per group of 32 runs with blocks of 32, 64 and 128
- * threads, three warps per 32 groups) and keep the fastest for later ssa_run calls whose
- * options leave layout = SSA_LAYOUT_AUTO and block_size = 0 (fixed options win).  Results do
- * not depend on the configuration: every one draws the same streams and gives the same runs.
+ * Autotuner: time the context's work under each launch configuration the library has and keep
+ * the fastest for later ssa_run calls whose options leave layout = SSA_LAYOUT_AUTO, block_size =
+ * 0 and recompute = 0 (fixed options win).  Frank's model: the automatic layout rule, one thread
+ * per group of 32 runs with blocks of 32, 64 and 128 threads, three warps per 32 groups.  A
+ * general network: blocks of 32, 64 and 128 threads, each with the propensities incremented and
+ * with them recomputed by products.  Results do not depend on the configuration: every one draws
+ * the same streams and gives the same runs.
  *   t_end, snapshot_times, n_snap: the workload to time, as for ssa_run.
  *   probe_steps: 0 times whole runs (exact, costs ten runs); > 0 stops every group after that
  *     many steps (a cheap probe of the early, crowded part of a run).

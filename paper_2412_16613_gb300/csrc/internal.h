@@ -51,8 +51,11 @@ enum Counter {
   kGroupsDone = 6,
   kErrorFlags = 7,
   kMaxGroupSteps = 8, // the longest group, in steps
-  kLayoutUsed = 9     // set by the host: bit 0 one thread per group, bit 1 three warps per 32 groups
+  kLayoutUsed = 9     // set by the host: bit 0 one thread per group, bit 1 three warps per 32 groups,
+                      // bit 2 the general kernel incrementing propensities, bit 3 it recomputing them
 };
+constexpr int kLayoutGeneralIncremental = 4;
+constexpr int kLayoutGeneralProducts = 8;
 
 // Error flags (OR-ed into the status word).
 enum ErrorFlag : uint32_t {

@@ -208,6 +208,7 @@ struct ssa_ctx {
   int layout_used = 0;  // SSA_LAYOUT_* bits of the last run, 0 if none
   int tuned_layout = -1;  // ssa_tune's choice for SSA_LAYOUT_AUTO: -1 none, else an SSA_LAYOUT_*
   int tuned_block = 0;    // ssa_tune's block size for the one-thread layout, 0 none
+  int tuned_products = -1;  // ssa_tune's mode for the general kernel: -1 none, 0 incremental, 1 products
   int n_queues = 0;
   bool ran = false;
   int n_snap = 0;
@@ -380,7 +381,7 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.shared_n && o.engine == SSA_ENGINE_THREAD_PER_RUN)
     return (*why = "shared_n is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
   if (o.pad_pow2 != 0 && o.pad_pow2 != 1) return (*why = "pad_pow2 must be 0 or 1", SSA_EINVAL);
-  if (o.recompute != 0 && o.recompute != 1) return (*why = "recompute must be 0 or 1", SSA_EINVAL);
+  if (o.recompute < 0 || o.recompute > 2) return (*why = "recompute must be 0, 1 or 2", SSA_EINVAL);
   if (o.pad_pow2 && o.engine == SSA_ENGINE_THREAD_PER_RUN)
     return (*why = "pad_pow2 is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
@@ -483,7 +484,7 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
   c->general = general;
   if (general) {
     c->net = make_network(reac, prod, S, R, frank, perm);
-    c->net.incremental = o.recompute ? 0 : 1;
+    c->net.incremental = o.recompute == 1 ? 0 : 1;
   }
   for (int i = 0; i < 3; ++i) c->perm[i] = perm[i];
   {
@@ -559,9 +560,11 @@ int general_smem(const ssa_ctx* c, int K, int block) {
 // caller's stream, one after another) for a batch.
 int launch_general(ssa_ctx* c, FrankLaunch fl, int block, int clock_variant) {
   cudaError_t e;
+  // the propensity mode: a fixed option wins, then the tuner's choice, then incremental
+  c->net.incremental = c->opt.recompute == 1 ? 0 : (c->opt.recompute == 2 ? 1 : (c->tuned_products == 1 ? 0 : 1));
   fl.net = c->net;
   const int hist_smem = c->batch ? 0 : c->n_snap * kHistBins * (int)sizeof(unsigned int);
-  c->layout_used = SSA_LAYOUT_THREAD;
+  c->layout_used = SSA_LAYOUT_THREAD | (c->net.incremental ? kLayoutGeneralIncremental : kLayoutGeneralProducts);
   struct Range {
     int K;
     long long begin, end;
@@ -1080,14 +1083,24 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
   if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN)
     return fail(c, SSA_EUNSUPPORTED, "the tuner chooses bit-sliced layouts");
   struct Candidate {
-    int layout, block;
+    int layout, block, products;
   };
-  // the rule (per K bucket in a batch), one thread per group at three block sizes, three warps
-  const Candidate cands[] = {{SSA_LAYOUT_AUTO, 64}, {SSA_LAYOUT_THREAD, 32}, {SSA_LAYOUT_THREAD, 64},
-                             {SSA_LAYOUT_THREAD, 128}, {SSA_LAYOUT_WARPS, 64}};
+  // Frank's model: the rule (per K bucket in a batch), one thread per group at three block
+  // sizes, three warps.  A general network: one thread per group at three block sizes, with the
+  // propensities incremented or recomputed by products (unless the options fix the mode).
+  const Candidate frank_cands[] = {{SSA_LAYOUT_AUTO, 64, 0}, {SSA_LAYOUT_THREAD, 32, 0}, {SSA_LAYOUT_THREAD, 64, 0},
+                                   {SSA_LAYOUT_THREAD, 128, 0}, {SSA_LAYOUT_WARPS, 64, 0}};
+  const Candidate general_cands[] = {{SSA_LAYOUT_THREAD, 32, 0}, {SSA_LAYOUT_THREAD, 64, 0},
+                                     {SSA_LAYOUT_THREAD, 128, 0}, {SSA_LAYOUT_THREAD, 32, 1},
+                                     {SSA_LAYOUT_THREAD, 64, 1}, {SSA_LAYOUT_THREAD, 128, 1}};
+  std::vector<Candidate> cands;
+  if (!c->general) cands.assign(frank_cands, frank_cands + 5);
+  else
+    for (const Candidate& g : general_cands)
+      if (c->opt.recompute == 0 || g.products == (c->opt.recompute == 1 ? 1 : 0)) cands.push_back(g);
   DeviceGuard guard(c->device);
   const long long budget = c->opt.step_budget;
-  const int old_layout = c->tuned_layout, old_block = c->tuned_block;
+  const int old_layout = c->tuned_layout, old_block = c->tuned_block, old_products = c->tuned_products;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaError_t e;
   if ((e = cudaEventCreate(&ev[0])) != cudaSuccess || (e = cudaEventCreate(&ev[1])) != cudaSuccess) {
@@ -1099,9 +1112,9 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
   Candidate win = cands[0];
   c->opt.step_budget = probe_steps;
   for (const Candidate& cand : cands) {
-    if (c->general && cand.layout == SSA_LAYOUT_WARPS) continue;  // one layout for general networks
     c->tuned_layout = cand.layout;
     c->tuned_block = cand.block;
+    c->tuned_products = cand.products;
     float ms = -1.0f;
     for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel and records graphs
       cudaEventRecord(ev[0], c->stream);
@@ -1129,10 +1142,12 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
   if (st != SSA_OK) {
     c->tuned_layout = old_layout;
     c->tuned_block = old_block;
+    c->tuned_products = old_products;
     return st;
   }
   c->tuned_layout = win.layout;
   c->tuned_block = win.block;
+  c->tuned_products = c->general ? win.products : -1;
   if (choice) {
     choice[0] = win.layout;
     choice[1] = win.block;

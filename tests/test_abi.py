@@ -97,7 +97,7 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
      pkg.SSA_EUNSUPPORTED),                                                           # general: one layout
     (dict(reac=F_R, prod=F_P, engine=pkg.SSA_ENGINE_GENERAL, layout=pkg.SSA_LAYOUT_WARPS), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, engine=3), pkg.SSA_EINVAL),
-    (dict(reac=F_R, prod=F_P, recompute=2), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, recompute=3), pkg.SSA_EINVAL),
 ])
 def test_validation_before_any_cuda_call(lib, kw, status):
     with pytest.raises(pkg.SSAError) as ei:

@@ -65,7 +65,7 @@ def _check(g, r, S, snaps):
 
 
 @pytest.mark.parametrize("name", sorted(NETWORKS))
-@pytest.mark.parametrize("pad,recompute", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("pad,recompute", [(0, 0), (1, 0), (0, 1), (1, 1), (1, 2)])
 def test_general_network_parity(name, pad, recompute):
     """Every run, snapshot and histogram, 3 groups and a ragged tail, against the oracle, with the
     propensities kept and incremented (default) or recomputed by products every step."""
@@ -78,7 +78,7 @@ def test_general_network_parity(name, pad, recompute):
     r = oracle.run(_oracle_net(reac, prod, rates), init, n, seed=41, t_end=t_end, snap_times=snaps,
                    threads=THREADS, pad_pow2=bool(pad))
     _check(g, r, S, snaps)
-    assert g["counters"]["layout"] == pkg.SSA_LAYOUT_THREAD
+    assert g["counters"]["layout"] == pkg.SSA_LAYOUT_THREAD | (8 if recompute == 1 else 4)
     if pad:
         assert g["counters"]["redraw_rounds"] == 0
 
@@ -196,3 +196,24 @@ def test_general_step_budget_and_t_end_zero():
     assert g["counters"]["max_group_steps"] == 5
     g = gpu_run(init, 64, seed=1, t_end=0.0, snaps=[0.0], rates=rates, reac=reac, prod=prod)
     assert np.all(g["final_counts"] == init) and g["counters"]["group_steps"] == 0
+
+
+def test_tuner_picks_a_general_mode_and_keeps_the_runs():
+    """ssa_tune on a general network times blocks of 32/64/128 with the propensities incremented
+    and recomputed; the runs after tuning are the runs before it."""
+    import torch
+    reac, prod, rates, init, t_end = NETWORKS["dimer"]
+    o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), keep_snap_counts=1, pad_pow2=1)
+    ctx = pkg.ssa_create(reac, prod, rates, init, 2048, 3, o)
+    try:
+        pkg.ssa_run(ctx, t_end, [0.1])
+        before = pkg.fetch_all(ctx, n_species=2, snapshots=True)
+        layout, block = pkg.ssa_tune(ctx, t_end, [0.1])
+        assert layout == pkg.SSA_LAYOUT_THREAD and block in (32, 64, 128)
+        pkg.ssa_run(ctx, t_end, [0.1])
+        after = pkg.fetch_all(ctx, n_species=2, snapshots=True)
+    finally:
+        pkg.ssa_destroy(ctx)
+    for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
+        assert np.array_equal(before[k], after[k]), k
+    assert after["counters"]["layout"] in (pkg.SSA_LAYOUT_THREAD | 4, pkg.SSA_LAYOUT_THREAD | 8)
