@@ -217,3 +217,25 @@ def test_tuner_picks_a_general_mode_and_keeps_the_runs():
     for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
         assert np.array_equal(before[k], after[k]), k
     assert after["counters"]["layout"] in (pkg.SSA_LAYOUT_THREAD | 4, pkg.SSA_LAYOUT_THREAD | 8)
+
+
+@pytest.mark.parametrize("pad,recompute", [(0, 2), (1, 2), (1, 1)])
+def test_general_maximum_sizes(pad, recompute):
+    """8 species and 8 reactions (a ring X_i + X_{i+1} -> 2 X_{i+1}) at N_tot = 65536: K = 31,
+    17 count planes, the largest shared-memory layout (more than the default 48 KB a block)."""
+    S = 8
+    reac = [[1 if j in (i, (i + 1) % S) else 0 for j in range(S)] for i in range(S)]
+    prod = [[2 if j == (i + 1) % S else 0 for j in range(S)] for i in range(S)]
+    rates = [1.0, 0.9, 0.8, 0.7, 1.0, 0.6, 0.5, 0.4]
+    init = (8192,) * S
+    N = sum(init)
+    lam = (2 ** 31 if pad else N * (N - 1) // 2) * max(rates)
+    t_end = 3000 / lam
+    snaps = [t_end / 2]
+    n = 64 + 5
+    g = gpu_run(init, n, seed=19, t_end=t_end, snaps=snaps, rates=rates, reac=reac, prod=prod, pad_pow2=pad,
+                recompute=recompute)
+    r = oracle.run(_oracle_net(reac, prod, rates), init, n, seed=19, t_end=t_end, snap_times=snaps,
+                   threads=THREADS, pad_pow2=bool(pad))
+    _check(g, r, S, snaps)
+    assert g["counters"]["reactions"] > 0
