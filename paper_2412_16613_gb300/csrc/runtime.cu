@@ -498,6 +498,7 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
 // One bucket's launch in a batch: everything that decides the kernel and its arguments.
 struct BatchLaunch {
   int K, warps, grid, block, stream;
+  int general, smem;  // the general-network kernel and its dynamic shared memory
   FrankLaunch fl;
 };
 
@@ -509,7 +510,10 @@ int issue_batch(ssa_ctx* c, const std::vector<BatchLaunch>& plan) {
     if ((e = cudaStreamWaitEvent(s, c->fork, 0)) != cudaSuccess) return cuda_fail(c, e, "fork wait");
   for (const BatchLaunch& b : plan) {
     void* s = (void*)c->side[b.stream];
-    if (b.warps) {
+    if (b.general) {
+      if ((e = (cudaError_t)general_launcher(b.K)(b.fl, b.grid, b.block, b.smem, s)) != cudaSuccess)
+        return cuda_fail(c, e, "general bit-sliced kernel launch");
+    } else if (b.warps) {
       if ((e = (cudaError_t)frank_trio_launcher(b.K)(b.fl, b.grid, 0, s)) != cudaSuccess)
         return cuda_fail(c, e, "three-warp bit-sliced kernel launch");
     } else if ((e = (cudaError_t)frank_launcher(b.K)(b.fl, b.grid, b.block, 0, s)) != cudaSuccess) {
@@ -520,6 +524,38 @@ int issue_batch(ssa_ctx* c, const std::vector<BatchLaunch>& plan) {
     if ((e = cudaEventRecord(c->side_done[i], c->side[i])) != cudaSuccess) return cuda_fail(c, e, "join event");
     if ((e = cudaStreamWaitEvent(c->stream, c->side_done[i], 0)) != cudaSuccess) return cuda_fail(c, e, "join wait");
   }
+  return SSA_OK;
+}
+
+// Issue a batch's launch plan: on a capturable stream it is recorded once as a CUDA graph and
+// replayed while it stays the same, so a batch of any size is one graph launch.
+int run_plan(ssa_ctx* c, const std::vector<BatchLaunch>& plan) {
+  cudaError_t e;
+  if (!c->stream) return issue_batch(c, plan);  // the legacy default stream cannot be captured
+  std::vector<unsigned char> key(sizeof(BatchLaunch) * plan.size());
+  std::memcpy(key.data(), plan.data(), key.size());
+  if (!c->batch_graph || key != c->batch_graph_key) {
+    if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
+    c->batch_graph = nullptr;
+    c->batch_graph_key.clear();
+    if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(c, e, "begin capture of the batch launch");
+    const int st = issue_batch(c, plan);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    if (st != SSA_OK || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return st != SSA_OK ? st : cuda_fail(c, ee, "end capture of the batch launch");
+    }
+    e = cudaGraphInstantiate(&c->batch_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->batch_graph = nullptr;
+      return cuda_fail(c, e, "instantiate the batch graph");
+    }
+    c->batch_graph_key = key;
+  }
+  if ((e = cudaGraphLaunch(c->batch_graph, c->stream)) != cudaSuccess) return cuda_fail(c, e, "batch graph launch");
   return SSA_OK;
 }
 
@@ -565,39 +601,51 @@ int launch_general(ssa_ctx* c, FrankLaunch fl, int block, int clock_variant) {
   fl.net = c->net;
   const int hist_smem = c->batch ? 0 : c->n_snap * kHistBins * (int)sizeof(unsigned int);
   c->layout_used = SSA_LAYOUT_THREAD | (c->net.incremental ? kLayoutGeneralIncremental : kLayoutGeneralProducts);
-  struct Range {
-    int K;
-    long long begin, end;
-  };
-  std::vector<Range> ranges;
   if (!c->batch) {
-    ranges.push_back({std::max(1, c->ens[0].K), 0, (c->ens[0].n_runs + 31) / 32});
-    fl.ens = c->ens[0];
-    fl.ens_table = nullptr;
-  } else {
-    for (size_t r = 0; r < c->ranges.size(); ++r)
-      ranges.push_back({std::max(1, c->ranges[r].first), c->ranges[r].second.first, c->ranges[r].second.second});
-    fl.ens_table = c->d_ens;
-    fl.item_ens = c->d_item_ens;
-    fl.item_group = c->d_item_group;
-  }
-  for (size_t r = 0; r < ranges.size(); ++r) {
-    const int K = ranges[r].K;
+    const int K = std::max(1, c->ens[0].K);
     const int smem = hist_smem + general_smem(c, K, block);
     int occ = 0;
-    if (general_max_active_blocks(K, clock_variant | (c->batch ? 1 : 0), block, smem, &occ) != 0 || occ < 1)
+    if (general_max_active_blocks(K, clock_variant, block, smem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the general bit-sliced kernel (shared memory " +
                                     std::to_string(smem) + " bytes per block)");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
-    const long long groups = ranges[r].end - ranges[r].begin;
+    const long long groups = (c->ens[0].n_runs + 31) / 32;
     const int grid = (int)std::max(1ll, std::min((groups + block - 1) / block, (long long)c->sm_count * bpsm));
-    fl.item_begin = ranges[r].begin;
-    fl.item_end = ranges[r].end;
-    fl.queue = c->d_counters + kCounters + (c->batch ? 1 + r : 0);
+    fl.ens = c->ens[0];
+    fl.ens_table = nullptr;
+    fl.item_begin = 0;
+    fl.item_end = groups;
+    fl.queue = c->d_counters + kCounters;
     if ((e = (cudaError_t)general_launcher(K)(fl, grid, block, smem, (void*)c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "general bit-sliced kernel launch");
+    return SSA_OK;
   }
-  return SSA_OK;
+  // a batch: one launch per K bucket on the side streams, recorded as one graph like Frank's
+  fl.ens_table = c->d_ens;
+  fl.item_ens = c->d_item_ens;
+  fl.item_group = c->d_item_group;
+  std::vector<BatchLaunch> plan(c->ranges.size());
+  std::memset(plan.data(), 0, sizeof(BatchLaunch) * plan.size());
+  for (size_t r = 0; r < c->ranges.size(); ++r) {
+    BatchLaunch& b = plan[r];
+    b.K = std::max(1, c->ranges[r].first);
+    b.general = 1;
+    b.block = block;
+    b.smem = general_smem(c, b.K, block);
+    b.stream = (int)(r % c->side.size());
+    b.fl = fl;
+    b.fl.item_begin = c->ranges[r].second.first;
+    b.fl.item_end = c->ranges[r].second.second;
+    b.fl.queue = c->d_counters + kCounters + 1 + r;
+    int occ = 0;
+    if (general_max_active_blocks(b.K, clock_variant | 1, block, b.smem, &occ) != 0 || occ < 1)
+      return fail(c, SSA_ECUDA, "occupancy query failed for the general bit-sliced kernel (shared memory " +
+                                    std::to_string(b.smem) + " bytes per block)");
+    const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
+    const long long groups = b.fl.item_end - b.fl.item_begin;
+    b.grid = (int)std::max(1ll, std::min((groups + block - 1) / block, (long long)c->sm_count * bpsm));
+  }
+  return run_plan(c, plan);
 }
 
 int launch_runs(ssa_ctx* c) {
@@ -737,32 +785,7 @@ int launch_runs(ssa_ctx* c) {
       b.grid = (int)std::max(1ll, std::min((groups + block - 1) / block, (long long)c->sm_count * bpsm));
     }
   }
-  if (!c->stream) return issue_batch(c, plan);  // the legacy default stream cannot be captured
-  std::vector<unsigned char> key(sizeof(BatchLaunch) * plan.size());
-  std::memcpy(key.data(), plan.data(), key.size());
-  if (!c->batch_graph || key != c->batch_graph_key) {
-    if (c->batch_graph) cudaGraphExecDestroy(c->batch_graph);
-    c->batch_graph = nullptr;
-    c->batch_graph_key.clear();
-    if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-      return cuda_fail(c, e, "begin capture of the batch launch");
-    const int st = issue_batch(c, plan);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
-    if (st != SSA_OK || ee != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return st != SSA_OK ? st : cuda_fail(c, ee, "end capture of the batch launch");
-    }
-    e = cudaGraphInstantiate(&c->batch_graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      c->batch_graph = nullptr;
-      return cuda_fail(c, e, "instantiate the batch graph");
-    }
-    c->batch_graph_key = key;
-  }
-  if ((e = cudaGraphLaunch(c->batch_graph, c->stream)) != cudaSuccess) return cuda_fail(c, e, "batch graph launch");
-  return SSA_OK;
+  return run_plan(c, plan);
 }
 
 size_t field_bytes(const ssa_ctx* c, int field) {

@@ -239,3 +239,34 @@ def test_general_maximum_sizes(pad, recompute):
                    threads=THREADS, pad_pow2=bool(pad))
     _check(g, r, S, snaps)
     assert g["counters"]["reactions"] > 0
+
+
+def test_general_batch_graph_replay_and_legacy_stream():
+    """A general-network batch runs its K buckets as one captured graph; a replay and a run on the
+    legacy default stream (no capture) give the same runs."""
+    import torch
+    reac, prod, _, _, _ = NETWORKS["moran"]
+    N0 = np.array([[40, 60], [3, 2], [500, 524], [9000, 1000]])
+    rates = np.array([[1.0, 1.0], [1.0, 0.5], [0.7, 1.3], [1.0, 1.0]])
+    runs = np.array([64, 40, 64, 33])
+    seeds = np.array([1, 2, 3, 4], dtype=np.uint64)
+    outs = []
+    for stream in (torch.cuda.current_stream(), None):
+        o = pkg.ssa_default_options(cuda_stream=stream, pad_pow2=1)
+        ctx = pkg.ssa_create_batch(reac, prod, N0, rates, runs, seeds, o)
+        try:
+            for _ in range(2):
+                pkg.ssa_run(ctx, 0.02, [0.005])
+                outs.append(pkg.fetch_all(ctx, n_species=2))
+        finally:
+            pkg.ssa_destroy(ctx)
+    for g in outs[1:]:
+        for k in ("final_counts", "outcome", "t_abs", "ee_hist"):
+            assert np.array_equal(outs[0][k], g[k]), k
+    off = 0
+    for e in range(len(N0)):
+        r = oracle.run(_oracle_net(reac, prod, rates[e]), N0[e], int(runs[e]), seed=int(seeds[e]), t_end=0.02,
+                       snap_times=[0.005], threads=THREADS, pad_pow2=True)
+        sl = slice(off, off + runs[e])
+        assert_parity({k: outs[0][k][sl] for k in ("final_counts", "outcome", "t_abs")}, r, snaps=False)
+        off += runs[e]
