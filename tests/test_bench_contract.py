@@ -1,5 +1,5 @@
 """The benchmark's reference arm and its JSON line, on the CPU: `bench.py --impl reference`
-times the oracle on the same workload and prints one line with the contract's keys."""
+times the oracle on the same workload and prints one JSON line with the benchmark line's keys."""
 import json
 import os
 import subprocess

@@ -2,7 +2,7 @@
 
 The integer dynamics are exact in every mode; only event times differ.  The fp32
 uniform is the top 24 bits of the fp64 one, so runs with the same seed are paired
-and their time differences are the rounding error itself.  Checks (north-star
+and their time differences are the rounding error itself.  Checks (the precision
 targets): two-sample KS p > 0.01 on absorption times and means within 3 standard
 errors, both for paired runs and for independent seeds; the ee histograms at the
 snapshots agree (chi-square p > 0.01).  The plain fp32 sum (no compensation) is
