@@ -4,7 +4,7 @@ The integer dynamics are exact in every mode; only event times differ.  The fp32
 uniform is the top 24 bits of the fp64 one, so runs with the same seed are paired
 and their time differences are the rounding error itself.  Checks (the precision
 targets): two-sample KS p > 0.01 on absorption times and means within 3 standard
-errors, both for paired runs and for independent seeds; the ee histograms at the
+errors, both for paired runs and for independent seeds (one run per group); the ee histograms at the
 snapshots agree (chi-square p > 0.01).  The plain fp32 sum (no compensation) is
 the control: its paired time error must exceed the compensated one's.
 """
@@ -65,8 +65,12 @@ def test_fp32_clock_paired_with_fp64(runs, mode):
 
 
 def test_fp32_kahan_against_independent_fp64(runs):
+    """Independent seeds, one run per group: the 32 runs of a group share the group's clock, so
+    their absorption times are not independent samples and a KS test over all runs would be too
+    strict (over 2^22 runs it separates two fp64 seeds at p = 0.005; one run per group, p = 0.40)."""
     a, b = runs["kahan_other_seed"], runs["p64_other_seed"]
-    ta, tb = a["t_abs"][np.isfinite(a["t_abs"])], b["t_abs"][np.isfinite(b["t_abs"])]
+    ta, tb = a["t_abs"][::32], b["t_abs"][::32]
+    ta, tb = ta[np.isfinite(ta)], tb[np.isfinite(tb)]
     se = math.sqrt(ta.var() / len(ta) + tb.var() / len(tb))
     assert abs(ta.mean() - tb.mean()) < 3 * se
     assert stats.ks_2samp(ta, tb).pvalue > 0.01
