@@ -13,7 +13,9 @@
  * equation-v) and incremental propensity updates (Eqs. equation-a-1..3,
  * App. B).  Ghost reactions (Eqs. 4-6) make the total rate the constant
  * Lambda = k_max * N (N - 1) / 2 (Eq. equation-z), so the waiting time
- * tau ~ Exp(Lambda) (Eq. equation-tau) does not depend on the state.
+ * tau ~ Exp(Lambda) (Eq. equation-tau) does not depend on the state.  Options
+ * raise the bound to k_max 2^K (ssa_options.pad_pow2), and networks other than
+ * Frank's use k_max (m_pair C(N, 2) + u_max N) (see ssa_create).
  *
  * Here a word is 32 bits and holds one *group* of 32 runs; run j is lane
  * j % 32 of group j / 32.  Every group draws its random bits from a Philox4x32-10
