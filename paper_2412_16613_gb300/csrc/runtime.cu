@@ -819,7 +819,7 @@ void ssa_default_options(ssa_options* opt) {
   opt->device = -1;
 }
 
-int ssa_version(void) { return 100; }
+int ssa_version(void) { return 200; }  // 0.2.0: general networks, padded bound, general modes
 
 int ssa_create(const int32_t* reactants, const int32_t* products, int32_t n_species, int32_t n_reactions,
                const double* rates, const int64_t* N0, int32_t n0_per_run, int64_t n_runs, uint64_t seed,

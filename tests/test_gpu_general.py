@@ -270,3 +270,18 @@ def test_general_batch_graph_replay_and_legacy_stream():
         sl = slice(off, off + runs[e])
         assert_parity({k: outs[0][k][sl] for k in ("final_counts", "outcome", "t_abs")}, r, snaps=False)
         off += runs[e]
+
+
+@pytest.mark.parametrize("init,n", [((0, 5), 40), ((1, 0), 33), ((3, 3), 0)])
+def test_general_degenerate_and_empty(init, n):
+    """Runs that start absorbed (one species left, or N_tot = 1) keep their state with t_abs = 0;
+    a context with no runs runs and fetches nothing."""
+    reac, prod, rates, _, _ = NETWORKS["moran"]
+    g = gpu_run(init, n, seed=6, t_end=1.0, snaps=[0.5] if n else [], rates=rates, reac=reac, prod=prod)
+    if n == 0:
+        assert g["final_counts"].size == 0 and g["counters"]["group_steps"] == 0
+        return
+    r = oracle.run(_oracle_net(reac, prod, rates), init, n, seed=6, t_end=1.0, snap_times=[0.5], threads=THREADS)
+    _check(g, r, 2, [0.5])
+    assert np.all(g["t_abs"] == 0.0) and np.all(g["final_counts"] == init)
+    assert g["counters"]["group_steps"] == 0
