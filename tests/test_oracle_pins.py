@@ -588,3 +588,44 @@ def test_sum_pseudocode_reading():
         for y in range(16):
             assert ripple(x, y, 4, printed=False) == x + y
     assert [p & q for p, q in zip(g["and_b1"], g["and_b2"])] == g["and_out"]
+
+
+# --------------------------------------------------------------------------
+# Closed forms of networks other than Frank's.
+# --------------------------------------------------------------------------
+def test_closed_form_isomerisation(orc):
+    """A -> B at rate a, B -> A at rate b (first order, thinned when a != b): each molecule flips
+    on its own, so n_A(t) is Bin(n_A0, p_AA(t)) + Bin(n_B0, p_BA(t)) with
+    p_AA = (b + a e^{-(a+b)t}) / (a+b) and p_BA = b (1 - e^{-(a+b)t}) / (a+b)."""
+    a, b = 1.0, 0.4
+    nA0, nB0 = 14, 6
+    net = orc.Network([[1, 0], [0, 1]], [[0, 1], [1, 0]], [a, b])
+    snaps = [0.3, 1.2]
+    runs = 40_000
+    r = orc.run(net, (nA0, nB0), run_ids=np.arange(runs) * 32 + 2, seed=61, t_end=1.2, snap_times=snaps)
+    for s, t in enumerate(snaps):
+        e = math.exp(-(a + b) * t)
+        p_aa, p_ba = (b + a * e) / (a + b), b * (1 - e) / (a + b)
+        pmf = np.convolve(stats.binom.pmf(np.arange(nA0 + 1), nA0, p_aa), stats.binom.pmf(np.arange(nB0 + 1), nB0, p_ba))
+        obs = np.bincount(r["snap_counts"][s][:, 0], minlength=nA0 + nB0 + 1).astype(float)
+        exp = pmf * runs
+        big = exp >= 5
+        o, ex = np.append(obs[big], obs[~big].sum()), np.append(exp[big], exp[~big].sum())
+        assert stats.power_divergence(o, ex, lambda_="log-likelihood")[1] > 1e-4, t
+
+
+@pytest.mark.parametrize("k", [(1.0, 1.0), (1.0, 0.6)])
+def test_closed_form_moran_fixation(orc, k):
+    """A + B -> 2A (k1), A + B -> 2B (k2): the jump chain of n_A is a gambler's ruin with up-step
+    probability p = k1 / (k1 + k2), so A fixes from i with probability (1 - (q/p)^i) / (1 - (q/p)^N)
+    (i / N when p = 1/2)."""
+    net = orc.Network([[1, 1], [1, 1]], [[2, 0], [0, 2]], list(k))
+    i, N = 7, 20
+    runs = 40_000
+    r = orc.run(net, (i, N - i), run_ids=np.arange(runs) * 32 + 9, seed=71, t_end=np.inf)
+    assert np.all(r["outcome"] >= 0)
+    p = k[0] / (k[0] + k[1])
+    rho = (1 - p) / p
+    want = i / N if p == 0.5 else (1 - rho ** i) / (1 - rho ** N)
+    got = np.mean(r["outcome"] == 0)
+    assert abs(got - want) < 4.5 * math.sqrt(want * (1 - want) / runs), (got, want)
