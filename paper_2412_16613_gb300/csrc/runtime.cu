@@ -5,6 +5,7 @@
 // thinning thresholds), owns the device buffers, and launches the bit-sliced
 // kernel instantiation for each K (or the one-thread-per-run baseline).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -151,6 +152,13 @@ Threshold make_threshold(double t, double lambda) {
 }  // namespace bitssa
 
 namespace {
+
+// An NVTX range for the lifetime of a scope: named ranges around runs, launches and the tuner
+// for profilers that follow NVTX (no cost without one attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct Allocator {
   ssa_alloc_fn alloc = nullptr;
@@ -649,6 +657,7 @@ int launch_general(ssa_ctx* c, FrankLaunch fl, int block, int clock_variant) {
 }
 
 int launch_runs(ssa_ctx* c) {
+  NvtxRange range(c->batch ? "bitssa batch launch" : "bitssa launch");
   const int n_snap = c->n_snap;
   cudaError_t e;
   FrankLaunch fl;
@@ -1046,6 +1055,7 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
 }
 
 int ssa_run(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_snap) {
+  NvtxRange range("ssa_run");
   if (!c) return fail(nullptr, SSA_EINVAL, "ctx is NULL");
   if (!(t_end >= 0.0)) return fail(c, SSA_EINVAL, "t_end must be >= 0");
   if (n_snap < 0 || n_snap > kMaxSnap) return fail(c, SSA_EINVAL, "n_snap must be in [0, 64]");
@@ -1101,6 +1111,7 @@ int ssa_run(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_sn
 
 int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_snap, int64_t probe_steps,
              int32_t* choice) {
+  NvtxRange range("ssa_tune");
   if (!c) return fail(nullptr, SSA_EINVAL, "ctx is NULL");
   if (probe_steps < 0) return fail(c, SSA_EINVAL, "probe_steps must be >= 0");
   if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN)
