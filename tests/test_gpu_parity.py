@@ -419,3 +419,15 @@ def test_parity_padded_bound_shared_n():
     r = oracle.run(oracle.frank(), init, seed=5, t_end=2.0, snap_times=[0.01, 0.1], shared_n=True,
                    pad_pow2=True, threads=THREADS)
     assert_parity(g, r)
+
+
+@LAYOUTS
+def test_a_later_t_end_extends_the_same_runs(layout):
+    """A run is a fixed function of its stream: the final counts of a run stopped at t1 are the
+    snapshot at t1 of the same run continued to t2 > t1 (absorbed runs: the same t_abs)."""
+    t1, t2 = 0.01, 0.05
+    a = gpu_run((256, 256, 512), 2048, seed=9, t_end=t1, layout=layout, pad_pow2=1)
+    b = gpu_run((256, 256, 512), 2048, seed=9, t_end=t2, snaps=[t1], layout=layout, pad_pow2=1)
+    assert np.array_equal(a["final_counts"], b["snap_counts"][0])
+    done = np.isfinite(a["t_abs"])
+    assert np.array_equal(a["t_abs"][done], b["t_abs"][done])
