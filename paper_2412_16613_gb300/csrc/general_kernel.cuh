@@ -8,10 +8,10 @@
 //   h_r = x_a x_b            (A + B -> ...)
 //   h_r = x_a (x_a - 1) / 2  (2A -> ...)
 //   h_r = x_a                (A -> ...)
-// The count planes live in shared memory as [species][plane][thread] words, so that a
-// reaction's reactants are found by index at run time and one kernel serves every network
-// of up to 8 species and 8 reactions; the per-step values (n, the running sum S, one
-// product) stay in registers.
+// The count planes live in shared memory (each warp's region laid out [word][lane], plane i of
+// species s at word s PL + i), so that a reaction's reactants are found by index at run time and
+// one kernel serves every network of up to 8 species and 8 reactions; the per-step values (n,
+// the running sum S, one product) stay in registers.
 //
 // Incremental mode (the default) keeps every h_r in shared memory as well and, after each
 // event, adds its change, which for mass action is linear in the counts before the event
