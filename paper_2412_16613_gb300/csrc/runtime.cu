@@ -1,9 +1,11 @@
 // runtime.cu -- host side of libbitssa: the C ABI declared in include/bitssa.h.
 //
 // Validates and copies the inputs, derives the per-ensemble constants of the
-// method (lambda_int = N (N - 1) / 2 of Eq. equation-z, its bit length K, the
-// thinning thresholds), owns the device buffers, and launches the bit-sliced
-// kernel instantiation for each K (or the one-thread-per-run baseline).
+// method (lambda_int = N (N - 1) / 2 of Eq. equation-z, or its general form
+// m_pair C(N, 2) + u_max N, or 2^K when padded; K; the thinning thresholds), owns
+// the device buffers, and launches the bit-sliced kernel instantiation for each K:
+// Frank's two layouts or the general-network kernel (or the one-thread-per-run
+// baseline).
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -290,7 +292,8 @@ void dev_free_all(ssa_ctx* c) {
 
 // ---------------------------------------------------------------------------
 // Validation of the network: order 1 or 2, conservation of the total count
-// (Sec. 2), and recognition of Frank's model (Eqs. 1-3) up to relabelling.
+// (Sec. 2), at most 8 species and 8 reactions, and recognition of Frank's model
+// (Eqs. 1-3) up to relabelling (every other network goes to the general kernel).
 // ---------------------------------------------------------------------------
 int check_network(const int32_t* reac, const int32_t* prod, int S, int R, int perm[3], bool* frank,
                   std::string* why) {
