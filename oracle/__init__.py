@@ -52,6 +52,7 @@ class Problem(C.Structure):
         ("precision", C.c_int32), ("thin_bits", C.c_int32), ("t_end", C.c_double),
         ("snap_times", C.POINTER(C.c_double)), ("n_snap", C.c_int32),
         ("step_budget", C.c_int64), ("shared_n", C.c_int32), ("pad_pow2", C.c_int32),
+        ("ensemble_runs", C.c_int64),
     ]
 
 
@@ -122,13 +123,13 @@ def frank(k1=1.0, k2=1.0, k3=1.0) -> Network:
 
 
 def _problem(net: Network, n_tot, seed, precision=P64, thin_bits=32, t_end=np.inf,
-             snap_times=(), step_budget=0, shared_n=False, pad_pow2=False):
+             snap_times=(), step_budget=0, shared_n=False, pad_pow2=False, ensemble_runs=0):
     snaps = np.ascontiguousarray(snap_times, dtype=np.float64)
     p = Problem(net.n_species, net.n_reactions, _ptr(net.reactants, C.c_int32),
                 _ptr(net.products, C.c_int32), _ptr(net.rates, C.c_double), int(n_tot),
                 int(seed) & (2**64 - 1), int(precision), int(thin_bits), float(t_end),
                 _ptr(snaps, C.c_double) if len(snaps) else None, len(snaps), int(step_budget),
-                1 if shared_n else 0, 1 if pad_pow2 else 0)
+                1 if shared_n else 0, int(pad_pow2), int(ensemble_runs))
     p._keep = (net, snaps)  # keep the arrays alive as long as the struct
     return p
 
@@ -174,12 +175,17 @@ def ee_bin(L, D):
 
 def run(net: Network, init, n_runs=None, *, seed=0, precision=P64, thin_bits=32, t_end=np.inf,
         snap_times=(), step_budget=0, first_run=0, run_ids=None, threads=None,
-        want_snapshots=True, check=True, shared_n=False, pad_pow2=False):
+        want_snapshots=True, check=True, shared_n=False, pad_pow2=False, ensemble_runs=None):
     """Run the oracle on runs first_run .. first_run+n_runs-1 (or on run_ids).
 
     init: [S] shared initial counts or [n_runs][S] per-run counts.
     shared_n: every run of a group of 32 uses the n of the group's lane 0 (Sec. 4, step a).
-    pad_pow2: the uniformisation bound is 2^K (null events fill the gap above lambda_int).
+    pad_pow2: 1 (or True): the uniformisation bound is 2^K (null events fill the gap above
+        lambda_int); 2: the bound follows the group's state, 2^p with p the bit length of the
+        largest S_R over the group's live runs, and each run comes out of its whole group.
+    ensemble_runs (pad_pow2 = 2): runs in the ensemble, which fixes the lanes of its last group;
+        default first_run + n_runs without run_ids, else every group full.  A per-run init then
+        holds one row per run of the ensemble, indexed by run.
     Returns a dict of numpy arrays indexed by run position.
     """
     init = np.ascontiguousarray(init, dtype=np.int64)
@@ -190,9 +196,17 @@ def run(net: Network, init, n_runs=None, *, seed=0, precision=P64, thin_bits=32,
         n_runs = len(ids)
     if n_runs is None:
         n_runs = init.shape[0] if per_run else 1
+    pad_pow2 = int(pad_pow2)
+    if ensemble_runs is None:
+        ensemble_runs = first_run + n_runs if (pad_pow2 == 2 and ids is None) else 0
+    if pad_pow2 == 2 and per_run:
+        last = int(ids.max()) if ids is not None and len(ids) else first_run + n_runs - 1
+        need = max(ensemble_runs, 32 * (last // 32 + 1)) if ensemble_runs == 0 else ensemble_runs
+        if init.shape[0] < need:
+            raise ValueError("pad_pow2 = 2 with per-run counts needs a row for every run of each group")
     n_tot = int(init.reshape(-1, net.n_species)[0].sum())
     p = _problem(net, n_tot, seed, precision, thin_bits, t_end, snap_times, step_budget, shared_n,
-                 pad_pow2)
+                 pad_pow2, ensemble_runs)
     out = (Result * max(n_runs, 1))()
     n_snap = len(snap_times)
     snaps = (np.zeros((n_snap, n_runs, net.n_species), dtype=np.int64)

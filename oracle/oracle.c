@@ -203,7 +203,7 @@ int orc_derive(const orc_problem* p, orc_derived* d) {
   d->K = bit_length(d->lambda_int);
   /* Uniformisation at any bound at or above the largest total propensity samples the same
    * process; padding the bound to 2^K with further null events makes every K-bit n valid. */
-  if (p->pad_pow2 != 0 && p->pad_pow2 != 1) return ORC_EINVAL;
+  if (p->pad_pow2 < 0 || p->pad_pow2 > 2 || p->ensemble_runs < 0) return ORC_EINVAL;
   if (p->pad_pow2) d->lambda_int = (uint64_t)1 << d->K;
   d->k_max = k_max;
   d->lambda = k_max * (double)d->lambda_int;
@@ -256,6 +256,7 @@ int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index, const
   out->t_abs = INFINITY;
   out->outcome = -1;
   out->margin = INFINITY;
+  if (p->pad_pow2 == 2) return out->status = ORC_EINVAL; /* needs the whole group: orc_run_group */
   for (int i = 0; i < S; i++) {
     n[i] = init[i];
     total += n[i];
@@ -405,6 +406,181 @@ fill_snapshots:
 }
 
 /* ------------------------------------------------------------------------ */
+/* A group of runs under a bound that follows the group's state.             */
+/* ------------------------------------------------------------------------ */
+/* Uniformisation samples the process at any rate that is at least the total
+ * propensity, and the rate may change with the state, which is constant between
+ * steps.  With pad_pow2 = 2 the bound of a step is 2^p, p the bit length of the
+ * largest S_R over the group's live runs, so S_R < 2^p for every live run and a
+ * p-bit n always lands in [0, 2^p).  A run still jumps by reaction r at rate
+ * (k_max 2^p) (h_r / 2^p) (k_r / k_max) = k_r h_r, whatever the other runs hold. */
+static int group_bound_bits(const orc_problem* p, int lanes, const int64_t (*n)[ORC_MAX_SPECIES],
+                            const int* live) {
+  uint64_t top = 0;
+  for (int l = 0; l < lanes; l++) {
+    if (!live[l]) continue;
+    uint64_t sum = 0;
+    for (int r = 0; r < p->n_reactions; r++) sum += (uint64_t)propensity(p, r, n[l]);
+    if (sum > top) top = sum;
+  }
+  return bit_length(top);
+}
+
+int orc_run_group(const orc_problem* p, const orc_derived* d, uint64_t group, int32_t lanes,
+                  const int64_t* init, int32_t init_per_lane, orc_result* out, int64_t* snap_counts) {
+  const int S = p->n_species;
+  const int K = d->K;
+  if (p->pad_pow2 != 2 || lanes < 1 || lanes > 32) return ORC_EINVAL;
+  int64_t n[32][ORC_MAX_SPECIES];
+  int live[32];
+  int n_live = 0;
+  for (int l = 0; l < lanes; l++) {
+    memset(&out[l], 0, sizeof out[l]);
+    out[l].t_abs = INFINITY;
+    out[l].outcome = -1;
+    out[l].margin = INFINITY;
+    const int64_t* c = init + (init_per_lane ? (int64_t)l * S : 0);
+    int64_t total = 0;
+    for (int i = 0; i < S; i++) {
+      n[l][i] = c[i];
+      total += c[i];
+      if (c[i] < 0) return ORC_EINVAL;
+    }
+    if (total != p->n_tot) return ORC_EINVAL;
+    live[l] = real_propensity_sum(p, n[l]) > 0;
+    if (!live[l]) {
+      out[l].t_abs = 0.0;
+      out[l].outcome = outcome_of(p, n[l]);
+    }
+    n_live += live[l];
+  }
+
+  word_source ws;
+  memset(&ws, 0, sizeof ws);
+  ws.key[0] = (uint32_t)(p->seed & 0xFFFFFFFFu);
+  ws.key[1] = (uint32_t)(p->seed >> 32);
+  double t = 0.0;
+  float t_f = 0.0f, c_f = 0.0f;
+  int has_event = 0, next_snap = 0, status = ORC_OK;
+  int64_t step = 0;
+
+  while (n_live > 0) {
+    if (p->step_budget > 0 && step >= p->step_budget) {
+      status = ORC_ETIMEOUT;
+      break;
+    }
+    /* (1) this step's bound from the group's state */
+    const int bits = group_bound_bits(p, lanes, (const int64_t(*)[ORC_MAX_SPECIES])n, live);
+    const double lambda_s = ldexp(d->k_max, bits);
+
+    /* (2) the waiting time at rate lambda_s, from the words K and K+1 of attempt 0 */
+    uint32_t wk0 = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)K);
+    uint32_t wk1 = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)K + 1);
+    double t_new;
+    float t_f_new = 0.0f, c_f_new = 0.0f;
+    if (p->precision == ORC_P64) {
+      uint64_t x = ((uint64_t)wk1 << 21) | (uint64_t)(wk0 >> 11);
+      double u = (double)(x + 1) * 0x1p-53;
+      t_new = t + (-log(u) / lambda_s);
+    } else {
+      float u = (float)((wk1 >> 8) + 1u) * 0x1p-24f;
+      float tau = -logf(u) * (float)(1.0 / lambda_s);
+      if (p->precision == ORC_P32_KAHAN) {
+        float y = tau - c_f;
+        float sum = t_f + y;
+        c_f_new = (sum - t_f) - y;
+        t_f_new = sum;
+        t_new = (double)sum;
+      } else if (p->precision == ORC_P32_PLAIN) {
+        t_f_new = t_f + tau;
+        t_new = (double)t_f_new;
+      } else {
+        t_new = t + (double)tau;
+      }
+    }
+
+    /* (3) snapshots and t_end, as for a single run */
+    int stop = 0;
+    for (;;) {
+      const int at_end = !(next_snap < p->n_snap && p->snap_times[next_snap] < t_new);
+      if (at_end && !(t_new > p->t_end)) break;
+      const double ts = at_end ? p->t_end : p->snap_times[next_snap];
+      double gap = relative_gap(t_new, ts, ts);
+      double gap_before = has_event ? relative_gap(ts, t, ts) : INFINITY;
+      if (gap_before < gap) gap = gap_before;
+      for (int l = 0; l < lanes; l++)
+        if (live[l] && gap < out[l].margin) out[l].margin = gap;
+      if (at_end) {
+        stop = 1;
+        break;
+      }
+      if (snap_counts)
+        for (int l = 0; l < lanes; l++)
+          for (int i = 0; i < S; i++)
+            snap_counts[((int64_t)l * p->n_snap + next_snap) * S + i] = n[l][i];
+      next_snap++;
+    }
+    if (stop) break;
+    t = t_new;
+    t_f = t_f_new;
+    c_f = c_f_new;
+    has_event = 1;
+
+    /* (4) every live run draws its n from the low `bits` planes and reacts */
+    for (int l = 0; l < lanes; l++) {
+      if (!live[l]) continue;
+      const int n_lane = p->shared_n ? 0 : l;
+      uint64_t draw = 0;
+      for (int i = 0; i < bits; i++)
+        draw |= (uint64_t)lane_bit(word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)i), n_lane) << i;
+      int32_t r = orc_select(p, n[l], draw);
+      if (r >= 0 && !d->thin_always[r]) {
+        uint64_t U = 0;
+        for (int i = 0; i < p->thin_bits; i++) {
+          uint32_t w = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)(K + 2 + i));
+          U |= (uint64_t)lane_bit(w, l) << (p->thin_bits - 1 - i);
+        }
+        if (!(U < d->thin_T[r])) r = -1;
+      }
+      if (r < 0) continue;
+      int64_t check = 0;
+      for (int i = 0; i < S; i++) {
+        n[l][i] += p->products[r * S + i] - p->reactants[r * S + i];
+        if (n[l][i] < 0) return ORC_ERANGE;
+        check += n[l][i];
+      }
+      if (check != p->n_tot) return ORC_ERANGE;
+      out[l].reactions++;
+    }
+    step++;
+
+    /* (5) absorption, run by run */
+    for (int l = 0; l < lanes; l++) {
+      if (!live[l] || real_propensity_sum(p, n[l]) != 0) continue;
+      live[l] = 0;
+      n_live--;
+      out[l].t_abs = t;
+      out[l].outcome = outcome_of(p, n[l]);
+      out[l].steps = step;
+      out[l].t_last = (p->precision == ORC_P32_KAHAN || p->precision == ORC_P32_PLAIN) ? (double)t_f : t;
+    }
+  }
+
+  for (int l = 0; l < lanes; l++) {
+    if (out[l].outcome != -1 && snap_counts)  /* an absorbed run keeps its state for ever */
+      for (int s = next_snap; s < p->n_snap; s++)
+        for (int i = 0; i < S; i++) snap_counts[((int64_t)l * p->n_snap + s) * S + i] = n[l][i];
+    for (int i = 0; i < S; i++) out[l].final_counts[i] = n[l][i];
+    if (live[l]) {
+      out[l].steps = step;
+      out[l].t_last = (p->precision == ORC_P32_KAHAN || p->precision == ORC_P32_PLAIN) ? (double)t_f : t;
+      out[l].status = status;
+    }
+  }
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Many runs over host threads.                                              */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -422,9 +598,64 @@ typedef struct {
   pthread_mutex_t lock;
 } batch_job;
 
+/* pad_pow2 = 2: a run's result comes out of its whole group, which is kept while the
+ * following runs asked for fall in the same group. */
+static void* group_worker(void* arg) {
+  batch_job* job = (batch_job*)arg;
+  const orc_problem* p = job->p;
+  const int S = p->n_species;
+  const int64_t per_group = (int64_t)p->n_snap * S;
+  orc_result res[32];
+  int64_t lane_init[32 * ORC_MAX_SPECIES];
+  int64_t* snaps = NULL;
+  if (job->snap_counts && p->n_snap > 0) snaps = (int64_t*)malloc(sizeof(int64_t) * 32 * (size_t)per_group);
+  int64_t held = -1; /* the group in res, -1 none */
+  int held_status = ORC_OK, held_lanes = 0;
+  for (;;) {
+    int64_t i = __atomic_fetch_add(&job->next, 16, __ATOMIC_RELAXED);
+    if (i >= job->n_runs) break;
+    int64_t stop = i + 16 < job->n_runs ? i + 16 : job->n_runs;
+    for (; i < stop; i++) {
+      const int64_t run = job->run_ids ? job->run_ids[i] : job->first_run + i;
+      const int64_t g = run / 32;
+      int st = ORC_OK;
+      if (run < 0 || (p->ensemble_runs > 0 && run >= p->ensemble_runs)) {
+        st = ORC_EINVAL;
+      } else {
+        if (g != held) {
+          int64_t left = p->ensemble_runs > 0 ? p->ensemble_runs - 32 * g : 32;
+          held_lanes = left < 32 ? (int)left : 32;
+          for (int l = 0; l < held_lanes; l++)
+            for (int k = 0; k < S; k++)
+              lane_init[l * S + k] = job->init[(job->init_per_run ? (32 * g + l) * S : 0) + k];
+          held_status = orc_run_group(p, job->d, (uint64_t)g, held_lanes, lane_init, 1, res, snaps);
+          held = g;
+        }
+        const int lane = (int)(run % 32);
+        job->out[i] = res[lane];
+        if (held_status != ORC_OK && held_status != ORC_ETIMEOUT) st = held_status;
+        else st = res[lane].status;
+        if (snaps)
+          for (int s = 0; s < p->n_snap; s++)
+            for (int k = 0; k < S; k++)
+              job->snap_counts[((int64_t)s * job->n_runs + i) * S + k] = snaps[lane * per_group + s * S + k];
+      }
+      if (st != ORC_OK) {
+        job->out[i].status = st;
+        pthread_mutex_lock(&job->lock);
+        if (job->status == ORC_OK) job->status = st;
+        pthread_mutex_unlock(&job->lock);
+      }
+    }
+  }
+  free(snaps);
+  return NULL;
+}
+
 static void* batch_worker(void* arg) {
   batch_job* job = (batch_job*)arg;
   const int S = job->p->n_species;
+  if (job->p->pad_pow2 == 2) return group_worker(arg);
   int64_t* snaps = NULL;
   if (job->snap_counts && job->p->n_snap > 0)
     snaps = (int64_t*)malloc(sizeof(int64_t) * (size_t)job->p->n_snap * (size_t)S);

@@ -19,8 +19,11 @@
  *   n   = sum_{i<K} bit_l(w_i) 2^i; while n >= Lambda_int, its bits from p up (p the
  *         highest bit where n and Lambda_int differ, 0 if equal) are replaced by the
  *         same bits of attempt a+1 (a uniform integer in [0, Lambda_int), Sec. 3 step
- *         5(i) and step a); with pad_pow2, Lambda_int = 2^K and no draw is rejected;
- *   tau = -log(u) / Lambda from the whole words w_K, w_{K+1} of attempt 0
+ *         5(i) and step a); with pad_pow2 = 1, Lambda_int = 2^K and no draw is rejected;
+ *         with pad_pow2 = 2 the bound of step s is 2^p, p = the bit length of the largest
+ *         S_R over the live runs of the group, and n = sum_{i<p} bit_l(w_i) 2^i;
+ *   tau = -log(u) / Lambda (Lambda = k_max 2^p with pad_pow2 = 2) from the whole
+ *         words w_K, w_{K+1} of attempt 0
  *         (Eq. equation-tau, with the uniformisation rate of Eq. equation-z):
  *         fp64 u = (x + 1) 2^-53 with x = w_{K+1} << 21 | w_K >> 11; the fp32
  *         modes take u = ((w_{K+1} >> 8) + 1) 2^-24, the top 24 of those bits;
@@ -74,7 +77,12 @@ typedef struct {
   int32_t shared_n;         /* 1: every run of a group of 32 uses the n of the group's lane 0 (one n
                                for all copies, Sec. 4 step a), drawn whether or not lane 0 is live */
   int32_t pad_pow2;         /* 1: the uniformisation bound is raised from lambda_int to 2^K with
-                               further null events, so that every K-bit draw of n is accepted */
+                               further null events, so that every K-bit draw of n is accepted;
+                               2: the bound follows the group's state (2^p at each step, p the
+                               bit length of the largest S_R over the group's live runs), so the
+                               32 runs of a group are stepped together */
+  int64_t ensemble_runs;    /* pad_pow2 = 2: runs in the ensemble, which fixes how many lanes the
+                               last group holds; 0 = every group holds 32 runs */
 } orc_problem;
 
 /* Derived constants of a problem, computed from their definitions. */
@@ -121,10 +129,17 @@ int32_t orc_select(const orc_problem* p, const int64_t* state, uint64_t n);
 int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index,
             const int64_t* init, orc_result* out, int64_t* snap_counts);
 
+/* The lanes of one group stepped together (pad_pow2 = 2).  init is [S] (init_per_lane = 0)
+ * or [lanes][S]; out is [lanes]; snap_counts is [lanes][n_snap][S] or NULL. */
+int orc_run_group(const orc_problem* p, const orc_derived* d, uint64_t group, int32_t lanes,
+                  const int64_t* init, int32_t init_per_lane, orc_result* out, int64_t* snap_counts);
+
 /* Many runs on n_threads host threads.  Run i is global run run_ids[i] (or
  * first_run + i when run_ids is NULL).  init is [S] (init_per_run = 0) or
- * [n_runs][S].  Outputs are per run, indexed by i; any may be NULL except out.
- * snap_counts is [n_snap][n_runs][S].  Returns the first non-OK status. */
+ * [n_runs][S]; with pad_pow2 = 2 a per-run init is indexed by the run's global index
+ * instead, and holds a row for every run of the groups asked for.  Outputs are per run,
+ * indexed by i; any may be NULL except out.  snap_counts is [n_snap][n_runs][S].
+ * Returns the first non-OK status. */
 int orc_run_many(const orc_problem* p, int64_t first_run, const int64_t* run_ids, int64_t n_runs,
                  const int64_t* init, int32_t init_per_run, orc_result* out,
                  int64_t* snap_counts, int32_t n_threads);

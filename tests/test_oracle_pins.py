@@ -282,15 +282,16 @@ def _frank_me(N, rates=(1.0, 1.0, 1.0)):
 
 
 @pytest.mark.parametrize("lane,shared,pad", [(0, False, False), (17, False, False), (17, True, False),
-                                            (5, False, True), (9, True, True)])
+                                            (5, False, True), (9, True, True), (0, False, 2), (23, False, 2)])
 def test_master_equation_distribution(orc, lane, shared, pad):
     """Each lane is an exact sample path, also when it reacts to the n of its group's lane 0
-    (one n for all copies, Sec. 4 step a): n never depends on the state; and also with the
-    bound padded from Z = 66 to 128 (uniformisation at a larger rate)."""
+    (one n for all copies, Sec. 4 step a): n never depends on the state; also with the
+    bound padded from Z = 66 to 128 (uniformisation at a larger rate); and with a bound that
+    follows the state of the lane's whole group (pad = 2: a rate that changes between steps)."""
     N, init = 12, (3, 3, 6)
     st, index, Q = _frank_me(N)
     snaps = [0.02, 0.05, 0.1, 0.2, 0.4]
-    runs = 40_000
+    runs = 40_000 if pad != 2 else 20_000
     # one lane per group: groups draw from independent counters
     r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32 + lane, seed=21, t_end=0.5,
                 snap_times=snaps, shared_n=shared, pad_pow2=pad)
@@ -375,14 +376,14 @@ def test_shared_n_lanes_follow_one_draw(orc):
     assert len({tuple(x) for x in a["final_counts"][:32]}) > 1
 
 
-@pytest.mark.parametrize("pad", [False, True])
+@pytest.mark.parametrize("pad", [False, True, 2])
 def test_master_equation_absorption(orc, pad):
     """Absorption probabilities and mean absorption time from the fundamental matrix."""
     N, init = 12, (5, 2, 5)
     st, index, Q = _frank_me(N)
     absorbing, B, T, transient = me.absorption(Q)
     i0 = transient.index(index[init])
-    runs = 40_000
+    runs = 40_000 if pad != 2 else 20_000
     r = orc.run(orc.frank(), init, run_ids=np.arange(runs) * 32, seed=33, t_end=np.inf, pad_pow2=pad)
     assert np.all(r["outcome"] >= 0)
     for col, a in enumerate(absorbing):
@@ -629,3 +630,91 @@ def test_closed_form_moran_fixation(orc, k):
     want = i / N if p == 0.5 else (1 - rho ** i) / (1 - rho ** N)
     got = np.mean(r["outcome"] == 0)
     assert abs(got - want) < 4.5 * math.sqrt(want * (1 - want) / runs), (got, want)
+
+
+# --------------------------------------------------------------------------
+# The bound that follows the group's state (pad_pow2 = 2).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("others", [None, (16, 16, 32)])
+def test_state_following_bound_first_step(orc, others):
+    """The first step of a run in state (1, 1, 62): reaction r with probability h_r / 2^p and a
+    waiting time of mean 1 / 2^p, p the bit length of the largest S_R in the group. Alone with
+    its copies S_R = 62 + 62 + 1 = 125 and 2^p = 128; next to runs in (16, 16, 32)
+    (S_R = 1280) 2^p = 2048, the padded bound of N = 64."""
+    groups = 6000
+    init = np.tile(np.array([16, 16, 32] if others else [1, 1, 62]), (32 * groups, 1))
+    init[::32] = (1, 1, 62)
+    r = orc.run(orc.frank(), init, seed=41, step_budget=1, check=False, pad_pow2=2)
+    bound = 2048 if others else 128
+    lanes = np.arange(32 * groups) % 32 == 0 if others else np.ones(32 * groups, bool)
+    fc = r["final_counts"][lanes]
+    m = lanes.sum()
+    h = np.array([62, 62, 1])
+    got = [np.sum(fc[:, 0] == 2), np.sum(fc[:, 1] == 2), np.sum(fc[:, 2] == 64)]
+    for k in range(3):
+        p = h[k] / bound
+        assert abs(got[k] - m * p) < 4.5 * math.sqrt(m * p * (1 - p)) + 1, (k, got[k], m * p)
+    t1 = r["t_last"][::32]  # one clock per group
+    assert abs(t1.mean() * bound - 1.0) < 4.5 / math.sqrt(groups)
+
+
+@pytest.mark.parametrize("net_i", [0, 3])
+def test_state_following_bound_general_networks(orc, net_i):
+    """Networks other than Frank's under the state-following bound, against the master equation."""
+    reac, prod, rates, init = GENERAL_NETWORKS[net_i]
+    N = sum(init)
+    st, index, Q = me.generator(reac, prod, rates, N)
+    snaps = [0.05, 0.2, 0.6]
+    runs = 15_000
+    r = orc.run(orc.Network(reac, prod, rates), init, run_ids=np.arange(runs) * 32 + 11, seed=97 + net_i,
+                t_end=0.6, snap_times=snaps, pad_pow2=2)
+    p0 = np.zeros(len(st))
+    p0[index[init]] = 1.0
+    for s, t in enumerate(snaps):
+        p = me.distribution(Q, p0, t)
+        obs = np.zeros(len(st))
+        for c in r["snap_counts"][s]:
+            obs[index[tuple(int(x) for x in c)]] += 1
+        exp = p * runs
+        big = exp >= 5
+        o = np.append(obs[big], obs[~big].sum())
+        e = np.append(exp[big], exp[~big].sum())
+        if e[-1] < 5:
+            o, e = o[:-1], e[:-1]
+            e *= o.sum() / e.sum()
+        assert stats.power_divergence(o, e, lambda_="log-likelihood")[1] > 1e-4, (t, net_i)
+
+
+def test_state_following_bound_isomerisation(orc):
+    """A <-> B (rates 1 and 0.4) under the state-following bound: the binomial closed form."""
+    a, b = 1.0, 0.4
+    nA0, nB0 = 14, 6
+    net = orc.Network([[1, 0], [0, 1]], [[0, 1], [1, 0]], [a, b])
+    snaps = [0.3, 1.2]
+    runs = 20_000
+    r = orc.run(net, (nA0, nB0), run_ids=np.arange(runs) * 32 + 30, seed=62, t_end=1.2, snap_times=snaps,
+                pad_pow2=2)
+    for s, t in enumerate(snaps):
+        e = math.exp(-(a + b) * t)
+        p_aa, p_ba = (b + a * e) / (a + b), b * (1 - e) / (a + b)
+        pmf = np.convolve(stats.binom.pmf(np.arange(nA0 + 1), nA0, p_aa), stats.binom.pmf(np.arange(nB0 + 1), nB0, p_ba))
+        obs = np.bincount(r["snap_counts"][s][:, 0], minlength=nA0 + nB0 + 1).astype(float)
+        exp = pmf * runs
+        big = exp >= 5
+        o, ex = np.append(obs[big], obs[~big].sum()), np.append(exp[big], exp[~big].sum())
+        assert stats.power_divergence(o, ex, lambda_="log-likelihood")[1] > 1e-4, t
+
+
+def test_state_following_bound_group_consistency(orc):
+    """A run's result does not depend on which runs of its group are asked for, and a partial
+    last group holds only its own lanes."""
+    a = orc.run(orc.frank(), (40, 40, 80), 70, seed=5, t_end=3.0, pad_pow2=2)
+    ids = np.array([69, 3, 64, 31, 0])
+    b = orc.run(orc.frank(), (40, 40, 80), run_ids=ids, seed=5, t_end=3.0, pad_pow2=2, ensemble_runs=70)
+    for k in ("final_counts", "t_abs", "steps", "reactions"):
+        assert np.array_equal(a[k][ids], b[k]), k
+    full = orc.run(orc.frank(), (40, 40, 80), 96, seed=5, t_end=3.0, pad_pow2=2)
+    assert np.array_equal(full["final_counts"][:64], a["final_counts"][:64])
+    assert np.all(a["final_counts"].sum(1) == 160) and np.all(a["redraws"] == 0)
+    with pytest.raises(RuntimeError):
+        orc.run(orc.frank(), (40, 40, 80), run_ids=[70], seed=5, pad_pow2=2, ensemble_runs=70)
