@@ -72,11 +72,12 @@ def general_ops_per_group_step(K: int, b: int, products: bool) -> int:
     return 3 * per_reaction + 3 * (2 * b + 3 * 3) + 20 * ((K + 2 + 3) // 4)
 
 
-def algorithmic_ops_per_group_step(K: int, b: int, padded: bool = False) -> int:
+def algorithmic_ops_per_group_step(K: int, b: int, pad: int = 0) -> int:
     """Word operations one group step must do (27K + 6b logic plus 20 LOP3 per Philox call
     for the ceil((K+2)/4) calls of n and tau); a bound padded to 2^K has no rejection test
-    (K fewer)."""
-    return (26 if padded else 27) * K + 6 * b + 20 * ((K + 2 + 3) // 4)
+    (K fewer); the state-following bound (pad 2) adds the reduction of S_R's planes over the
+    live lanes and the mask of n's planes above it (2K more)."""
+    return {0: 27, 1: 26, 2: 28}[int(pad)] * K + 6 * b + 20 * ((K + 2 + 3) // 4)
 
 
 def bit_length(v: int) -> int:
@@ -138,7 +139,7 @@ def cpu_baseline(sample_runs: int, threads: int):
     oracle.build()
     t0 = time.perf_counter()
     r = oracle.run(oracle.frank(), INIT, sample_runs, seed=SEED, t_end=T_END, snap_times=SNAPS,
-                   threads=threads, pad_pow2=bool(PAD))
+                   threads=threads, pad_pow2=PAD, ensemble_runs=0)
     dt = time.perf_counter() - t0
     reactions = int(r["reactions"].sum())
     return {"value": reactions / dt, "unit": "lane-reactions/s", "cores": threads, "kind": "oracle",
@@ -157,12 +158,12 @@ def run_reference(args, rank, world):
     oracle.build()
     for _ in range(args.warmup):
         oracle.run(oracle.frank(), INIT, 64, seed=SEED, t_end=T_END, snap_times=SNAPS, threads=threads,
-                   pad_pow2=bool(PAD))
+                   pad_pow2=PAD, ensemble_runs=0)
     total_react, total_abs, total_t = 0, 0, 0.0
     for k in range(args.steps):
         t0 = time.perf_counter()
         r = oracle.run(oracle.frank(), INIT, per_step, first_run=k * per_step, seed=SEED, t_end=T_END,
-                       snap_times=SNAPS, threads=threads, pad_pow2=bool(PAD))
+                       snap_times=SNAPS, threads=threads, pad_pow2=PAD, ensemble_runs=0)
         total_t += time.perf_counter() - t0
         total_react += int(r["reactions"].sum())
         total_abs += int((r["outcome"] >= 0).sum())
@@ -214,7 +215,8 @@ def workload_config(world):
     return workload_config_single(world)
 
 
-BOUND_NAMES = ["lambda_int = N(N-1)/2, rejected draws redrawn", "lambda_int padded to 2^K with null events"]
+BOUND_NAMES = ["lambda_int = N(N-1)/2, rejected draws redrawn", "lambda_int padded to 2^K with null events",
+               "2^p per step, p = bit length of the largest S_R over the group's live runs"]
 
 
 def workload_config_single(world):
@@ -249,9 +251,10 @@ def main():
                     help="skip ssa_tune (by default it times every launch configuration on the "
                          "workload during warm-up and keeps the fastest; c3 keeps the per-bucket rule)")
     ap.add_argument("--precision", type=int, default=0)
-    ap.add_argument("--pad", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--pad", type=int, default=1, choices=[0, 1, 2],
                     help="1: pad the uniformisation bound to 2^K with null events, so that no draw of n "
-                         "is rejected (the same process, sampled through a different draw)")
+                         "is rejected (the same process, sampled through a different draw); 2: a "
+                         "power-of-two bound that follows each group's state")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 2],
                     help="0: Frank's kernels; 2: the general-network kernel on the same workload")
     ap.add_argument("--runs", type=int, default=0,
@@ -355,7 +358,7 @@ def main():
     # number of planes K, so its per-unit count is not a single figure and is not reported)
     K, b = bit_length(N_TOT * (N_TOT - 1) // 2), bit_length(N_TOT)
     ops_unit = (general_ops_per_group_step(K, b, bool(layout_used & 8)) if ENGINE == 2
-                else algorithmic_ops_per_group_step(K, b, bool(PAD)))
+                else algorithmic_ops_per_group_step(K, b, PAD))
     gs_per_launch = group_steps / world / args.steps
     achieved = ops_unit * gs_per_launch / (statistics.mean(kernel_ms) / 1e3) / 1e9
     peak_ops_per_clk = float(os.environ.get("BITSSA_ALU_OPS_PER_CLK_PER_SM", "64"))

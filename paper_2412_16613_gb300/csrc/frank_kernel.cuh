@@ -143,17 +143,52 @@ __device__ __forceinline__ bool clock_advance(const Clock<true>& c, Clock<true>&
   return nx.E < c.th_E || (nx.E == c.th_E && nx.M < *c.th_M);
 }
 
+// A step at the state-following bound's rate Lambda 2^-j (j = K - p) multiplies exp(-Lambda t)
+// by u^(2^j): v is normalised to a 64-bit mantissa and squared j times, each square truncated
+// to its top 64 bits (relative error below 2^-63 a square, doubling with each further square:
+// 2^(j-62) in -ln of the factor, that is 2^-62 of the step's mean waiting time 2^j / Lambda).
+__device__ __forceinline__ bool clock_advance(const Clock<true>& c, Clock<true>& nx, uint32_t wk, uint32_t wk1,
+                                              const Ensemble& e, int precision, int j) {
+  if (j == 0) return clock_advance(c, nx, wk, wk1, e, precision);
+  const unsigned long long v = (((unsigned long long)wk1 << 21) | (wk >> 11)) + 1ull;
+  const int lz0 = __clzll((long long)v);
+  unsigned long long m = v << lz0;  // u = m 2^(f - 63)
+  long long f = 10 - lz0;
+  for (int k = 0; k < j; ++k) {
+    const unsigned long long hi = __umul64hi(m, m), lo = m * m;
+    if (hi >> 63) {
+      m = hi;
+      f = 2 * f + 1;
+    } else {
+      m = (hi << 1) | (lo >> 63);
+      f = 2 * f;
+    }
+  }
+  const unsigned long long hi = __umul64hi(c.M, m), lo = c.M * m;
+  nx = c;
+  if (hi >> 63) {
+    nx.M = hi;
+    nx.E = c.E + f + 1;
+  } else {
+    nx.M = (hi << 1) | (lo >> 63);
+    nx.E = c.E + f;
+  }
+  return nx.E < c.th_E || (nx.E == c.th_E && nx.M < *c.th_M);
+}
+
+// The other clocks at rate Lambda 2^-j: the waiting time at rate Lambda times 2^j, which is
+// exactly the waiting time at the lower rate (a power-of-two scaling rounds the same way).
 __device__ __forceinline__ bool clock_advance(const Clock<false>& c, Clock<false>& nx, uint32_t wk, uint32_t wk1,
-                                              const Ensemble& e, int precision) {
+                                              const Ensemble& e, int precision, int j = 0) {
   nx = c;
   if (precision == kP64LogSum) {
     const unsigned long long x = ((unsigned long long)wk1 << 21) | (wk >> 11);
     const double u = (double)(x + 1ull) * 0x1p-53;
-    nx.t = c.t + (-log(u) / e.lambda);
+    nx.t = c.t + (-log(u) / e.lambda) * (double)(1ull << j);
     return nx.t > c.th_t;
   }
   const float u = (float)((wk1 >> 8) + 1u) * 0x1p-24f;  // the top 24 of the 53 bits
-  const float tau = -logf(u) * e.inv_lambda_f;
+  const float tau = -logf(u) * e.inv_lambda_f * (float)(1u << j);
   if (precision == kP32Kahan) {
     const float y = tau - c.c_f;
     const float sum = c.t_f + y;
@@ -491,6 +526,17 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   uint32_t n[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) n[i] = w[i];
+  // the state-following bound: 2^p, p the bit length of the largest S_3 over the live lanes,
+  // and n its low p planes
+  int j = 0;
+  if (e.adapt) {
+    int bits = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) bits = (s.S3[i] & s.live) ? i + 1 : bits;
+#pragma unroll
+    for (int i = 0; i < K; ++i) n[i] = i < bits ? n[i] : 0u;
+    j = K - bits;
+  }
   // the rejection test and the three comparators are independent borrow chains: run them
   // together, and redo the comparators only in the rare step where a lane redraws
   const uint32_t need = rejected_lanes<K>(n, e, s.live);
@@ -510,7 +556,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
 
   // (2) the clock: the candidate time of this step's event, snapshots, t_end
   Clock<PROD> nx;
-  bool crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision);
+  bool crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision, j);
   while (crossed) {
     if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
       s.done = true;

@@ -52,6 +52,7 @@ Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], in
   const unsigned long long lam = pad_pow2 ? (1ull << e.K) : z;
   e.lambda_int = (unsigned int)lam;
   e.reject = pad_pow2 ? 0 : 1;
+  e.adapt = pad_pow2 == 2 ? 1 : 0;
   set_precheck(e);
   const double kmax = std::max(k[0], std::max(k[1], k[2]));
   e.lambda = kmax * (double)lam;
@@ -391,7 +392,10 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.shared_n != 0 && o.shared_n != 1) return (*why = "shared_n must be 0 or 1", SSA_EINVAL);
   if (o.shared_n && o.engine == SSA_ENGINE_THREAD_PER_RUN)
     return (*why = "shared_n is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
-  if (o.pad_pow2 != 0 && o.pad_pow2 != 1) return (*why = "pad_pow2 must be 0 or 1", SSA_EINVAL);
+  if (o.pad_pow2 < 0 || o.pad_pow2 > 2) return (*why = "pad_pow2 must be 0, 1 or 2", SSA_EINVAL);
+  if (o.pad_pow2 == 2 && (o.engine == SSA_ENGINE_GENERAL || o.layout == SSA_LAYOUT_WARPS || o.shared_n))
+    return (*why = "the state-following bound (pad_pow2 = 2) runs Frank's model on one thread per group",
+            SSA_EUNSUPPORTED);
   if (o.recompute < 0 || o.recompute > 2) return (*why = "recompute must be 0, 1 or 2", SSA_EINVAL);
   if (o.pad_pow2 && o.engine == SSA_ENGINE_THREAD_PER_RUN)
     return (*why = "pad_pow2 is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
@@ -488,6 +492,8 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
     return fail(nullptr, SSA_EUNSUPPORTED, "shared_n runs Frank's model on the three-warp layout");
   if (general && o.layout == SSA_LAYOUT_WARPS)
     return fail(nullptr, SSA_EUNSUPPORTED, "a general network runs one thread per group");
+  if (general && o.pad_pow2 == 2)
+    return fail(nullptr, SSA_EUNSUPPORTED, "the state-following bound (pad_pow2 = 2) runs Frank's model only");
   ssa_ctx* c = new ssa_ctx();
   c->opt = o;
   c->S = S;
@@ -588,6 +594,7 @@ bool use_warps_layout(const ssa_options& o, long long groups, int sm_count) {
 // rule above.
 bool ctx_warps(const ssa_ctx* c, long long groups) {
   if (c->general) return false;      // the general kernel has one layout
+  if (c->opt.pad_pow2 == 2) return false;  // the state-following bound is built into one thread only
   if (c->opt.shared_n) return true;  // Frank's kernels: the shared draw is built into three warps only
   if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_THREAD) return false;
   if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_WARPS) return true;
@@ -1131,8 +1138,10 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
                                      {SSA_LAYOUT_THREAD, 128, 0}, {SSA_LAYOUT_THREAD, 32, 1},
                                      {SSA_LAYOUT_THREAD, 64, 1}, {SSA_LAYOUT_THREAD, 128, 1}};
   std::vector<Candidate> cands;
-  if (!c->general) cands.assign(frank_cands, frank_cands + 5);
-  else
+  if (!c->general) {
+    for (const Candidate& f : frank_cands)
+      if (c->opt.pad_pow2 != 2 || f.layout == SSA_LAYOUT_THREAD) cands.push_back(f);
+  } else
     for (const Candidate& g : general_cands)
       if (c->opt.recompute == 0 || g.products == (c->opt.recompute == 1 ? 1 : 0)) cands.push_back(g);
   DeviceGuard guard(c->device);

@@ -84,7 +84,12 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
     (dict(reac=F_R, prod=F_P, shared_n=2), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, shared_n=1, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, shared_n=1, layout=pkg.SSA_LAYOUT_THREAD), pkg.SSA_EUNSUPPORTED),
-    (dict(reac=F_R, prod=F_P, pad_pow2=2), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, pad_pow2=3), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, pad_pow2=2, layout=pkg.SSA_LAYOUT_WARPS), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, pad_pow2=2, shared_n=1), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, pad_pow2=2, engine=pkg.SSA_ENGINE_GENERAL), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, pad_pow2=2, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=[[1, 1], [1, 1]], prod=[[2, 0], [0, 2]], N0=(3, 3), pad_pow2=2), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, pad_pow2=-1), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, pad_pow2=1, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
     (dict(reac=[[1] + [0] * 8], prod=[[0, 1] + [0] * 7]), pkg.SSA_EUNSUPPORTED),    # 9 species

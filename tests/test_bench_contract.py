@@ -26,7 +26,8 @@ def test_bench_helpers():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.algorithmic_ops_per_group_step(19, 11) == 27 * 19 + 6 * 11 + 20 * 6 == 699
-    assert bench.algorithmic_ops_per_group_step(19, 11, padded=True) == 680
+    assert bench.algorithmic_ops_per_group_step(19, 11, pad=1) == 680
+    assert bench.algorithmic_ops_per_group_step(19, 11, pad=2) == 718
     assert bench.general_ops_per_group_step(19, 11, products=False) == 954
     assert bench.general_ops_per_group_step(19, 11, products=True) == 1473
     assert bench.layout_name(1) == "thread" and bench.layout_name(3) == "thread+warps"
