@@ -50,9 +50,9 @@ SMS = 152
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) of one launch of the one-thread bit-sliced kernel on the default
 # workload: the metrics-only capture of the quarter-size case in
-# profiles/frank_kernel_n1024_2p20runs_launches.md (129 024 B), scaled x4 by the number of runs.
+# profiles/frank_kernel_n1024_2p20runs_launches.md (562 688 B), scaled x4 by the number of runs.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 4 * 129_024
+TRAFFIC_BYTES_PER_LAUNCH = 4 * 562_688
 
 
 def layout_name(bits: int) -> str:

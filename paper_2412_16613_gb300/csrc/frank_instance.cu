@@ -14,32 +14,33 @@
 
 namespace bitssa {
 
-// variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64)
-int BITSSA_CAT(frank_launch_k, BITSSA_K)(const FrankLaunch& p, int grid, int block, int smem,
-                                          void* stream) {
-  const cudaStream_t st = (cudaStream_t)stream;
-  const bool prod = p.precision == kP64;
-  if (p.ens_table) {
-    if (prod) frank_kernel<BITSSA_K, true, true><<<grid, block, smem, st>>>(p);
-    else frank_kernel<BITSSA_K, true, false><<<grid, block, smem, st>>>(p);
-  } else {
-    if (prod) frank_kernel<BITSSA_K, false, true><<<grid, block, smem, st>>>(p);
-    else frank_kernel<BITSSA_K, false, false><<<grid, block, smem, st>>>(p);
-  }
-  return (int)cudaGetLastError();
-}
-
+// variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64), bit 2 = the
+// state-following bound (FrankLaunch::adapt)
 namespace {
 template <typename F>
 int with_kernel(int variant, F f) {
-  switch (variant & 3) {
-    case 0: return f(frank_kernel<BITSSA_K, false, false>);
-    case 1: return f(frank_kernel<BITSSA_K, true, false>);
-    case 2: return f(frank_kernel<BITSSA_K, false, true>);
-    default: return f(frank_kernel<BITSSA_K, true, true>);
+  switch (variant & 7) {
+    case 0: return f(frank_kernel<BITSSA_K, false, false, false>);
+    case 1: return f(frank_kernel<BITSSA_K, true, false, false>);
+    case 2: return f(frank_kernel<BITSSA_K, false, true, false>);
+    case 3: return f(frank_kernel<BITSSA_K, true, true, false>);
+    case 4: return f(frank_kernel<BITSSA_K, false, false, true>);
+    case 5: return f(frank_kernel<BITSSA_K, true, false, true>);
+    case 6: return f(frank_kernel<BITSSA_K, false, true, true>);
+    default: return f(frank_kernel<BITSSA_K, true, true, true>);
   }
 }
 }  // namespace
+
+int BITSSA_CAT(frank_launch_k, BITSSA_K)(const FrankLaunch& p, int grid, int block, int smem,
+                                          void* stream) {
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int variant = (p.ens_table ? 1 : 0) | (p.precision == kP64 ? 2 : 0) | (p.adapt ? 4 : 0);
+  return with_kernel(variant, [&](auto kern) {
+    kern<<<grid, block, smem, st>>>(p);
+    return (int)cudaGetLastError();
+  });
+}
 
 // Occupancy at `smem` bytes of dynamic shared memory; lifts the kernel's dynamic shared-memory
 // limit first when the request exceeds the default 48 KB (the staging rows of a snapshot dump).

@@ -506,7 +506,7 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K, P
 
 // One group step (see the file header).  Never leaves the caller's loop: a group that
 // stops sets s.done.
-template <int K, bool PROD>
+template <int K, bool PROD, bool ADAPT>
 __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e,
                                            const Threshold* thr, unsigned int* s_hist, unsigned int& errors) {
   using Sh = FrankShape<K>;
@@ -529,7 +529,7 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   // the state-following bound: 2^p, p the bit length of the largest S_3 over the live lanes,
   // and n its low p planes
   int j = 0;
-  if (e.adapt) {
+  if constexpr (ADAPT) {
     int bits = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) bits = (s.S3[i] & s.live) ? i + 1 : bits;
@@ -556,7 +556,9 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
 
   // (2) the clock: the candidate time of this step's event, snapshots, t_end
   Clock<PROD> nx;
-  bool crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision, j);
+  bool crossed;
+  if constexpr (ADAPT) crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision, j);
+  else crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision);
   while (crossed) {
     if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
       s.done = true;
@@ -690,7 +692,7 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
 // snapshots, absorptions, a new group) cost one pass each instead of leaving the warp
 // split for the rest of the run.  Single-ensemble launches read the ensemble from the
 // kernel parameters (warp-uniform); batches from a table.
-template <int K, bool BATCH, bool PROD>
+template <int K, bool BATCH, bool PROD, bool ADAPT>
 __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ FrankLaunch p) {
   unsigned int* const s_hist_mem = frank_dyn_smem;
   const bool smem_hist = !BATCH && p.n_snap > 0;
@@ -722,7 +724,7 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
     if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
     if (active) {
       const Ensemble& e = BATCH ? p.ens_table[s.ens] : p.ens;
-      if (!s.done) group_step<K, PROD>(p, s, e, thr, s_hist, errors);
+      if (!s.done) group_step<K, PROD, ADAPT>(p, s, e, thr, s_hist, errors);
       if (s.done) {
         group_finish<K, PROD>(p, s, e);
         active = false;

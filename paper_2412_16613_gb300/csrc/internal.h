@@ -97,8 +97,6 @@ struct Ensemble {
   int shared_n;              // 1: every lane of a group uses lane 0's n
   int reject;                // 1: lambda_int < 2^K, draws of n at or above it are redrawn;
                              // 0: the bound is padded to 2^K and every draw is accepted
-  int adapt;                 // 1: each step's bound is 2^p, p the bit length of the largest S_R
-                             // over the group's live lanes (lambda_int = 2^K is its ceiling)
   unsigned int top_ones;     // planes of the leading run of ones of lambda_int (bit i = plane i):
                              // n >= lambda_int needs all of them set (0: no pre-check)
   unsigned int top_mask[32]; // per plane: 0 on the run, ~0 elsewhere, so that the AND over planes
@@ -169,6 +167,9 @@ struct FrankLaunch {
   unsigned long long* counters;   // [kCounters]
   unsigned int* status;           // error flags
   unsigned long long* queue;      // work-item counter of this launch
+  int adapt;                      // one-thread Frank kernel: 1 runs the instantiation with the
+                                  // state-following bound (each step's bound 2^p, p the bit length
+                                  // of the largest S_R over the group's live lanes; 2^K its ceiling)
   int stage_offset;               // one-thread Frank kernel with a snapshot dump: the word of dynamic
                                   // shared memory where the per-thread staging rows start; -1: none
   Network net;                    // general kernel only

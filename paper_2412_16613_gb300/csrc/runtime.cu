@@ -52,7 +52,6 @@ Ensemble make_ensemble(long long n_tot, const int init[3], const double k[3], in
   const unsigned long long lam = pad_pow2 ? (1ull << e.K) : z;
   e.lambda_int = (unsigned int)lam;
   e.reject = pad_pow2 ? 0 : 1;
-  e.adapt = pad_pow2 == 2 ? 1 : 0;
   set_precheck(e);
   const double kmax = std::max(k[0], std::max(k[1], k[2]));
   e.lambda = kmax * (double)lam;
@@ -686,6 +685,7 @@ int launch_runs(ssa_ctx* c) {
   fl.ens_absorbed = c->d_ens_abs;
   fl.snap_counts = c->opt.keep_snap_counts ? c->d_snap : nullptr;
   fl.stage_offset = -1;
+  fl.adapt = c->opt.pad_pow2 == 2 ? 1 : 0;
   fl.n_runs_total = c->n_runs_total;
   fl.counters = c->d_counters;
   fl.status = c->d_status;
@@ -729,6 +729,7 @@ int launch_runs(ssa_ctx* c) {
   }
 
   const int clock_variant = c->opt.precision == SSA_P64 ? 2 : 0;
+  const int adapt_variant = fl.adapt ? 4 : 0;  // the one-thread Frank kernel's instantiation
   if (c->general) return launch_general(c, fl, block, clock_variant);
   if (!c->batch) {
     const Ensemble& en = c->ens[0];
@@ -759,7 +760,7 @@ int launch_runs(ssa_ctx* c) {
       fl.stage_offset = ((smem / (int)sizeof(unsigned int)) + 3) & ~3;
       tsmem = (fl.stage_offset + block * kStageStride) * (int)sizeof(unsigned int);
     }
-    if (frank_max_active_blocks(K, clock_variant, block, tsmem, &occ) != 0 || occ < 1)
+    if (frank_max_active_blocks(K, clock_variant | adapt_variant, block, tsmem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (groups + block - 1) / block;
@@ -797,7 +798,7 @@ int launch_runs(ssa_ctx* c) {
       const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
       b.grid = (int)std::max(1ll, std::min((groups + 31) / 32, (long long)c->sm_count * bpsm));
     } else {
-      if (frank_max_active_blocks(b.K, clock_variant | 1, block, 0, &occ) != 0 || occ < 1)
+      if (frank_max_active_blocks(b.K, clock_variant | adapt_variant | 1, block, 0, &occ) != 0 || occ < 1)
         return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
       b.block = block;
       const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
