@@ -22,6 +22,16 @@ def test_reference_arm_prints_the_contract_line():
     assert line["config"]["workload"].startswith("frank_N1024") and "padded" in line["config"]["bound"]
 
 
+def test_reference_arm_with_the_state_following_bound():
+    """--pad 2: the oracle steps whole groups; the line names the bound."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--pad", "2", "--steps", "1",
+                        "--warmup", "1", "--ref-runs", "64"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["bound"].startswith("2^p per step")
+
+
 def test_bench_helpers():
     sys.path.insert(0, ROOT)
     import bench
