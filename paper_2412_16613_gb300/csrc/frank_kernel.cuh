@@ -20,9 +20,12 @@
 // One group step (Sec. 3, steps 1-7, with the draw of step 5 done by Sec. 4's steps a-d):
 //   1. Philox words of attempt 0: planes of the uniform integer n and the
 //      group's waiting-time bits; lanes with n >= lambda_int redraw from the
-//      next attempt.
-//   2. Clock: tau ~ Exp(Lambda) (Eq. equation-tau).  Snapshots whose time is
-//      passed record the state before the event; passing t_end stops the group.
+//      next attempt.  With the state-following bound (template flag ADAPT) the
+//      step's bound is 2^p, p the highest plane set in S3 over the live lanes,
+//      and n keeps its low p planes: nothing is redrawn.
+//   2. Clock: tau ~ Exp(Lambda) (Eq. equation-tau), Lambda = k_max 2^p under
+//      ADAPT.  Snapshots whose time is passed record the state before the event;
+//      passing t_end stops the group.
 //   3. Comparators lt_r = [n < S_r] (borrow chains) and changer words
 //      xi_r = lt_r & ~lt_{r-1} (Eq. equation-changer: the CDF walk of Fig. 2
 //      done for all lanes at once); lanes with n >= S_3 fire a ghost reaction.
