@@ -164,3 +164,14 @@ def test_product_path_has_no_cpu_fallback():
         if name.endswith(".py"):
             text = open(os.path.join(src_dir, name)).read()
             assert "import oracle" not in text and "from oracle" not in text, name
+
+
+@pytest.mark.parametrize("kw", [dict(pad_pow2=2, layout=pkg.SSA_LAYOUT_WARPS), dict(pad_pow2=2, shared_n=1),
+                                dict(pad_pow2=2, engine=pkg.SSA_ENGINE_GENERAL), dict(pad_pow2=3)])
+def test_batch_validates_the_bound_option(lib, kw):
+    """A batch goes through the same option checks, before any CUDA call."""
+    init = np.array([[16, 16, 32], [25, 25, 50]])
+    with pytest.raises(pkg.SSAError) as ei:
+        pkg.ssa_create_batch(F_R, F_P, init, np.ones((2, 3)), np.array([64, 32]), np.array([1, 2], dtype=np.uint64),
+                             pkg.ssa_default_options(**kw))
+    assert ei.value.status == (pkg.SSA_EINVAL if kw.get("pad_pow2") == 3 else pkg.SSA_EUNSUPPORTED)
