@@ -138,7 +138,10 @@ typedef struct {
                                 so this is uniformisation at a rate that changes with it: each run
                                 still jumps by reaction r at rate k_r h_r and is an exact sample path.
                                 Fewer null steps once a group's runs near absorption: at N = 10 000
-                                a group takes about 40% of the padded bound's steps.  Frank's model
+                                a group takes about 40% of the padded bound's steps.  A run's draws
+                                then depend on the other runs its group holds in this context, so
+                                contexts split by first_run reproduce a single one when every part
+                                but the last holds whole groups.  Frank's model
                                 on one thread per group only
                                 (SSA_LAYOUT_AUTO takes it; SSA_LAYOUT_WARPS, shared_n or a general
                                 network give SSA_EUNSUPPORTED). */

@@ -5,7 +5,8 @@ so a rank that holds runs [first_run, first_run + n_runs) (first_run a multiple 
 32, passed as ssa_options.first_run) produces exactly the runs a single context
 would.  The only exchange is the final sum of the per-snapshot histograms and run
 counters (and the maximum of the longest-group counter); there is no collective on
-the data path.
+the data path.  Under the state-following bound (pad_pow2 = 2) a run's draws also
+depend on the other runs of its group, and whole-group shards keep those together.
 """
 from __future__ import annotations
 

@@ -1,6 +1,7 @@
 """The multi-rank host path on CPU: two gloo ranks each run their shard of one ensemble
 (the oracle stands in for a GPU context, since shards are defined by the run indices
-alone) and combine histograms and counters; the result must equal one process."""
+alone) and combine histograms and counters; the result must equal one process, also under
+the state-following bound, where a run depends on the other runs of its group."""
 import os
 import socket
 
@@ -22,9 +23,10 @@ def _free_port():
     return port
 
 
-def _oracle_shard(first, n):
+def _oracle_shard(first, n, pad=0):
     import oracle
-    r = oracle.run(oracle.frank(), INIT, n, first_run=first, seed=5, t_end=1.0, snap_times=SNAPS, threads=2)
+    r = oracle.run(oracle.frank(), INIT, n, first_run=first, seed=5, t_end=1.0, snap_times=SNAPS, threads=2,
+                   pad_pow2=pad, ensemble_runs=N_RUNS if pad == 2 else None)
     hist = oracle.ee_histogram(r["snap_counts"]) if n else np.zeros((len(SNAPS), 65), dtype=np.uint64)
     counters = np.zeros(10, dtype=np.uint64)
     counters[1] = r["steps"].sum()
@@ -35,12 +37,12 @@ def _oracle_shard(first, n):
     return hist, counters, r
 
 
-def _worker(rank, world, port, out_dir):
+def _worker(rank, world, port, out_dir, pad):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     first, n = sharding.shard(N_RUNS, rank, world)
-    hist, counters, r = _oracle_shard(first, n)
+    hist, counters, r = _oracle_shard(first, n, pad)
     hist, counters = sharding.combine(hist, counters, dist)
     np.savez(os.path.join(out_dir, f"rank{rank}.npz"), hist=hist, counters=counters,
              final=r["final_counts"], first=first, n=n)
@@ -60,13 +62,14 @@ def test_shards_cover_the_runs_in_whole_groups():
     assert sharding.weak_shard(1 << 20, 3) == (3 << 20, 1 << 20)
 
 
-def test_two_gloo_ranks_equal_one_process(tmp_path):
+@pytest.mark.parametrize("pad", [0, 2])
+def test_two_gloo_ranks_equal_one_process(tmp_path, pad):
     import oracle
     import torch.multiprocessing as mp
     oracle.build()
     port = _free_port()
-    mp.start_processes(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
-    whole_hist, whole_counters, whole = _oracle_shard(0, N_RUNS)
+    mp.start_processes(_worker, args=(2, port, str(tmp_path), pad), nprocs=2, join=True, start_method="spawn")
+    whole_hist, whole_counters, whole = _oracle_shard(0, N_RUNS, pad)
     parts = [np.load(os.path.join(tmp_path, f"rank{r}.npz")) for r in range(2)]
     whole_counters[9] = 3  # rank 0 ran layout bit 0, rank 1 layout bit 1
     for p in parts:
