@@ -7,7 +7,8 @@ gcc and marshals numpy arrays through ctypes.
 
 The oracle is a plain serial Gillespie simulation with integer counts
 (Sec. 3 of the paper, steps 1-7), driven by the counter-based stream described
-in ``oracle.h`` so that one run can be recomputed on its own.
+in ``oracle.h`` so that one run can be recomputed on its own (with its whole group
+under the state-following bound, ``pad_pow2=2``).
 """
 from __future__ import annotations
 

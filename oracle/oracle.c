@@ -5,7 +5,9 @@
  * benchmark's CPU-baseline leg; never by the product library.
  *
  * Plain serial Gillespie, one run at a time, integer counts, propensities
- * recomputed from their definition at every step.  The random stream and the
+ * recomputed from their definition at every step.  Under the state-following
+ * bound (pad_pow2 = 2) the 32 runs of a group are stepped together, since the
+ * bound of each step depends on all of them.  The random stream and the
  * integer reaction-choice rule are described in oracle.h.  Compile with
  * -ffp-contract=off.
  */
