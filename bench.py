@@ -46,13 +46,39 @@ T_END = 50.0
 N_SNAP = 10
 SNAPS = [T_END * 10.0 ** (4.0 * (s - (N_SNAP - 1)) / (N_SNAP - 1)) for s in range(N_SNAP)]
 L2_BYTES = 129 * 2**20
-SMS = 152
-MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) of one launch of the one-thread bit-sliced kernel on the default
-# workload: the metrics-only capture of the quarter-size case in
-# profiles/frank_kernel_n1024_2p20runs_launches.md (562 688 B), scaled x4 by the number of runs.
-# Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 4 * 562_688
+# workload, from one ncu capture, keyed by a fingerprint of the kernel's sources (below): a
+# kernel changed since its capture has no entry and reports null.
+TRAFFIC_BYTES_PER_LAUNCH = {}
+KERNEL_SOURCES = ("frank_kernel.cuh", "bitslice.cuh", "philox.cuh", "internal.h", "frank_instance.cu")
+
+
+def kernel_fingerprint() -> str:
+    """sha256 (16 hex digits) of the one-thread kernel's source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2412_16613_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def device_sm_count_and_max_mhz(index: int):
+    """SM count from the device properties; the maximum SM clock from nvidia-smi (MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(index).multi_processor_count
+    mhz, basis = None, "nvidia-smi clocks.max.sm"
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=30).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except Exception:
+        khz = getattr(torch.cuda.get_device_properties(index), "clock_rate", None)
+        if khz:
+            mhz, basis = khz / 1e3, "device property clock_rate"
+    if not mhz:
+        mhz, basis = 2070.0, "not readable: GB300's listed maximum"
+    return sms, mhz, basis
 
 
 def layout_name(bits: int) -> str:
@@ -244,6 +270,9 @@ def main():
     ap.add_argument("--ref-runs", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=8192)
     ap.add_argument("--no-baselines", action="store_true", help="skip the K7 and CPU legs")
+    ap.add_argument("--c4-steps", type=int, default=3,
+                    help="timed runs of the N_tot = 10 000, 2^22-run workload per bound after the main "
+                         "measurement (0: skip)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--layout", type=int, default=0,
                     help="0 auto, 1 one thread per group of 32 runs, 2 three warps per 32 groups")
@@ -311,6 +340,24 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    def time_runs(ctx_, steps, snaps=None):
+        """One warm-up run, then `steps` runs each timed with CUDA events after an L2 flush:
+        mean ms per run, lane-reactions/s, the counters of the last run."""
+        snaps = SNAPS if snaps is None else snaps
+        pkg.ssa_run(ctx_, T_END, snaps)
+        ms, react = [], 0
+        for k in range(steps):
+            flush.fill_(k + 7)
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            pkg.ssa_run(ctx_, T_END, snaps)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a_.elapsed_time(b_))
+            cnt = pkg.ssa_fetch(ctx_, pkg.SSA_FIELD_COUNTERS)
+            react += int(cnt[2])
+        return statistics.mean(ms), react / (sum(ms) / 1e3), cnt
+
     tuned = None
     if not args.no_tune and WORKLOAD != "c3" and args.layout == 0 and args.block == 0:
         tuned = pkg.ssa_tune(ctx, T_END, SNAPS, probe_steps=0)
@@ -356,27 +403,38 @@ def main():
 
     # ---- roofline of the bit-sliced kernel (one launch per step; a batch runs one launch per
     # number of planes K, so its per-unit count is not a single figure and is not reported)
-    K, b = bit_length(N_TOT * (N_TOT - 1) // 2), bit_length(N_TOT)
-    ops_unit = (general_ops_per_group_step(K, b, bool(layout_used & 8)) if ENGINE == 2
-                else algorithmic_ops_per_group_step(K, b, PAD))
-    gs_per_launch = group_steps / world / args.steps
-    achieved = ops_unit * gs_per_launch / (statistics.mean(kernel_ms) / 1e3) / 1e9
-    peak_ops_per_clk = float(os.environ.get("BITSSA_ALU_OPS_PER_CLK_PER_SM", "64"))
-    peak = SMS * peak_ops_per_clk * MAX_SM_MHZ * 1e6 / 1e9
+    sms, max_mhz, mhz_basis = device_sm_count_and_max_mhz(local)
     micro = None
     try:
         micro = pkg.bitssa_bench_alu(local, 4000)[0] / 1e9
     except Exception:
         pass
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s",
-                "frac": achieved / peak,
-                "traffic": TRAFFIC_BYTES_PER_LAUNCH if (WORKLOAD == "c2" and RUNS_PER_GPU == 1 << 20
-                                                        and PRECISION == 0 and PAD == 1 and ENGINE == 0
-                                                        and layout_used == 1)
-                else None,
-                "ops_per_group_step": ops_unit, "group_steps_per_launch": gs_per_launch,
-                "peak_basis": f"{SMS} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {MAX_SM_MHZ:g} MHz",
+
+    def roofline_of(n_tot, pad, gs_per_launch, launch_ms, engine=ENGINE, layout_bits=1):
+        K, b = bit_length(n_tot * (n_tot - 1) // 2), bit_length(n_tot)
+        # the per-unit figure of the method (27K + 6b logic, 20 LOP3 per Philox call), whatever the
+        # bound; the count of the mode that ran is reported beside it
+        ops_unit = (general_ops_per_group_step(K, b, bool(layout_bits & 8)) if engine == 2
+                    else algorithmic_ops_per_group_step(K, b, 0))
+        ops_mode = ops_unit if engine == 2 else algorithmic_ops_per_group_step(K, b, pad)
+        achieved = ops_unit * gs_per_launch / (launch_ms / 1e3) / 1e9
+        peak_ops_per_clk = float(os.environ.get("BITSSA_ALU_OPS_PER_CLK_PER_SM", "64"))
+        peak = sms * peak_ops_per_clk * max_mhz * 1e6 / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+                "ops_per_group_step": ops_unit, "ops_per_group_step_of_the_mode": ops_mode,
+                "frac_at_the_mode_count": achieved * ops_mode / ops_unit / peak,
+                "group_steps_per_launch": gs_per_launch,
+                "peak_basis": f"{sms} SMs x {peak_ops_per_clk:g} LOP3 lanes/clk/SM x {max_mhz:g} MHz "
+                              f"(SM count from the device, clock from {mhz_basis}); derived, not measured",
                 "lop3_microbench_gops": micro}
+
+    roofline = roofline_of(N_TOT, PAD, group_steps / world / args.steps, statistics.mean(kernel_ms),
+                           layout_bits=layout_used)
+    fp = kernel_fingerprint()
+    roofline["traffic"] = (TRAFFIC_BYTES_PER_LAUNCH.get(fp) if (WORKLOAD == "c2" and RUNS_PER_GPU == 1 << 20
+                                                                 and PRECISION == 0 and PAD == 1 and ENGINE == 0
+                                                                 and layout_used == 1) else None)
+    roofline["kernel_sources_sha"] = fp
     if WORKLOAD == "c3":
         roofline = None
 
@@ -470,10 +528,45 @@ def main():
         r7 = int(c[2]) / (ms7 / 1e3)
         result["thread_per_run"] = {"value": r7 * world, "unit": "lane-reactions/s", "ms_per_step": ms7,
                                     "absorbed_runs_per_s": int(c[5]) * world / (ms7 / 1e3),
-                                    "speedup_bitsliced_over_thread_per_run": (reactions / t_dev) / (r7 * world)}
+                                    "speedup_bitsliced_over_thread_per_run": (reactions / t_dev) / (r7 * world),
+                                    "precision": PRECISION_NAMES[PRECISION]}
+        # the same pairing with fp32 Kahan clocks on both sides: the baseline's fp64 clock takes a
+        # logarithm and a division per reaction, the bit-sliced product clock none
+        if PRECISION == 0:
+            pair = {}
+            for name, eng in (("bitsliced", ENGINE), ("thread_per_run", pkg.SSA_ENGINE_THREAD_PER_RUN)):
+                kw = dict(pad_pow2=PAD, layout=opt.layout, block_size=opt.block_size) if eng != 1 else {}
+                of = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=pkg.SSA_P32_KAHAN,
+                                             engine=eng, first_run=first_run, **kw)
+                cf = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT),
+                                    RUNS_PER_GPU, SEED, of)
+                pair[name] = time_runs(cf, 3)
+                pkg.ssa_destroy(cf)
+            result["thread_per_run_fp32"] = {
+                "precision": "p32kahan", "bitsliced_ms_per_step": pair["bitsliced"][0],
+                "thread_per_run_ms_per_step": pair["thread_per_run"][0],
+                "bitsliced_value": pair["bitsliced"][1] * world, "thread_per_run_value": pair["thread_per_run"][1] * world,
+                "unit": "lane-reactions/s",
+                "speedup_bitsliced_over_thread_per_run": pair["thread_per_run"][0] / pair["bitsliced"][0]}
         if rank == 0:
             sample = args.cpu_sample if WORKLOAD == "c2" else max(64, args.cpu_sample // 8)
             result["cpu_baseline"] = cpu_baseline(sample, os.cpu_count() or 1)
+    # ---- the precision workload (N_tot = 10 000, 2^22 runs), a few steps per bound, with its roofline
+    if args.c4_steps > 0 and WORKLOAD == "c2" and ENGINE == 0 and PRECISION == 0:
+        result["c4"] = {}
+        for pad in (1, 2):
+            o4 = pkg.ssa_default_options(cuda_stream=stream, device=local, pad_pow2=pad,
+                                         first_run=sharding.weak_shard(1 << 22, rank)[0])
+            c4 = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array([2500, 2500, 5000]),
+                                1 << 22, SEED, o4)
+            ms4, val4, cnt4 = time_runs(c4, args.c4_steps, snaps=SNAPS)
+            pkg.ssa_destroy(c4)
+            result["c4"][f"pad{pad}"] = {
+                "workload": f"frank_N10000_2500-2500-5000_runs{1 << 22}xgpu_tend50_snap10log_p64",
+                "bound": BOUND_NAMES[pad], "steps": args.c4_steps, "warmup": 1, "ms_per_step": ms4,
+                "value": val4 * world, "unit": "lane-reactions/s", "max_group_steps": int(cnt4[8]),
+                "layout": layout_name(int(cnt4[9])),
+                "roofline": roofline_of(10000, pad, float(cnt4[0]), ms4, engine=0, layout_bits=int(cnt4[9]))}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:

@@ -287,24 +287,28 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
 /*
  * ssa_run_frank_noalloc: one run of Frank's model that allocates no device memory.
  *
- * The paper has no counterpart; this entry point exists for callers that cannot
- * allocate: work recorded into a CUDA stream capture (where cudaMalloc is not
- * allowed), plug-ins whose host framework owns all device memory and forbids
- * allocations outside its pool, and latency-critical loops in which an allocation
- * could synchronise the device.  It runs the same bit-sliced kernel as ssa_run on
- * a context-free single ensemble; the caller passes every input and output buffer.
+ * The paper has no counterpart; this is a service of the library.  Some callers
+ * cannot allocate device memory at all: a plug-in hosted by a framework that owns
+ * every byte of device memory (its pool hands out buffers, and memory taken
+ * behind its back can make its own allocations fail), or a latency-critical loop
+ * in which cudaMalloc, which can synchronise the whole device and has no bounded
+ * latency, is not allowed.  They pass in every input and output buffer, and this
+ * call runs the same one-thread bit-sliced kernel as ssa_run on a single ensemble
+ * without a context.  It uses the paper's bound (pad_pow2 = 0: n uniform below
+ * N (N - 1) / 2, draws above it redrawn), the group clock and blocks of 64 threads;
+ * ssa_run with those options gives the same runs.
  *
  * The kernel's own scratch (work-queue counter, run counters, error word and the
- * snapshot thresholds, about 2.2 KB) is a fixed device array inside the library,
- * one per GPU that loads the library, held until the process exits.  Its device
- * address is looked up on the first call on each device (with that device
- * current), so make that first call before any stream capture.  Every call clears
- * the parts that must start at zero, and calls share the array: calls that
- * overlap on the GPU (other streams, other host threads on the same device) race
- * and must be serialised by the caller.
+ * crossing thresholds of up to 64 snapshot times plus t_end, about 2.2 KB) is a
+ * fixed device array inside the library: every GPU that loads the library holds a
+ * copy until the process exits.  The first call on a device looks up that copy's
+ * address, with the device current.  Every call clears what must start at zero and
+ * overwrites the thresholds, so calls share the array: two calls that overlap on
+ * one GPU (other streams, other host threads) race, and the caller must serialise
+ * them.
  *
- *   N0: int64[3] host, the shared initial counts in Frank's species order (L, D, A)
- *       for the reactions A+L->2L, A+D->2D, L+D->2A (Eqs. 1-3); total in [1, 65536].
+ *   N0: int64[3] host, the shared initial counts of L, D and A for the reactions
+ *       A+L->2L, A+D->2D, L+D->2A; total in [1, 65536].
  *   rates: double[3] host, k >= 0 with max > 0 (thinning as in ssa_create, q = thin_bits).
  *   n_runs >= 0, seed: as in ssa_create (run j is lane j % 32 of group j / 32).
  *   t_end, snapshot_times (double[n_snap] host, ascending, in [0, t_end]), n_snap in
@@ -313,13 +317,15 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
  *   precision: SSA_P64 ... SSA_P32_PLAIN.
  *   outputs, device memory on the current device, written on cuda_stream:
  *       final_counts int32[n_runs][3], t_abs double[n_runs], outcome int8[n_runs]
- *       (as SSA_FIELD_FINAL_COUNTS / ABSORB_TIME / ABSORB_OUTCOME, species order L, D, A),
- *       ee_hist uint64[n_snap][65] (cleared by the call; may be NULL when n_snap == 0).
+ *       (as SSA_FIELD_FINAL_COUNTS / ABSORB_TIME / ABSORB_OUTCOME, species order L, D, A;
+ *       may be NULL when n_runs == 0), ee_hist uint64[n_snap][65] (cleared by the call;
+ *       may be NULL when n_snap == 0).
  *   counters_out: uint64[10] host (as SSA_FIELD_COUNTERS) or NULL.
  *   cuda_stream: cudaStream_t, NULL = the legacy default stream.
- * Blocks until the work is done.  Returns an ssa_status; the message of a failure is
- * given by ssa_last_error(NULL) on the calling thread.  Calls no cudaMalloc, cudaFree
- * or other allocating routine.
+ * The thresholds are copied from host memory and the counters read back into it, and
+ * the call waits for the stream before it returns.  Returns an ssa_status; the message
+ * of a failure is given by ssa_last_error(NULL) on the calling thread.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  */
 int ssa_run_frank_noalloc(const int64_t* N0, const double* rates, int64_t n_runs, uint64_t seed,
                           int32_t thin_bits, double t_end, const double* snapshot_times, int32_t n_snap,

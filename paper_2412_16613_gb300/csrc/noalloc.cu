@@ -1,14 +1,14 @@
 // noalloc.cu -- ssa_run_frank_noalloc: a single-ensemble run of the bit-sliced
 // kernel that allocates no device memory.
 //
-// Who needs it: code that may not call cudaMalloc -- work recorded into a CUDA
-// graph or a stream capture, where allocation calls are not allowed; plug-ins
-// hosted by a framework that owns every byte of device memory and forbids
-// allocations outside its pool; latency-critical loops where an allocation could
-// synchronise the device.  Such callers hand in their own input and output
-// buffers; the small scratch the kernel needs for itself (the work-queue counter,
-// the run counters, the error word and the snapshot thresholds) lives in a
-// fixed-size device array that is part of the library image.
+// Who needs it: callers that may not allocate device memory -- a plug-in hosted by
+// a framework that owns every byte of device memory and hands out buffers from its
+// own pool, or a latency-critical loop in which cudaMalloc (which can synchronise
+// the device and has no bounded latency) is not allowed.  They hand in their own
+// input and output buffers; the small scratch the kernel needs for itself (the
+// work-queue counter, the run counters, the error word and the snapshot thresholds)
+// lives in a fixed-size device array that is part of the library image.  The call
+// uses the paper's bound (pad_pow2 = 0) and the group clock.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,6 +1,7 @@
 """Helpers for the GPU tests: run libbitssa through its C ABI and compare with the oracle."""
 import numpy as np
 
+import oracle
 import paper_2412_16613_gb300 as pkg
 
 FRANK_R, FRANK_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
@@ -50,3 +51,17 @@ def assert_parity(g, r, rtol=1e-12, tie=1e-12, snaps=True, min_ok=0.99):
     if snaps and r["snap_counts"] is not None and "snap_counts" in g:
         assert np.array_equal(g["snap_counts"][:, ok], r["snap_counts"][:, ok])
     return ok
+
+
+def assert_hist_parity(g, r, ok):
+    """ee_hist: the GPU's histogram is the histogram of its own per-run snapshot counts (all
+    runs), and on the runs without a near tie those counts bin exactly as the oracle's."""
+    assert np.array_equal(g["ee_hist"].reshape(-1, 65), oracle.ee_histogram(g["snap_counts"]))
+    assert np.array_equal(oracle.ee_histogram(g["snap_counts"][:, ok]), oracle.ee_histogram(r["snap_counts"][:, ok]))
+
+
+def group_steps(r, n_runs):
+    """Per group of 32 runs: the steps of its longest run (a group steps until its last run stops)."""
+    steps = np.zeros(((n_runs + 31) // 32) * 32, dtype=np.int64)
+    steps[:n_runs] = r["steps"]
+    return steps.reshape(-1, 32).max(1)

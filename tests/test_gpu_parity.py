@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import paper_2412_16613_gb300 as pkg
-from tests._gpu import FRANK_P, FRANK_R, assert_parity, gpu_run, log_snapshots
+from tests._gpu import FRANK_P, FRANK_R, assert_hist_parity, assert_parity, group_steps, gpu_run, log_snapshots
 
 pytestmark = pytest.mark.gpu
 
@@ -106,12 +106,36 @@ def test_parity_n1024_subset_ragged(layout):
     r = oracle.run(oracle.frank(), (256, 256, 512), n, seed=0, t_end=50.0, snap_times=snaps,
                    threads=THREADS)
     ok = assert_parity(g, r)
-    if ok.all():
-        assert np.array_equal(g["ee_hist"], oracle.ee_histogram(r["snap_counts"]))
-        assert g["counters"]["reactions"] == r["reactions"].sum()
-        assert g["counters"]["lane_steps"] == r["steps"].sum()
+    assert_hist_parity(g, r, ok)
+    assert ok.all()  # at this seed the oracle reports no event within 1e-12 of a snapshot or t_end
+    assert np.array_equal(g["ee_hist"], oracle.ee_histogram(r["snap_counts"]))
+    assert g["counters"]["reactions"] == r["reactions"].sum()
+    assert g["counters"]["lane_steps"] == r["steps"].sum()
     assert np.all(g["ee_hist"].sum(1) == n)
     assert np.all(g["final_counts"].sum(1) == 1024)
+
+
+def test_parity_bench_configuration():
+    """The benchmark's launch configuration on a subset of its workload: N_tot = 1024 from
+    (256, 256, 512), the bound padded to 2^19, one thread per group in blocks of 128, the 10
+    log-spaced snapshots to t_end = 50, seed 0; 8192 + 21 runs (257 groups, the last ragged).
+    Every run, snapshot and histogram, and the run counters, against the oracle at the same bound."""
+    n = 8192 + 21
+    snaps = log_snapshots(50.0, 10)
+    g = gpu_run((256, 256, 512), n, seed=0, t_end=50.0, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD,
+                block_size=128, pad_pow2=1)
+    r = oracle.run(oracle.frank(), (256, 256, 512), n, seed=0, t_end=50.0, snap_times=snaps, pad_pow2=True,
+                   threads=THREADS)
+    ok = assert_parity(g, r)
+    assert_hist_parity(g, r, ok)
+    assert ok.all()  # at this seed the oracle reports no event within 1e-12 of a snapshot or t_end
+    assert np.array_equal(g["ee_hist"], oracle.ee_histogram(r["snap_counts"]))
+    c = g["counters"]
+    assert c["reactions"] == r["reactions"].sum() and c["lane_steps"] == r["steps"].sum()
+    gs = group_steps(r, n)
+    assert c["group_steps"] == gs.sum() and c["max_group_steps"] == gs.max()
+    assert c["redraw_rounds"] == 0 and c["absorbed"] == (r["outcome"] >= 0).sum()
+    assert c["groups_done"] == (n + 31) // 32 and c["layout"] == pkg.SSA_LAYOUT_THREAD
 
 
 def test_parity_n1024_full_size_sampled():
@@ -140,17 +164,19 @@ def test_parity_n1024_full_size_sampled():
     (pkg.SSA_P64_LOGSUM, oracle.P64, 1e-12, 1e-12),
     (pkg.SSA_P32_KAHAN, oracle.P32_KAHAN, 2e-5, 1e-6),
     (pkg.SSA_P32_D64ACC, oracle.P32_D64ACC, 2e-5, 1e-6),
+    (pkg.SSA_P32_PLAIN, oracle.P32_PLAIN, 2e-5, 1e-6),
 ])
+@pytest.mark.parametrize("pad", [0, 1], ids=["paper_bound", "padded"])
 @LAYOUTS
-def test_parity_precision_modes(mode, omode, rtol, tie, layout):
+def test_parity_precision_modes(mode, omode, rtol, tie, pad, layout):
     """fp32 clocks: CUDA's logf and the host's may differ by an ulp, so event times agree to
     ~1e-7 relative; runs with an event within `tie` of a snapshot are left out of the
     count comparison (several percent of runs at 10 snapshots)."""
     snaps = log_snapshots(50.0, 10)
     n = 1024 + 5
-    g = gpu_run((256, 256, 512), n, seed=3, t_end=50.0, snaps=snaps, precision=mode, layout=layout)
+    g = gpu_run((256, 256, 512), n, seed=3, t_end=50.0, snaps=snaps, precision=mode, layout=layout, pad_pow2=pad)
     r = oracle.run(oracle.frank(), (256, 256, 512), n, seed=3, t_end=50.0, snap_times=snaps,
-                   precision=omode, threads=THREADS)
+                   precision=omode, threads=THREADS, pad_pow2=bool(pad))
     assert_parity(g, r, rtol=rtol, tie=tie, min_ok=0.95)
 
 
@@ -404,10 +430,12 @@ def test_parity_padded_bound(N, rates, layout):
     r = oracle.run(oracle.frank(*rates), init, n, seed=29, t_end=t_end, snap_times=snaps, threads=THREADS,
                    pad_pow2=True)
     ok = assert_parity(g, r)
+    assert_hist_parity(g, r, ok)
     assert g["counters"]["redraw_rounds"] == 0 and r["redraws"].sum() == 0
-    if ok.all():
-        assert g["counters"]["lane_steps"] == r["steps"].sum()
-        assert g["counters"]["reactions"] == r["reactions"].sum()
+    assert ok.all()  # at this seed the oracle reports no event within 1e-12 of a snapshot or t_end
+    assert np.array_equal(g["ee_hist"], oracle.ee_histogram(r["snap_counts"]))
+    assert g["counters"]["lane_steps"] == r["steps"].sum()
+    assert g["counters"]["reactions"] == r["reactions"].sum()
 
 
 def test_parity_padded_bound_shared_n():

@@ -226,7 +226,7 @@ def test_first_step_probabilities_padded(orc, init):
     assert r["redraws"].sum() == 0
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_waiting_time_exponential(orc, precision):
     """Eq. equation-tau: tau ~ Exp(Lambda), one clock per 32-lane group."""
     net = orc.frank()
@@ -466,6 +466,27 @@ def test_precision_modes_share_the_trajectory(orc):
         # the fp32 uniform is the top 24 bits of the fp64 one, so the clocks are paired
         rel = np.abs(r["t_abs"] / base["t_abs"] - 1)
         assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-3
+
+
+def test_plain_fp32_sum_shares_the_trajectory_and_loses_more(orc):
+    """The plain fp32 clock (Eq. eq-update-time summed in fp32 without compensation): the same
+    counts and steps as the other modes, every time an fp32 value, and a larger error against the
+    fp64 sum than the Kahan-compensated fp32 sum of the same fp32 waiting times.  An fp64
+    accumulator in its place would give times that are not fp32 values; a compensated sum would
+    give Kahan's error."""
+    init, n, th = (256, 256, 512), 256, os.cpu_count() or 4  # about 16 000 steps a run
+    base = orc.run(orc.frank(), init, n, seed=11, t_end=np.inf, threads=th)
+    kahan = orc.run(orc.frank(), init, n, seed=11, t_end=np.inf, precision=orc.P32_KAHAN, threads=th)
+    plain = orc.run(orc.frank(), init, n, seed=11, t_end=np.inf, precision=orc.P32_PLAIN, threads=th)
+    for r in (kahan, plain):
+        assert np.array_equal(r["final_counts"], base["final_counts"])
+        assert np.array_equal(r["steps"], base["steps"])
+    assert np.array_equal(plain["t_abs"].astype(np.float32).astype(np.float64), plain["t_abs"])
+    assert np.array_equal(plain["t_last"].astype(np.float32).astype(np.float64), plain["t_last"])
+    rel_k = np.abs(kahan["t_abs"] / base["t_abs"] - 1)
+    rel_p = np.abs(plain["t_abs"] / base["t_abs"] - 1)
+    assert np.median(rel_p) > 2.0 * np.median(rel_k), (np.median(rel_p), np.median(rel_k))
+    assert np.median(rel_p) < 1e-4
 
 
 def test_ee_bin_definition(orc):
