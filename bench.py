@@ -83,8 +83,8 @@ def device_sm_count_and_max_mhz(index: int):
 
 def layout_name(bits: int) -> str:
     """The layouts counter 9 reports: one thread / three warps, and the general kernel's mode."""
-    names = [n for bit, n in ((1, "thread"), (2, "warps"), (4, "general incremental"), (8, "general products"))
-             if bits & bit]
+    names = [n for bit, n in ((1, "thread"), (2, "warps"), (4, "general incremental"), (8, "general products"),
+                              (16, "tail one run per thread")) if bits & bit]
     return "+".join(names) or "none"
 
 
@@ -280,6 +280,9 @@ def main():
                     help="skip ssa_tune (by default it times every launch configuration on the "
                          "workload during warm-up and keeps the fastest; c3 keeps the per-bucket rule)")
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--tail", type=int, default=0,
+                    help="ssa_options.tail_groups: 0 the library's choice, -1 never hand the last groups of "
+                         "a warp to one run per thread, 1..8 the threshold")
     ap.add_argument("--pad", type=int, default=1, choices=[0, 1, 2],
                     help="1: pad the uniformisation bound to 2^K with null events, so that no draw of n "
                          "is rejected (the same process, sampled through a different draw); 2: a "
@@ -325,7 +328,7 @@ def main():
     first_run = sharding.weak_shard(RUNS_PER_GPU, rank)[0] if WORKLOAD != "c3" else 0
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                   block_size=args.block, first_run=first_run, layout=args.layout,
-                                  pad_pow2=PAD, engine=ENGINE)
+                                  pad_pow2=PAD, engine=ENGINE, tail_groups=args.tail)
     if WORKLOAD == "c3":
         opt.first_run = 0
         ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],
@@ -447,7 +450,7 @@ def main():
               "group_steps_per_step": group_steps / args.steps, "max_group_steps": max_group_steps,
               "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
               "hist_checksum": float(htot.sum().item()),
-              "layout": layout_name(layout_used),
+              "layout": layout_name(layout_used), "layout_bits": layout_used,
               "tuned": None if tuned is None else {"layout": {0: "rule", 1: "thread", 2: "warps"}[tuned[0]],
                                                    "block": tuned[1]}}
 

@@ -152,8 +152,25 @@ typedef struct {
                                 at every step (Sec. 4.1); 0 (default) incremental unless ssa_tune
                                 found products faster on the caller's workload.  Same runs in
                                 every mode. */
+  int32_t clock;             /* SSA_CLOCK_GROUP (default): the 32 runs of a group share one clock (one
+                                waiting time per group and step, the paper's one tau for all copies,
+                                end of Sec. 4).  SSA_CLOCK_LANE: every run has its own clock */
+  int32_t word_width;        /* lanes per word: 0 (default) or 32.  64 (two groups per thread) gives
+                                SSA_EUNSUPPORTED: a thread's registers hold one group's state */
+  int32_t tail_groups;       /* one-thread layout of Frank's model: once every group has started, a warp
+                                with at most this many groups still running finishes them with one run
+                                per thread and plain integer arithmetic on the same words (same runs,
+                                bit for bit).  0 (default): the library's choice (8, or what ssa_tune
+                                found); -1: never; 1..8.  Groups with thinned reactions (some
+                                k_r < k_max) always stay bit-sliced */
   int32_t reserved[3];
 } ssa_options;
+
+/* Clock of the runs of a group (ssa_options.clock). */
+enum {
+  SSA_CLOCK_GROUP = 0,
+  SSA_CLOCK_LANE = 1
+};
 
 /* Fields for ssa_fetch.  n_runs = the context's total number of runs (for a batch,
  * ensembles are concatenated in order); S = n_species, in the caller's species order. */
@@ -177,7 +194,9 @@ enum {
                                    the layouts that ran (bit 0 SSA_LAYOUT_THREAD, bit 1
                                    SSA_LAYOUT_WARPS: 1, 2, or 3 for a batch that used both;
                                    0 no bit-sliced launch; on the general kernel also bit 2
-                                   with propensities incremented, bit 3 recomputed by products) */
+                                   with propensities incremented, bit 3 recomputed by products;
+                                   bit 4: some groups were finished one run per thread, see
+                                   ssa_options.tail_groups) */
   SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,
                                    and [3] the others: not absorbed, absorbed with several
                                    species left, or with one species of index 3 or above */

@@ -27,6 +27,7 @@ SSA_ECUDA, SSA_ETIMEOUT, SSA_EOVERFLOW, SSA_ESTATE = -4, -5, -6, -7
 SSA_P64, SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P64_LOGSUM, SSA_P32_PLAIN = 0, 1, 2, 3, 4
 SSA_ENGINE_BITSLICED, SSA_ENGINE_THREAD_PER_RUN, SSA_ENGINE_GENERAL = 0, 1, 2
 SSA_LAYOUT_AUTO, SSA_LAYOUT_THREAD, SSA_LAYOUT_WARPS = 0, 1, 2
+SSA_CLOCK_GROUP, SSA_CLOCK_LANE = 0, 1
 SSA_FIELD_FINAL_COUNTS, SSA_FIELD_ABSORB_TIME, SSA_FIELD_ABSORB_OUTCOME = 0, 1, 2
 SSA_FIELD_EE_HIST, SSA_FIELD_SNAP_COUNTS, SSA_FIELD_COUNTERS, SSA_FIELD_ENS_ABSORBED = 3, 4, 5, 6
 SSA_N_COUNTERS = 10
@@ -53,7 +54,8 @@ class ssa_options(C.Structure):
         ("blocks_per_sm", C.c_int32), ("thin_bits", C.c_int32), ("keep_snap_counts", C.c_int32),
         ("step_budget", C.c_int64), ("first_run", C.c_int64), ("cuda_stream", C.c_void_p),
         ("device", C.c_int32), ("layout", C.c_int32), ("shared_n", C.c_int32), ("pad_pow2", C.c_int32),
-        ("recompute", C.c_int32), ("reserved", C.c_int32 * 3),
+        ("recompute", C.c_int32), ("clock", C.c_int32), ("word_width", C.c_int32), ("tail_groups", C.c_int32),
+        ("reserved", C.c_int32 * 3),
     ]
 
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "frank_kernel.cuh"
+#include "frank_tail.cuh"
 
 #ifndef BITSSA_K
 #error "compile with -DBITSSA_K=<planes>"

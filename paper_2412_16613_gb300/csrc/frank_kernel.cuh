@@ -688,15 +688,25 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
   atomicMax(&p.counters[kMaxGroupSteps], s.step);
 }
 
+template <int K, bool BATCH, bool PROD, bool ADAPT>
+__device__ __forceinline__ void tail_run(const FrankLaunch& p, const GroupState<K, PROD>& s, bool active, unsigned int* s_hist,
+                         uint32_t* wbuf, unsigned int& errors);
+template <int K>
+struct TailShape;
+constexpr int kTailWarps = 8;  // warps of the largest block (256 threads)
+
 // The persistent kernel.  Every thread owns one group at a time and takes the next
 // work item from a queue when its group finishes.  The loop is warp-synchronous: all
 // 32 threads stay in it until the whole warp has run out of work, and the warp
 // reconverges after every group step, so the rare divergent paths (redraws,
 // snapshots, absorptions, a new group) cost one pass each instead of leaving the warp
 // split for the rest of the run.  Single-ensemble launches read the ensemble from the
-// kernel parameters (warp-uniform); batches from a table.
+// kernel parameters (warp-uniform); batches from a table.  Once the queue is drained, a warp
+// whose running groups are few enough hands them to tail_run (frank_tail.cuh), which finishes
+// them with one run per thread.
 template <int K, bool BATCH, bool PROD, bool ADAPT>
 __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ FrankLaunch p) {
+  __shared__ __align__(16) uint32_t tail_words[kTailWarps][TailShape<K>::kWarpWords];
   unsigned int* const s_hist_mem = frank_dyn_smem;
   const bool smem_hist = !BATCH && p.n_snap > 0;
   unsigned int* s_hist = smem_hist ? s_hist_mem : nullptr;
@@ -725,6 +735,16 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
       }
     }
     if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
+    if (p.tail_groups > 0) {
+      const bool running = active && !s.done;  // (a group can be done at its start: absorbed)
+      const uint32_t alive = __ballot_sync(0xFFFFFFFFu, running);
+      if (__popc(alive) <= p.tail_groups && __any_sync(0xFFFFFFFFu, exhausted) &&
+          !__any_sync(0xFFFFFFFFu, running && (BATCH ? p.ens_table[s.ens].thin : p.ens.thin))) {
+        if (active && s.done) group_finish<K, PROD>(p, s, BATCH ? p.ens_table[s.ens] : p.ens);
+        tail_run<K, BATCH, PROD, ADAPT>(p, s, running, s_hist, tail_words[threadIdx.x >> 5], errors);
+        break;  // the queue is drained and every group of the warp has finished
+      }
+    }
     if (active) {
       const Ensemble& e = BATCH ? p.ens_table[s.ens] : p.ens;
       if (!s.done) group_step<K, PROD, ADAPT>(p, s, e, thr, s_hist, errors);

@@ -28,6 +28,7 @@ __host__ __device__ constexpr int bit_length(long long v) {
 }
 
 constexpr int kMaxSnap = 64;
+constexpr int kDefaultTailGroups = 8;  // the one-thread kernel's tail hand-off (FrankLaunch::tail_groups)
 constexpr int kHistBins = 65;  // 64 enantiomeric-excess bins + one for L + D == 0
 constexpr int kCounters = 10;
 constexpr int kMaxK = 31;      // random / propensity planes: N_tot (N_tot - 1) / 2 < 2^31
@@ -52,10 +53,12 @@ enum Counter {
   kErrorFlags = 7,
   kMaxGroupSteps = 8, // the longest group, in steps
   kLayoutUsed = 9     // set by the host: bit 0 one thread per group, bit 1 three warps per 32 groups,
-                      // bit 2 the general kernel incrementing propensities, bit 3 it recomputing them
+                      // bit 2 the general kernel incrementing propensities, bit 3 it recomputing them,
+                      // bit 4 (by the device) the one-thread kernel's tail hand-off ran
 };
 constexpr int kLayoutGeneralIncremental = 4;
 constexpr int kLayoutGeneralProducts = 8;
+constexpr int kLayoutTail = 16;  // set by the device: some groups were finished one run per thread
 
 // Error flags (OR-ed into the status word).
 enum ErrorFlag : uint32_t {
@@ -170,6 +173,9 @@ struct FrankLaunch {
   int adapt;                      // one-thread Frank kernel: 1 runs the instantiation with the
                                   // state-following bound (each step's bound 2^p, p the bit length
                                   // of the largest S_R over the group's live lanes; 2^K its ceiling)
+  int tail_groups;                // one-thread Frank kernel: once the work queue is drained, a warp
+                                  // with at most this many running groups (1..8) finishes them with
+                                  // one run per thread; 0 never
   int stage_offset;               // one-thread Frank kernel with a snapshot dump: the word of dynamic
                                   // shared memory where the per-thread staging rows start; -1: none
   Network net;                    // general kernel only

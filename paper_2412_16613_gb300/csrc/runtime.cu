@@ -219,6 +219,7 @@ struct ssa_ctx {
   int tuned_layout = -1;  // ssa_tune's choice for SSA_LAYOUT_AUTO: -1 none, else an SSA_LAYOUT_*
   int tuned_block = 0;    // ssa_tune's block size for the one-thread layout, 0 none
   int tuned_products = -1;  // ssa_tune's mode for the general kernel: -1 none, 0 incremental, 1 products
+  int tuned_tail = -1;      // ssa_tune's tail hand-off threshold: -1 none, 0 off, else groups per warp
   int n_queues = 0;
   bool ran = false;
   int n_snap = 0;
@@ -404,6 +405,13 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.blocks_per_sm < 0) return (*why = "blocks_per_sm must be >= 0", SSA_EINVAL);
   if (o.step_budget < 0) return (*why = "step_budget must be >= 0", SSA_EINVAL);
   if (o.first_run < 0 || (o.first_run % 32) != 0) return (*why = "first_run must be a multiple of 32", SSA_EINVAL);
+  if (o.clock != SSA_CLOCK_GROUP && o.clock != SSA_CLOCK_LANE) return (*why = "unknown clock", SSA_EINVAL);
+  if (o.clock == SSA_CLOCK_LANE) return (*why = "the per-run clock is not built", SSA_EUNSUPPORTED);
+  if (o.word_width != 0 && o.word_width != 32 && o.word_width != 64)
+    return (*why = "word_width must be 0, 32 or 64", SSA_EINVAL);
+  if (o.word_width == 64)
+    return (*why = "64-lane words (two groups per thread) do not fit a thread's registers", SSA_EUNSUPPORTED);
+  if (o.tail_groups < -1 || o.tail_groups > 8) return (*why = "tail_groups must be in [-1, 8]", SSA_EINVAL);
   return SSA_OK;
 }
 
@@ -686,6 +694,9 @@ int launch_runs(ssa_ctx* c) {
   fl.snap_counts = c->opt.keep_snap_counts ? c->d_snap : nullptr;
   fl.stage_offset = -1;
   fl.adapt = c->opt.pad_pow2 == 2 ? 1 : 0;
+  // the tail hand-off of the one-thread kernel: a fixed option wins, then the tuner's choice
+  fl.tail_groups = c->opt.tail_groups < 0 ? 0 : (c->opt.tail_groups > 0 ? c->opt.tail_groups
+                                                 : (c->tuned_tail >= 0 ? c->tuned_tail : kDefaultTailGroups));
   fl.n_runs_total = c->n_runs_total;
   fl.counters = c->d_counters;
   fl.status = c->d_status;
@@ -1112,7 +1123,7 @@ int ssa_run(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_sn
     return cuda_fail(c, e, "read status");
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "simulation");
   c->counters[kErrorFlags] = status;
-  c->counters[kLayoutUsed] = c->layout_used;
+  c->counters[kLayoutUsed] = c->layout_used | (c->counters[kLayoutUsed] & kLayoutTail);
   c->ran = true;
   if (status & kErrRedraw) return fail(c, SSA_EOVERFLOW, "64 redraws of n in a row");
   if (status & kErrRange) return fail(c, SSA_EOVERFLOW, "internal range check failed");

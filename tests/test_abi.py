@@ -55,7 +55,8 @@ def test_default_options(lib):
     o = pkg.ssa_default_options()
     assert o.precision == pkg.SSA_P64 and o.engine == pkg.SSA_ENGINE_BITSLICED
     assert o.thin_bits == 32 and o.device == -1 and o.step_budget == 0 and o.first_run == 0
-    assert C.sizeof(pkg.ssa_options) == 80
+    assert C.sizeof(pkg.ssa_options) == 96
+    assert o.clock == pkg.SSA_CLOCK_GROUP and o.word_width == 0 and o.tail_groups == 0
 
 
 def _create(reac, prod, rates=(1.0, 1.0, 1.0), N0=(16, 16, 32), n_runs=64, **opt):
@@ -103,6 +104,11 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
     (dict(reac=F_R, prod=F_P, engine=pkg.SSA_ENGINE_GENERAL, layout=pkg.SSA_LAYOUT_WARPS), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, engine=3), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, recompute=3), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, clock=2), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, word_width=16), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, word_width=64), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, tail_groups=9), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, tail_groups=-2), pkg.SSA_EINVAL),
 ])
 def test_validation_before_any_cuda_call(lib, kw, status):
     with pytest.raises(pkg.SSAError) as ei:

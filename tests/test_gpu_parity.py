@@ -135,7 +135,7 @@ def test_parity_bench_configuration():
     gs = group_steps(r, n)
     assert c["group_steps"] == gs.sum() and c["max_group_steps"] == gs.max()
     assert c["redraw_rounds"] == 0 and c["absorbed"] == (r["outcome"] >= 0).sum()
-    assert c["groups_done"] == (n + 31) // 32 and c["layout"] == pkg.SSA_LAYOUT_THREAD
+    assert c["groups_done"] == (n + 31) // 32 and c["layout"] & 3 == pkg.SSA_LAYOUT_THREAD
 
 
 def test_parity_n1024_full_size_sampled():
@@ -206,7 +206,7 @@ def test_layouts_agree_bit_for_bit(init, n, t_end, seed):
     for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
         assert np.array_equal(a[k], b[k]), k
     assert same_counters(a, b)
-    assert (a["counters"]["layout"], b["counters"]["layout"]) == (pkg.SSA_LAYOUT_THREAD, pkg.SSA_LAYOUT_WARPS)
+    assert (a["counters"]["layout"] & 3, b["counters"]["layout"]) == (pkg.SSA_LAYOUT_THREAD, pkg.SSA_LAYOUT_WARPS)
 
 
 @LAYOUTS
@@ -459,3 +459,81 @@ def test_a_later_t_end_extends_the_same_runs(layout):
     assert np.array_equal(a["final_counts"], b["snap_counts"][0])
     done = np.isfinite(a["t_abs"])
     assert np.array_equal(a["t_abs"][done], b["t_abs"][done])
+
+
+TAIL_CASES = [
+    dict(init=(256, 256, 512), n=4096 + 17, t_end=50.0, seed=41, snaps=log_snapshots(50.0, 10)),
+    dict(init=(256, 256, 512), n=4096 + 17, t_end=50.0, seed=41, snaps=log_snapshots(50.0, 10), pad_pow2=1),
+    dict(init=(256, 256, 512), n=2048 + 3, t_end=50.0, seed=42, snaps=log_snapshots(50.0, 6), pad_pow2=2),
+    dict(init=(256, 256, 512), n=2048 + 3, t_end=50.0, seed=43, snaps=log_snapshots(50.0, 6),
+         precision=pkg.SSA_P32_KAHAN),
+    dict(init=(256, 256, 512), n=2048, t_end=50.0, seed=44, snaps=[0.01, 0.1], precision=pkg.SSA_P64_LOGSUM),
+    dict(init=(2500, 2500, 5000), n=1024 + 1, t_end=0.002, seed=45, snaps=[0.0005, 0.001]),
+    dict(init=(11600, 11600, 23200), n=512 + 9, t_end=5e-6, seed=46, snaps=[1e-6, 3e-6]),
+    dict(init=(3, 3, 6), n=3000, t_end=5.0, seed=47, snaps=[0.1, 1.0]),
+    dict(init=(256, 256, 512), n=4096, t_end=0.03, seed=48, snaps=[0.01, 0.02]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TAIL_CASES)))
+@pytest.mark.parametrize("block", [32, 128])
+def test_tail_hand_off_keeps_the_runs(case, block):
+    """The one-thread kernel's tail hand-off (the last groups of a warp finished one run per
+    thread) gives every run, snapshot, histogram, absorption time and counter of the kernel
+    without it, bit for bit: paper's, padded and state-following bounds, every clock, wide n with
+    heavy rejection (N = 46 400), t_end before absorption, and a hand-off threshold of 1 and 8."""
+    kw = dict(TAIL_CASES[case])
+    init, n, t_end, seed, snaps = kw.pop("init"), kw.pop("n"), kw.pop("t_end"), kw.pop("seed"), kw.pop("snaps")
+    base = gpu_run(init, n, seed=seed, t_end=t_end, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, block_size=block,
+                   tail_groups=-1, **kw)
+    assert not base["counters"]["layout"] & 16
+    for tail in (8, 1):
+        g = gpu_run(init, n, seed=seed, t_end=t_end, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, block_size=block,
+                    tail_groups=tail, **kw)
+        assert g["counters"]["layout"] & 16, tail
+        for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts", "ens_absorbed"):
+            assert np.array_equal(g[k], base[k]), (tail, k)
+        assert same_counters(g, base), (tail, g["counters"], base["counters"])
+
+
+def test_tail_hand_off_on_a_batch():
+    """A batch of ensembles with different N_tot and seeds: the tail hand-off keeps every run."""
+    import torch
+    init = np.array([[16, 16, 32], [256, 256, 512], [100, 60, 340], [2500, 2500, 5000]])
+    runs = np.array([100, 2048, 777, 513])
+    seeds = np.array([3, 4, 5, 6], dtype=np.uint64)
+    out = []
+    for tail in (-1, 8):
+        o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), layout=pkg.SSA_LAYOUT_THREAD,
+                                    tail_groups=tail, keep_snap_counts=1)
+        ctx = pkg.ssa_create_batch(FRANK_R, FRANK_P, init, np.ones((4, 3)), runs, seeds, o)
+        try:
+            pkg.ssa_run(ctx, 1.0, [0.001, 0.01])
+            out.append(pkg.fetch_all(ctx, snapshots=True))
+        finally:
+            pkg.ssa_destroy(ctx)
+    for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts", "ens_absorbed"):
+        assert np.array_equal(out[0][k], out[1][k]), k
+    assert same_counters(out[0], out[1])
+    assert out[1]["counters"]["layout"] & 16
+
+
+def test_tail_hand_off_with_groups_absorbed_at_start():
+    """Per-run initial states where whole groups start absorbed (a single species) next to groups
+    that run, to absorption (t_end = inf): the hand-off finishes the absorbed groups first and the
+    runs equal those without it and the oracle's."""
+    rng = np.random.default_rng(91)
+    n = 32 * 9 + 5
+    init = rng.multinomial(128, [0.25, 0.25, 0.5], size=n)
+    init[0:32] = (128, 0, 0)
+    init[64:96] = (0, 0, 128)
+    init[200:232] = (0, 128, 0)
+    snaps = [0.001, 0.01, 0.1]
+    base = gpu_run(init, n, seed=5, t_end=np.inf, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, tail_groups=-1)
+    g = gpu_run(init, n, seed=5, t_end=np.inf, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, tail_groups=8)
+    assert g["counters"]["layout"] & 16
+    for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts", "ens_absorbed"):
+        assert np.array_equal(g[k], base[k]), k
+    assert same_counters(g, base)
+    r = oracle.run(oracle.frank(), init, seed=5, t_end=np.inf, snap_times=snaps, threads=THREADS)
+    assert_parity(g, r)
