@@ -282,7 +282,7 @@ def main():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--tail", type=int, default=0,
                     help="ssa_options.tail_groups: 0 the library's choice, -1 never hand the last groups of "
-                         "a warp to one run per thread, 1..8 the threshold")
+                         "a warp to one run per thread, 1..4 the threshold")
     ap.add_argument("--pad", type=int, default=1, choices=[0, 1, 2],
                     help="1: pad the uniformisation bound to 2^K with null events, so that no draw of n "
                          "is rejected (the same process, sampled through a different draw); 2: a "

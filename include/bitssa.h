@@ -160,8 +160,8 @@ typedef struct {
   int32_t tail_groups;       /* one-thread layout of Frank's model: once every group has started, a warp
                                 with at most this many groups still running finishes them with one run
                                 per thread and plain integer arithmetic on the same words (same runs,
-                                bit for bit).  0 (default): the library's choice (8, or what ssa_tune
-                                found); -1: never; 1..8.  Groups with thinned reactions (some
+                                bit for bit).  0 (default): the library's choice (2, or what ssa_tune
+                                found); -1: never; 1..4.  Groups with thinned reactions (some
                                 k_r < k_max) always stay bit-sliced */
   int32_t reserved[3];
 } ssa_options;
@@ -259,8 +259,9 @@ int ssa_run(ssa_ctx* ctx, double t_end, const double* snapshot_times, int32_t n_
 /*
  * Autotuner: time the context's work under each launch configuration the library has and keep
  * the fastest for later ssa_run calls whose options leave layout = SSA_LAYOUT_AUTO, block_size =
- * 0 and recompute = 0 (fixed options win).  Frank's model: the automatic layout rule, one thread
- * per group of 32 runs with blocks of 32, 64 and 128 threads, three warps per 32 groups.  A
+ * 0, recompute = 0 and tail_groups = 0 (fixed options win).  Frank's model: the automatic layout
+ * rule, one thread per group of 32 runs with blocks of 32, 64 and 128 threads, three warps per 32
+ * groups; then, when one thread per group won, the tail hand-off off or at 1, 2 or 4 groups.  A
  * general network: blocks of 32, 64 and 128 threads, each with the propensities incremented and
  * with them recomputed by products.  Results do not depend on the configuration: every one draws
  * the same streams and gives the same runs.

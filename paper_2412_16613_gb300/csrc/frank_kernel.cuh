@@ -688,9 +688,14 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
   atomicMax(&p.counters[kMaxGroupSteps], s.step);
 }
 
+template <bool PROD>
+struct TailGroups;
+template <int K, bool BATCH, bool PROD>
+__device__ __forceinline__ TailGroups<PROD> tail_take(const FrankLaunch& p, const GroupState<K, PROD>& s, bool active,
+                                                      int& ns);
 template <int K, bool BATCH, bool PROD, bool ADAPT>
-__device__ __forceinline__ void tail_run(const FrankLaunch& p, const GroupState<K, PROD>& s, bool active, unsigned int* s_hist,
-                         uint32_t* wbuf, unsigned int& errors);
+__device__ __noinline__ unsigned int tail_run(const FrankLaunch& p, TailGroups<PROD> g, int ns, unsigned int* s_hist,
+                                              uint32_t* wbuf);
 template <int K>
 struct TailShape;
 constexpr int kTailWarps = 8;  // warps of the largest block (256 threads)
@@ -738,10 +743,12 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
     if (p.tail_groups > 0) {
       const bool running = active && !s.done;  // (a group can be done at its start: absorbed)
       const uint32_t alive = __ballot_sync(0xFFFFFFFFu, running);
-      if (__popc(alive) <= p.tail_groups && __any_sync(0xFFFFFFFFu, exhausted) &&
+      if (__popc(alive) <= min(p.tail_groups, kTailSlots) && __any_sync(0xFFFFFFFFu, exhausted) &&
           !__any_sync(0xFFFFFFFFu, running && (BATCH ? p.ens_table[s.ens].thin : p.ens.thin))) {
         if (active && s.done) group_finish<K, PROD>(p, s, BATCH ? p.ens_table[s.ens] : p.ens);
-        tail_run<K, BATCH, PROD, ADAPT>(p, s, running, s_hist, tail_words[threadIdx.x >> 5], errors);
+        int ns = 0;
+        const TailGroups<PROD> g = tail_take<K, BATCH, PROD>(p, s, running, ns);
+        errors |= tail_run<K, BATCH, PROD, ADAPT>(p, g, ns, s_hist, tail_words[threadIdx.x >> 5]);
         break;  // the queue is drained and every group of the warp has finished
       }
     }

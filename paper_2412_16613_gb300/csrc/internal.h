@@ -28,7 +28,9 @@ __host__ __device__ constexpr int bit_length(long long v) {
 }
 
 constexpr int kMaxSnap = 64;
-constexpr int kDefaultTailGroups = 8;  // the one-thread kernel's tail hand-off (FrankLaunch::tail_groups)
+constexpr int kTailSlots = 4;          // the one-thread kernel's tail hand-off: groups a warp hands over at most
+constexpr int kTailDepth = 4;          // steps whose random words it draws together
+constexpr int kDefaultTailGroups = 2;  // FrankLaunch::tail_groups unless an option or the tuner sets it
 constexpr int kHistBins = 65;  // 64 enantiomeric-excess bins + one for L + D == 0
 constexpr int kCounters = 10;
 constexpr int kMaxK = 31;      // random / propensity planes: N_tot (N_tot - 1) / 2 < 2^31
@@ -174,7 +176,7 @@ struct FrankLaunch {
                                   // state-following bound (each step's bound 2^p, p the bit length
                                   // of the largest S_R over the group's live lanes; 2^K its ceiling)
   int tail_groups;                // one-thread Frank kernel: once the work queue is drained, a warp
-                                  // with at most this many running groups (1..8) finishes them with
+                                  // with at most this many running groups (1..kTailSlots) finishes them with
                                   // one run per thread; 0 never
   int stage_offset;               // one-thread Frank kernel with a snapshot dump: the word of dynamic
                                   // shared memory where the per-thread staging rows start; -1: none

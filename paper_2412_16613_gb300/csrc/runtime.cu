@@ -411,7 +411,7 @@ int check_options(const ssa_options& o, std::string* why) {
     return (*why = "word_width must be 0, 32 or 64", SSA_EINVAL);
   if (o.word_width == 64)
     return (*why = "64-lane words (two groups per thread) do not fit a thread's registers", SSA_EUNSUPPORTED);
-  if (o.tail_groups < -1 || o.tail_groups > 8) return (*why = "tail_groups must be in [-1, 8]", SSA_EINVAL);
+  if (o.tail_groups < -1 || o.tail_groups > kTailSlots) return (*why = "tail_groups must be in [-1, 4]", SSA_EINVAL);
   return SSA_OK;
 }
 
@@ -1206,6 +1206,42 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
   c->tuned_layout = win.layout;
   c->tuned_block = win.block;
   c->tuned_products = c->general ? win.products : -1;
+  // Frank's model on one thread per group: the tail hand-off threshold, on the chosen layout
+  if (!c->general && c->opt.tail_groups == 0 && !ctx_warps(c, c->n_runs_total / 32)) {
+    const int old_tail = c->tuned_tail;
+    int best_tail = kDefaultTailGroups;
+    float best_ms = -1.0f;
+    c->opt.step_budget = probe_steps;
+    const int tails[] = {0, 1, 2, kTailSlots};  // 0: off
+    ev[0] = ev[1] = nullptr;
+    if ((e = cudaEventCreate(&ev[0])) != cudaSuccess || (e = cudaEventCreate(&ev[1])) != cudaSuccess)
+      st = cuda_fail(c, e, "tuner events");
+    for (int ti = 0; st == SSA_OK && ti < 4; ++ti) {
+      c->tuned_tail = tails[ti];
+      float ms = -1.0f;
+      for (int rep = 0; rep < 2 && st == SSA_OK; ++rep) {
+        cudaEventRecord(ev[0], c->stream);
+        st = ssa_run(c, t_end, snapshot_times, n_snap);
+        cudaEventRecord(ev[1], c->stream);
+        if (st == SSA_ETIMEOUT) st = SSA_OK;
+        float t = 0.0f;
+        if (st == SSA_OK && ((e = cudaEventSynchronize(ev[1])) != cudaSuccess ||
+                             (e = cudaEventElapsedTime(&t, ev[0], ev[1])) != cudaSuccess))
+          st = cuda_fail(c, e, "tuner timing");
+        if (ms < 0.0f || t < ms) ms = t;
+      }
+      if (st == SSA_OK && (best_ms < 0.0f || ms < best_ms)) {
+        best_ms = ms;
+        best_tail = tails[ti];
+      }
+    }
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    c->opt.step_budget = budget;
+    c->ran = false;
+    c->tuned_tail = st == SSA_OK ? best_tail : old_tail;
+    if (st != SSA_OK) return st;
+  }
   if (choice) {
     choice[0] = win.layout;
     choice[1] = win.block;

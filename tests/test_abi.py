@@ -107,7 +107,7 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
     (dict(reac=F_R, prod=F_P, clock=2), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, word_width=16), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, word_width=64), pkg.SSA_EUNSUPPORTED),
-    (dict(reac=F_R, prod=F_P, tail_groups=9), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, tail_groups=5), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, tail_groups=-2), pkg.SSA_EINVAL),
 ])
 def test_validation_before_any_cuda_call(lib, kw, status):

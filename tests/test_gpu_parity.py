@@ -481,13 +481,13 @@ def test_tail_hand_off_keeps_the_runs(case, block):
     """The one-thread kernel's tail hand-off (the last groups of a warp finished one run per
     thread) gives every run, snapshot, histogram, absorption time and counter of the kernel
     without it, bit for bit: paper's, padded and state-following bounds, every clock, wide n with
-    heavy rejection (N = 46 400), t_end before absorption, and a hand-off threshold of 1 and 8."""
+    heavy rejection (N = 46 400), t_end before absorption, and a hand-off threshold of 1 and 4."""
     kw = dict(TAIL_CASES[case])
     init, n, t_end, seed, snaps = kw.pop("init"), kw.pop("n"), kw.pop("t_end"), kw.pop("seed"), kw.pop("snaps")
     base = gpu_run(init, n, seed=seed, t_end=t_end, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, block_size=block,
                    tail_groups=-1, **kw)
     assert not base["counters"]["layout"] & 16
-    for tail in (8, 1):
+    for tail in (4, 1):
         g = gpu_run(init, n, seed=seed, t_end=t_end, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, block_size=block,
                     tail_groups=tail, **kw)
         assert g["counters"]["layout"] & 16, tail
@@ -503,7 +503,7 @@ def test_tail_hand_off_on_a_batch():
     runs = np.array([100, 2048, 777, 513])
     seeds = np.array([3, 4, 5, 6], dtype=np.uint64)
     out = []
-    for tail in (-1, 8):
+    for tail in (-1, 4):
         o = pkg.ssa_default_options(cuda_stream=torch.cuda.current_stream(), layout=pkg.SSA_LAYOUT_THREAD,
                                     tail_groups=tail, keep_snap_counts=1)
         ctx = pkg.ssa_create_batch(FRANK_R, FRANK_P, init, np.ones((4, 3)), runs, seeds, o)
@@ -530,7 +530,7 @@ def test_tail_hand_off_with_groups_absorbed_at_start():
     init[200:232] = (0, 128, 0)
     snaps = [0.001, 0.01, 0.1]
     base = gpu_run(init, n, seed=5, t_end=np.inf, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, tail_groups=-1)
-    g = gpu_run(init, n, seed=5, t_end=np.inf, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, tail_groups=8)
+    g = gpu_run(init, n, seed=5, t_end=np.inf, snaps=snaps, layout=pkg.SSA_LAYOUT_THREAD, tail_groups=4)
     assert g["counters"]["layout"] & 16
     for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts", "ens_absorbed"):
         assert np.array_equal(g[k], base[k]), k
