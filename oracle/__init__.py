@@ -53,7 +53,7 @@ class Problem(C.Structure):
         ("precision", C.c_int32), ("thin_bits", C.c_int32), ("t_end", C.c_double),
         ("snap_times", C.POINTER(C.c_double)), ("n_snap", C.c_int32),
         ("step_budget", C.c_int64), ("shared_n", C.c_int32), ("pad_pow2", C.c_int32),
-        ("ensemble_runs", C.c_int64),
+        ("ensemble_runs", C.c_int64), ("lane_clock", C.c_int32),
     ]
 
 
@@ -124,13 +124,13 @@ def frank(k1=1.0, k2=1.0, k3=1.0) -> Network:
 
 
 def _problem(net: Network, n_tot, seed, precision=P64, thin_bits=32, t_end=np.inf,
-             snap_times=(), step_budget=0, shared_n=False, pad_pow2=False, ensemble_runs=0):
+             snap_times=(), step_budget=0, shared_n=False, pad_pow2=False, ensemble_runs=0, lane_clock=False):
     snaps = np.ascontiguousarray(snap_times, dtype=np.float64)
     p = Problem(net.n_species, net.n_reactions, _ptr(net.reactants, C.c_int32),
                 _ptr(net.products, C.c_int32), _ptr(net.rates, C.c_double), int(n_tot),
                 int(seed) & (2**64 - 1), int(precision), int(thin_bits), float(t_end),
                 _ptr(snaps, C.c_double) if len(snaps) else None, len(snaps), int(step_budget),
-                1 if shared_n else 0, int(pad_pow2), int(ensemble_runs))
+                1 if shared_n else 0, int(pad_pow2), int(ensemble_runs), 1 if lane_clock else 0)
     p._keep = (net, snaps)  # keep the arrays alive as long as the struct
     return p
 
@@ -176,7 +176,7 @@ def ee_bin(L, D):
 
 def run(net: Network, init, n_runs=None, *, seed=0, precision=P64, thin_bits=32, t_end=np.inf,
         snap_times=(), step_budget=0, first_run=0, run_ids=None, threads=None,
-        want_snapshots=True, check=True, shared_n=False, pad_pow2=False, ensemble_runs=None):
+        want_snapshots=True, check=True, shared_n=False, pad_pow2=False, ensemble_runs=None, lane_clock=False):
     """Run the oracle on runs first_run .. first_run+n_runs-1 (or on run_ids).
 
     init: [S] shared initial counts or [n_runs][S] per-run counts.
@@ -184,6 +184,8 @@ def run(net: Network, init, n_runs=None, *, seed=0, precision=P64, thin_bits=32,
     pad_pow2: 1 (or True): the uniformisation bound is 2^K (null events fill the gap above
         lambda_int); 2: the bound follows the group's state, 2^p with p the bit length of the
         largest S_R over the group's live runs, and each run comes out of its whole group.
+    lane_clock: every run has its own clock (its waiting times from its own stream) instead of
+        one clock per group of 32 runs.
     ensemble_runs (pad_pow2 = 2): runs in the ensemble, which fixes the lanes of its last group;
         default first_run + n_runs without run_ids, else every group full.  A per-run init then
         holds one row per run of the ensemble, indexed by run.
@@ -207,7 +209,7 @@ def run(net: Network, init, n_runs=None, *, seed=0, precision=P64, thin_bits=32,
             raise ValueError("pad_pow2 = 2 with per-run counts needs a row for every run of each group")
     n_tot = int(init.reshape(-1, net.n_species)[0].sum())
     p = _problem(net, n_tot, seed, precision, thin_bits, t_end, snap_times, step_budget, shared_n,
-                 pad_pow2, ensemble_runs)
+                 pad_pow2, ensemble_runs, lane_clock)
     out = (Result * max(n_runs, 1))()
     n_snap = len(snap_times)
     snaps = (np.zeros((n_snap, n_runs, net.n_species), dtype=np.int64)

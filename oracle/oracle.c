@@ -96,6 +96,20 @@ static uint32_t word_at(word_source* ws, uint64_t group, uint64_t step, uint32_t
 
 static uint32_t lane_bit(uint32_t word, int lane) { return (word >> lane) & 1u; }
 
+/* The two waiting-time words of run j at step s under the per-run clock: words 0 and 1 of
+ * Philox4x32-10 with counter (j lo 32, s lo 32, s hi 16 | (j >> 32) << 16 | 1 << 24, 0). */
+static void lane_clock_words(const word_source* ws, int64_t run, int64_t step, uint32_t* w0, uint32_t* w1) {
+  uint32_t ctr[4], out[4];
+  ctr[0] = (uint32_t)((uint64_t)run & 0xFFFFFFFFu);
+  ctr[1] = (uint32_t)((uint64_t)step & 0xFFFFFFFFu);
+  ctr[2] = (uint32_t)(((uint64_t)step >> 32) & 0xFFFFu) | (uint32_t)((((uint64_t)run >> 32) & 0xFFu) << 16) |
+           (1u << 24);
+  ctr[3] = 0u;
+  orc_philox4x32_10(ctr, ws->key, out);
+  *w0 = out[0];
+  *w1 = out[1];
+}
+
 /* ------------------------------------------------------------------------ */
 /* The network: propensities (Eq. equation-as generalised to order <= 2     */
 /* mass action), the uniformisation bound, thinning thresholds.              */
@@ -206,6 +220,8 @@ int orc_derive(const orc_problem* p, orc_derived* d) {
   /* Uniformisation at any bound at or above the largest total propensity samples the same
    * process; padding the bound to 2^K with further null events makes every K-bit n valid. */
   if (p->pad_pow2 < 0 || p->pad_pow2 > 2 || p->ensemble_runs < 0) return ORC_EINVAL;
+  if (p->lane_clock != 0 && p->lane_clock != 1) return ORC_EINVAL;
+  if (p->lane_clock && p->pad_pow2 == 2) return ORC_EINVAL; /* not built */
   if (p->pad_pow2) d->lambda_int = (uint64_t)1 << d->K;
   d->k_max = k_max;
   d->lambda = k_max * (double)d->lambda_int;
@@ -310,19 +326,24 @@ int orc_run(const orc_problem* p, const orc_derived* d, int64_t run_index, const
     }
     out->redraws += attempt;
 
-    /* (2) the waiting time, from the whole words K and K+1 of attempt 0 */
-    uint32_t wk0 = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)K);
+    /* (2) the waiting time, from the whole words K and K+1 of attempt 0 (per-run clock: the
+     * words 0 and 1 of the run's own stream) */
+    uint32_t wk0, wk1;
+    if (p->lane_clock) {
+      lane_clock_words(&ws, run_index, step, &wk0, &wk1);
+    } else {
+      wk0 = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)K);
+      wk1 = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)K + 1);
+    }
     double t_new;
     float t_f_new = 0.0f, c_f_new = 0.0f;
     if (p->precision == ORC_P64) {
-      uint32_t wk1 = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)K + 1);
       uint64_t x = ((uint64_t)wk1 << 21) | (uint64_t)(wk0 >> 11);
       double u = (double)(x + 1) * 0x1p-53;
       double tau = -log(u) / d->lambda;
       t_new = t + tau;
     } else {
       /* the top 24 of the 53 bits above: the fp32 clock is a rounding of the fp64 one */
-      uint32_t wk1 = word_at(&ws, group, (uint64_t)step, 0, 0, (uint32_t)K + 1);
       float u = (float)((wk1 >> 8) + 1u) * 0x1p-24f;
       float tau = -logf(u) * inv_lambda_f;
       if (p->precision == ORC_P32_KAHAN) {

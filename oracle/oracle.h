@@ -23,7 +23,9 @@
  *         with pad_pow2 = 2 the bound of step s is 2^p, p = the bit length of the largest
  *         S_R over the live runs of the group, and n = sum_{i<p} bit_l(w_i) 2^i;
  *   tau = -log(u) / Lambda (Lambda = k_max 2^p with pad_pow2 = 2) from the whole
- *         words w_K, w_{K+1} of attempt 0
+ *         words w_K, w_{K+1} of attempt 0 (with lane_clock = 1, from the words v_0, v_1 of
+ *         run j's own stream: element k of Philox4x32-10(key as above, ctr = (j lo 32,
+ *         s lo 32, s hi 16 | (j >> 32) << 16 | 1 << 24, 0)); so every run has its own clock)
  *         (Eq. equation-tau, with the uniformisation rate of Eq. equation-z):
  *         fp64 u = (x + 1) 2^-53 with x = w_{K+1} << 21 | w_K >> 11; the fp32
  *         modes take u = ((w_{K+1} >> 8) + 1) 2^-24, the top 24 of those bits;
@@ -83,6 +85,10 @@ typedef struct {
                                32 runs of a group are stepped together */
   int64_t ensemble_runs;    /* pad_pow2 = 2: runs in the ensemble, which fixes how many lanes the
                                last group holds; 0 = every group holds 32 runs */
+  int32_t lane_clock;       /* 0: one clock per group of 32 runs (the waiting-time words K, K+1 of
+                               the group's stream); 1: every run has its own clock, the waiting time
+                               of run j at step s from words 0 and 1 of its own stream (below).
+                               Not with pad_pow2 = 2 */
 } orc_problem;
 
 /* Derived constants of a problem, computed from their definitions. */

@@ -739,3 +739,97 @@ def test_state_following_bound_group_consistency(orc):
     assert np.all(a["final_counts"].sum(1) == 160) and np.all(a["redraws"] == 0)
     with pytest.raises(RuntimeError):
         orc.run(orc.frank(), (40, 40, 80), run_ids=[70], seed=5, pad_pow2=2, ensemble_runs=70)
+
+
+# --------------------------------------------------------------------------
+# The per-run clock: every run draws its waiting times from its own stream
+# --------------------------------------------------------------------------
+def test_lane_clock_waiting_times_are_independent_exponentials(orc):
+    """Eq. equation-tau per run: the first waiting time of every run is Exp(Lambda), and the 32
+    runs of a group no longer share it (the group clock gives them one value)."""
+    N, groups = 64, 4000
+    Z = N * (N - 1) // 2
+    r = orc.run(orc.frank(), (16, 16, 32), groups * 32, seed=3, step_budget=1, check=False, lane_clock=True)
+    tau = r["t_last"] * Z
+    assert abs(tau.mean() - 1.0) < 4.5 / math.sqrt(len(tau))
+    assert stats.kstest(tau, "expon").pvalue > 1e-4
+    by_group = tau.reshape(groups, 32)
+    assert np.all(np.ptp(by_group, axis=1) > 0)
+    c = np.corrcoef(by_group[:, 0], by_group[:, 1])[0, 1]
+    assert abs(c) < 4.5 / math.sqrt(groups), c
+    g = orc.run(orc.frank(), (16, 16, 32), 64, seed=3, step_budget=1, check=False)
+    assert np.all(g["t_last"].reshape(2, 32) == g["t_last"].reshape(2, 32)[:, :1])
+
+
+@pytest.mark.parametrize("pad", [False, True])
+def test_master_equation_lane_clock(orc, pad):
+    """Every run of every group (40 000 runs in 1250 groups, all lanes) against the master
+    equation at N = 12: with its own clock each run is an exact sample path and the runs of a
+    group are independent samples."""
+    N, init = 12, (3, 3, 6)
+    st, index, Q = _frank_me(N)
+    snaps = [0.02, 0.05, 0.1, 0.2, 0.4]
+    runs = 40_000
+    r = orc.run(orc.frank(), init, runs, seed=27, t_end=0.5, snap_times=snaps, pad_pow2=pad, lane_clock=True)
+    p0 = np.zeros(len(st))
+    p0[index[init]] = 1.0
+    for s, t in enumerate(snaps):
+        p = me.distribution(Q, p0, t)
+        obs = np.zeros(len(st))
+        for c in r["snap_counts"][s]:
+            obs[index[tuple(int(x) for x in c)]] += 1
+        exp = p * runs
+        big = exp >= 5
+        o = np.append(obs[big], obs[~big].sum())
+        e = np.append(exp[big], exp[~big].sum())
+        if e[-1] < 5:
+            o, e = o[:-1], e[:-1]
+            e *= o.sum() / e.sum()
+        stat, pval = stats.power_divergence(o, e, lambda_="log-likelihood")
+        assert pval > 1e-4, (t, pval)
+
+
+def test_lane_clock_closed_form(orc):
+    """L+D->2A alone from L = D = m0: T = sum_{m=1}^{m0} Exp(m^2) for every run, over all 32
+    runs of each group; the jump chain is the group clock's, step for step."""
+    net = orc.Network([[1, 1, 0]], [[0, 0, 2]], [1.0])
+    m0, A0, groups = 8, 4, 2000
+    mean = sum(1 / m**2 for m in range(1, m0 + 1))
+    var = sum(1 / m**4 for m in range(1, m0 + 1))
+    lane = orc.run(net, (m0, m0, A0), groups * 32, seed=45, t_end=np.inf, lane_clock=True)
+    n = len(lane["t_abs"])
+    assert abs(lane["t_abs"].mean() - mean) < 4.5 * math.sqrt(var / n)
+    assert abs(lane["t_abs"].var() - var) < 0.05 * var
+    grp = orc.run(net, (m0, m0, A0), groups * 32, seed=45, t_end=np.inf)
+    assert np.array_equal(lane["steps"], grp["steps"])  # the jump chain does not depend on the clock
+    assert np.array_equal(lane["final_counts"], grp["final_counts"])
+
+
+def test_lane_clock_removes_the_correlation_within_a_group(orc):
+    """N = 2 from (1, 1, 0): Z = 1 and the one reaction fires at the first step, so a run's
+    absorption time is its first waiting time, Exp(1).  Under the group clock the 32 runs of a
+    group share it (correlation 1); under the per-run clock they are independent Exp(1)."""
+    groups = 3000
+    grp = orc.run(orc.frank(), (1, 1, 0), groups * 32, seed=46, t_end=np.inf)
+    tg = grp["t_abs"].reshape(groups, 32)
+    assert np.all(tg == tg[:, :1])
+    lane = orc.run(orc.frank(), (1, 1, 0), groups * 32, seed=46, t_end=np.inf, lane_clock=True)
+    tl = lane["t_abs"].reshape(groups, 32)
+    assert stats.kstest(lane["t_abs"], "expon").pvalue > 1e-4
+    for a, b in ((0, 1), (5, 31)):
+        c = np.corrcoef(tl[:, a], tl[:, b])[0, 1]
+        assert abs(c) < 4.5 / math.sqrt(groups), (a, b, c)
+
+
+def test_lane_clock_stream_layout(orc):
+    """The per-run waiting-time words are elements 0 and 1 of Philox4x32-10 with counter
+    (j lo 32, s lo 32, s hi 16 | (j >> 32) << 16 | 1 << 24, 0): one step of run j, checked
+    against the Philox block function called directly."""
+    seed, N = 0x1234_5678_9ABC, 64
+    Z = N * (N - 1) // 2
+    for j in (0, 31, 32 * 1000 + 7):
+        r = orc.run(orc.frank(), (16, 16, 32), run_ids=[j], seed=seed, step_budget=1, check=False, lane_clock=True)
+        w = orc.philox4x32_10([j & 0xFFFFFFFF, 0, ((j >> 32) & 0xFF) << 16 | 1 << 24, 0],
+                              [seed & 0xFFFFFFFF, seed >> 32])
+        u = ((w[1] << 21 | w[0] >> 11) + 1) * 2.0**-53
+        assert r["t_last"][0] == pytest.approx(-math.log(u) / Z, rel=1e-15)
