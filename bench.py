@@ -554,6 +554,18 @@ def main():
         if rank == 0:
             sample = args.cpu_sample if WORKLOAD == "c2" else max(64, args.cpu_sample // 8)
             result["cpu_baseline"] = cpu_baseline(sample, os.cpu_count() or 1)
+    # ---- the same workload with a clock per run (SSA_CLOCK_LANE): what independent runs in a group cost
+    if not args.no_baselines and WORKLOAD == "c2" and ENGINE == 0 and PAD in (0, 1):
+        ol = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision, pad_pow2=PAD,
+                                     first_run=first_run, clock=pkg.SSA_CLOCK_LANE)
+        cl = pkg.ssa_create(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, [1.0, 1.0, 1.0], np.array(INIT), RUNS_PER_GPU,
+                            SEED, ol)
+        msl, vall, cntl = time_runs(cl, 2)
+        pkg.ssa_destroy(cl)
+        result["lane_clock"] = {"ms_per_step": msl, "value": vall * world, "unit": "lane-reactions/s",
+                                "relative_to_group_clock": result["ms_per_step"] / msl,
+                                "layout": layout_name(int(cntl[9]))}
+
     # ---- the precision workload (N_tot = 10 000, 2^22 runs), a few steps per bound, with its roofline
     if args.c4_steps > 0 and WORKLOAD == "c2" and ENGINE == 0 and PRECISION == 0:
         result["c4"] = {}

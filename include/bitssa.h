@@ -154,7 +154,19 @@ typedef struct {
                                 every mode. */
   int32_t clock;             /* SSA_CLOCK_GROUP (default): the 32 runs of a group share one clock (one
                                 waiting time per group and step, the paper's one tau for all copies,
-                                end of Sec. 4).  SSA_CLOCK_LANE: every run has its own clock */
+                                end of Sec. 4, Eq. equation-tau): each run is an exact sample path, but
+                                the runs of a group are not independent of each other.
+                                SSA_CLOCK_LANE: every run has its own clock: run j's waiting time at
+                                step s comes from words 0 and 1 of its own Philox4x32-10 stream (key
+                                the seed, counter (j lo 32, s lo 32, s hi 16 | (j >> 32) << 16 |
+                                1 << 24, 0)), with u taken from them as for the group clock; it keeps
+                                its own snapshots and stops alone at t_end, and the runs of a group are
+                                independent.  The integer steps are those of the group clock.  About
+                                four times the work per step (a Philox call and a clock per run).
+                                Frank's model, single ensembles, one thread per group in blocks of at
+                                most 128 threads (544 bytes of shared memory per thread), the paper's or
+                                the padded bound (SSA_LAYOUT_AUTO takes it; otherwise
+                                SSA_EUNSUPPORTED) */
   int32_t word_width;        /* lanes per word: 0 (default) or 32.  64 (two groups per thread) gives
                                 SSA_EUNSUPPORTED: a thread's registers hold one group's state */
   int32_t tail_groups;       /* one-thread layout of Frank's model: once every group has started, a warp

@@ -16,11 +16,12 @@
 namespace bitssa {
 
 // variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64), bit 2 = the
-// state-following bound (FrankLaunch::adapt)
+// state-following bound (FrankLaunch::adapt), bit 3 = per-run clocks (FrankLaunch::lane_clock,
+// single ensembles only: variants 8 and 10)
 namespace {
 template <typename F>
 int with_kernel(int variant, F f) {
-  switch (variant & 7) {
+  switch (variant & 15) {
     case 0: return f(frank_kernel<BITSSA_K, false, false, false>);
     case 1: return f(frank_kernel<BITSSA_K, true, false, false>);
     case 2: return f(frank_kernel<BITSSA_K, false, true, false>);
@@ -28,7 +29,9 @@ int with_kernel(int variant, F f) {
     case 4: return f(frank_kernel<BITSSA_K, false, false, true>);
     case 5: return f(frank_kernel<BITSSA_K, true, false, true>);
     case 6: return f(frank_kernel<BITSSA_K, false, true, true>);
-    default: return f(frank_kernel<BITSSA_K, true, true, true>);
+    case 7: return f(frank_kernel<BITSSA_K, true, true, true>);
+    case 8: return f(frank_kernel<BITSSA_K, false, false, false, true>);
+    default: return f(frank_kernel<BITSSA_K, false, true, false, true>);
   }
 }
 }  // namespace
@@ -36,7 +39,8 @@ int with_kernel(int variant, F f) {
 int BITSSA_CAT(frank_launch_k, BITSSA_K)(const FrankLaunch& p, int grid, int block, int smem,
                                           void* stream) {
   const cudaStream_t st = (cudaStream_t)stream;
-  const int variant = (p.ens_table ? 1 : 0) | (p.precision == kP64 ? 2 : 0) | (p.adapt ? 4 : 0);
+  const int variant = (p.ens_table ? 1 : 0) | (p.precision == kP64 ? 2 : 0) | (p.adapt ? 4 : 0) |
+                      (p.lane_clock ? 8 : 0);
   return with_kernel(variant, [&](auto kern) {
     kern<<<grid, block, smem, st>>>(p);
     return (int)cudaGetLastError();
@@ -49,9 +53,14 @@ int BITSSA_CAT(frank_occupancy_k, BITSSA_K)(int variant, int block, int smem, in
   return with_kernel(variant, [&](auto kern) {
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return (int)e;
+      if (e != cudaSuccess) {
+        cudaGetLastError();  // the caller reports it; leave no error pending for later calls
+        return (int)e;
+      }
     }
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, block, (size_t)smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, block, (size_t)smem);
+    if (e != cudaSuccess) cudaGetLastError();
+    return (int)e;
   });
 }
 

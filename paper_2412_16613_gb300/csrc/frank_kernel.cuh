@@ -25,7 +25,8 @@
 //      and n keeps its low p planes: nothing is redrawn.
 //   2. Clock: tau ~ Exp(Lambda) (Eq. equation-tau), Lambda = k_max 2^p under
 //      ADAPT.  Snapshots whose time is passed record the state before the event;
-//      passing t_end stops the group.
+//      passing t_end stops the group.  With per-run clocks (template flag LANE) every
+//      run draws its own tau, keeps its own snapshots, and stops alone at t_end.
 //   3. Comparators lt_r = [n < S_r] (borrow chains) and changer words
 //      xi_r = lt_r & ~lt_{r-1} (Eq. equation-changer: the CDF walk of Fig. 2
 //      done for all lanes at once); lanes with n >= S_3 fire a ghost reaction.
@@ -334,6 +335,7 @@ struct GroupState {
   uint32_t L[FrankShape<K>::B], P[FrankShape<K>::WP], U[FrankShape<K>::WP];
   uint32_t R1[FrankShape<K>::WR1], R3[FrankShape<K>::WR3];
   uint32_t live;     // lanes that can still react
+  uint32_t stopped;  // per-run clock: lanes stopped at t_end (they cannot react any more either)
   uint32_t sgroup;   // stream group index
   int nvalid;        // lanes holding a run (the last group may be partial)
   int ens;           // ensemble index
@@ -401,9 +403,62 @@ __device__ __forceinline__ void capture(const FrankLaunch& p, const GroupState<K
   }
 }
 
+// ---------------------------------------------------------------------------
+// Per-run clocks (SSA_CLOCK_LANE).  Each run of a group has its own clock, kept in dynamic shared
+// memory from word p.lane_offset: a 16-byte record per run laid out [lane][thread] (a warp reads
+// 32 consecutive records), holding the product clock's mantissa and exponent, or the fp64 time and
+// the fp32 time with its compensation; then a byte per run, [lane][thread], with the index of its
+// next time point (snapshot, or t_end).  Run j's waiting time at step s comes from words 0 and 1
+// of its own Philox stream, counter (j lo 32, s lo 32, s hi 16 | (j >> 32) << 16 | 1 << 24, 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4* lane_record(const FrankLaunch& p, int lane) {
+  return reinterpret_cast<uint4*>(frank_dyn_smem + p.lane_offset) + lane * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ unsigned char* lane_next(const FrankLaunch& p, int lane) {
+  return reinterpret_cast<unsigned char*>(frank_dyn_smem + p.lane_offset + 4 * 32 * blockDim.x) +
+         lane * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ uint4 pack_clock(const Clock<true>& c) {
+  return make_uint4((uint32_t)c.M, (uint32_t)(c.M >> 32), (uint32_t)c.E, (uint32_t)((unsigned long long)c.E >> 32));
+}
+__device__ __forceinline__ void unpack_clock(Clock<true>& c, uint4 r) {
+  c.M = ((unsigned long long)r.y << 32) | r.x;
+  c.E = (long long)(((unsigned long long)r.w << 32) | r.z);
+}
+__device__ __forceinline__ uint4 pack_clock(const Clock<false>& c) {
+  const unsigned long long t = (unsigned long long)__double_as_longlong(c.t);
+  return make_uint4((uint32_t)t, (uint32_t)(t >> 32), __float_as_uint(c.t_f), __float_as_uint(c.c_f));
+}
+__device__ __forceinline__ void unpack_clock(Clock<false>& c, uint4 r) {
+  c.t = __longlong_as_double((long long)(((unsigned long long)r.y << 32) | r.x));
+  c.t_f = __uint_as_float(r.z);
+  c.c_f = __uint_as_float(r.w);
+}
+__device__ __forceinline__ uint4 lane_clock_counter(unsigned long long run, unsigned long long step) {
+  return make_uint4((uint32_t)run, (uint32_t)step,
+                    ((uint32_t)(step >> 32) & 0xFFFFu) | (((uint32_t)(run >> 32) & 0xFFu) << 16) | (1u << 24), 0u);
+}
+
+// The current state of lane l into snapshot `snap` (histogram and per-run counts).
+template <int K, bool PROD>
+__device__ __forceinline__ void capture_lane(const FrankLaunch& p, const GroupState<K, PROD>& s, const Ensemble& e,
+                                             int snap, unsigned int* s_hist, int l) {
+  using Sh = FrankShape<K>;
+  int cl, cd, ca;
+  lane_counts<Sh::B, Sh::WP>(s.L, s.U, e.n_tot, l, cl, cd, ca);
+  if (s_hist) atomicAdd(&s_hist[snap * kHistBins + ee_bin(cl, cd)], 1u);
+  else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + ee_bin(cl, cd)], 1ull);
+  if (p.snap_counts) {
+    int* o = p.snap_counts + ((long long)snap * p.n_runs_total + group_row0(s, e) + l) * p.n_species;
+    o[p.perm[0]] = cl;
+    o[p.perm[1]] = cd;
+    o[p.perm[2]] = ca;
+  }
+}
+
 // Set up group `group_local` of ensemble `e`: initial planes, cumulative propensities by
 // bit-sliced products, the linear forms, the runs that start absorbed.
-template <int K, bool PROD>
+template <int K, bool PROD, bool LANE = false>
 __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e,
                                            const Threshold* thr, long long group_local, int ens_index,
                                            unsigned int* s_hist) {
@@ -502,14 +557,23 @@ __device__ __forceinline__ void group_init(const FrankLaunch& p, GroupState<K, P
   s.clk.aim(thr[0]);
   s.reactions = s.lane_steps = 0;
   s.redraws = 0;
+  s.stopped = 0u;
   s.done = s.live == 0u;
-  if (s.done)
+  if constexpr (LANE) {  // every run's clock at t = 0, aimed at the first time point
+    Clock<PROD> c;
+    c.reset();
+    for (int l = 0; l < 32; ++l) {
+      *lane_record(p, l) = pack_clock(c);
+      *lane_next(p, l) = 0;
+    }
+  } else if (s.done) {
     for (; s.snap < p.n_snap; ++s.snap) capture<K, PROD>(p, s, e, s.snap, s_hist);
+  }
 }
 
 // One group step (see the file header).  Never leaves the caller's loop: a group that
 // stops sets s.done.
-template <int K, bool PROD, bool ADAPT>
+template <int K, bool PROD, bool ADAPT, bool LANE = false>
 __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e,
                                            const Threshold* thr, unsigned int* s_hist, unsigned int& errors) {
   using Sh = FrankShape<K>;
@@ -558,26 +622,71 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   }
 
   // (2) the clock: the candidate time of this step's event, snapshots, t_end
-  Clock<PROD> nx;
-  bool crossed;
-  if constexpr (ADAPT) crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision, j);
-  else crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision);
-  while (crossed) {
-    if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
-      s.done = true;
-      return;
+  if constexpr (LANE) {
+    // every live run advances its own clock; a run whose event lies beyond t_end stops
+    uint32_t stop = 0u;
+    const unsigned long long run0 = (unsigned long long)s.sgroup * 32u;
+    for (uint32_t m = s.live; m; m &= m - 1u) {
+      const int l = __ffs((int)m) - 1;
+      const uint4 r = philox4x32_10(lane_clock_counter(run0 + (unsigned)l, s.step), key);
+      uint4* rec = lane_record(p, l);
+      unsigned char* nxt = lane_next(p, l);
+      int k = *nxt;
+      Clock<PROD> c, nc;
+      unpack_clock(c, *rec);
+      c.aim(thr[k]);
+      bool crossed = clock_advance(c, nc, r.x, r.y, e, precision);
+      while (crossed) {
+        if (k >= p.n_snap) {  // t_end passed: the run's event is not applied
+          stop |= 1u << l;
+          break;
+        }
+        capture_lane<K, PROD>(p, s, e, k, s_hist, l);
+        ++k;
+        nc.aim(thr[k]);
+        if constexpr (PROD) crossed = clock_crosses(nc);
+        else crossed = clock_crosses(nc, precision);
+      }
+      *nxt = (unsigned char)k;
+      if (!((stop >> l) & 1u)) *rec = pack_clock(nc);
     }
-    capture<K, PROD>(p, s, e, s.snap, s_hist);
-    ++s.snap;
-    nx.aim(thr[s.snap]);
-    if constexpr (PROD) crossed = clock_crosses(nx);
-    else crossed = clock_crosses(nx, precision);
+    if (stop) {
+      s.lane_steps += (unsigned long long)__popc(stop) * s.step;
+      s.live &= ~stop;
+      s.stopped |= stop;
+      if (!s.live) {
+        s.done = true;
+        return;
+      }
+    }
+  } else {
+    Clock<PROD> nx;
+    bool crossed;
+    if constexpr (ADAPT) crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision, j);
+    else crossed = clock_advance(s.clk, nx, w[K], w[K + 1], e, precision);
+    while (crossed) {
+      if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
+        s.done = true;
+        return;
+      }
+      capture<K, PROD>(p, s, e, s.snap, s_hist);
+      ++s.snap;
+      nx.aim(thr[s.snap]);
+      if constexpr (PROD) crossed = clock_crosses(nx);
+      else crossed = clock_crosses(nx, precision);
+    }
+    s.clk = nx;
   }
-  s.clk = nx;
 
   // (3) changer words: xi_r = [S_{r-1} <= n < S_r].  A lane that cannot react has S_r = 0
-  // for every reaction with k_r > 0, so only reactions that thinning rejects can be picked.
+  // for every reaction with k_r > 0, so only reactions that thinning rejects can be picked
+  // (with per-run clocks, a run stopped at t_end is masked out).
   uint32_t x1 = lt1, x2 = lt2 & ~lt1, x3 = lt3 & ~lt2;
+  if constexpr (LANE) {
+    x1 &= s.live;
+    x2 &= s.live;
+    x3 &= s.live;
+  }
 
   // (4) thinning for k_r < k_max
   if (e.thin)
@@ -633,26 +742,48 @@ __device__ __forceinline__ void group_step(const FrankLaunch& p, GroupState<K, P
   const uint32_t now_live = live_lanes(s, e) & s.live;
   uint32_t newly = s.live & ~now_live;
   if (newly) {
-    const double tn = s.clk.time(e, precision);
     s.lane_steps += (unsigned long long)__popc(newly) * s.step;
-    while (newly) {
-      const int l = __ffs(newly) - 1;
-      newly &= newly - 1;
-      p.t_abs[group_row0(s, e) + l] = tn;
+    if constexpr (LANE) {  // each run's own clock gives its absorption time
+      while (newly) {
+        const int l = __ffs(newly) - 1;
+        newly &= newly - 1;
+        Clock<PROD> c;
+        unpack_clock(c, *lane_record(p, l));
+        p.t_abs[group_row0(s, e) + l] = c.time(e, precision);
+      }
+    } else {
+      const double tn = s.clk.time(e, precision);
+      while (newly) {
+        const int l = __ffs(newly) - 1;
+        newly &= newly - 1;
+        p.t_abs[group_row0(s, e) + l] = tn;
+      }
     }
     s.live = now_live;
     if (!s.live) {
       s.done = true;
-      for (; s.snap < p.n_snap; ++s.snap) capture<K, PROD>(p, s, e, s.snap, s_hist);
+      if constexpr (!LANE)  // (per-run clocks: each absorbed run fills its own, at the end)
+        for (; s.snap < p.n_snap; ++s.snap) capture<K, PROD>(p, s, e, s.snap, s_hist);
     }
   }
 }
 
 // Outputs of a finished group: final counts, outcomes, per-ensemble tallies, counters.
-template <int K, bool PROD>
-__device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e) {
+template <int K, bool PROD, bool LANE = false>
+__device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K, PROD>& s, const Ensemble& e,
+                                             unsigned int* s_hist = nullptr) {
   using Sh = FrankShape<K>;
   unsigned long long outc[4] = {0, 0, 0, 0};
+  uint32_t unabsorbed = s.live;
+  if constexpr (LANE) {
+    unabsorbed |= s.stopped;
+    // an absorbed run keeps its state for ever: it fills the snapshots its clock had not reached
+    const uint32_t valid = s.nvalid >= 32 ? 0xFFFFFFFFu : ((1u << s.nvalid) - 1u);
+    for (uint32_t m = valid & ~unabsorbed; m; m &= m - 1u) {
+      const int l = __ffs((int)m) - 1;
+      for (int k = *lane_next(p, l); k < p.n_snap; ++k) capture_lane<K, PROD>(p, s, e, k, s_hist, l);
+    }
+  }
   for (int l = 0; l < s.nvalid; ++l) {
     int cl, cd, ca;
     lane_counts<Sh::B, Sh::WP>(s.L, s.U, e.n_tot, l, cl, cd, ca);
@@ -661,7 +792,7 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
     o[p.perm[1]] = cd;
     o[p.perm[2]] = ca;
     signed char oc = -1;
-    if (!((s.live >> l) & 1u)) {
+    if (!((unabsorbed >> l) & 1u)) {
       const int nz = (cl != 0) + (cd != 0) + (ca != 0);
       oc = nz == 1 ? (signed char)(cl ? p.perm[0] : (cd ? p.perm[1] : p.perm[2])) : (signed char)-2;
       outc[nz == 1 ? (int)oc : 3] += 1;  // [3] also counts absorbed-with-several
@@ -683,7 +814,7 @@ __device__ __forceinline__ void group_finish(const FrankLaunch& p, GroupState<K,
   atomicAdd(&p.counters[kReactions], s.reactions);
   atomicAdd(&p.counters[kNullLaneSteps], s.lane_steps - s.reactions);
   if (s.redraws) atomicAdd(&p.counters[kRedrawRounds], (unsigned long long)s.redraws);
-  atomicAdd(&p.counters[kAbsorbed], (unsigned long long)__popc(valid & ~s.live));
+  atomicAdd(&p.counters[kAbsorbed], (unsigned long long)__popc(valid & ~unabsorbed));
   atomicAdd(&p.counters[kGroupsDone], 1ull);
   atomicMax(&p.counters[kMaxGroupSteps], s.step);
 }
@@ -709,7 +840,7 @@ constexpr int kTailWarps = 8;  // warps of the largest block (256 threads)
 // kernel parameters (warp-uniform); batches from a table.  Once the queue is drained, a warp
 // whose running groups are few enough hands them to tail_run (frank_tail.cuh), which finishes
 // them with one run per thread.
-template <int K, bool BATCH, bool PROD, bool ADAPT>
+template <int K, bool BATCH, bool PROD, bool ADAPT, bool LANE = false>
 __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ FrankLaunch p) {
   __shared__ __align__(16) uint32_t tail_words[kTailWarps][TailShape<K>::kWarpWords];
   unsigned int* const s_hist_mem = frank_dyn_smem;
@@ -730,7 +861,7 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
       if (item >= p.item_end) {
         exhausted = true;
       } else if (!BATCH) {
-        group_init<K, PROD>(p, s, p.ens, thr, item, 0, s_hist);
+        group_init<K, PROD, LANE>(p, s, p.ens, thr, item, 0, s_hist);
         active = true;
       } else {
         const int ei = p.item_ens[item];
@@ -740,7 +871,7 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
       }
     }
     if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
-    if (p.tail_groups > 0) {
+    if (!LANE && p.tail_groups > 0) {
       const bool running = active && !s.done;  // (a group can be done at its start: absorbed)
       const uint32_t alive = __ballot_sync(0xFFFFFFFFu, running);
       if (__popc(alive) <= min(p.tail_groups, kTailSlots) && __any_sync(0xFFFFFFFFu, exhausted) &&
@@ -754,9 +885,9 @@ __global__ void __launch_bounds__(256) frank_kernel(const __grid_constant__ Fran
     }
     if (active) {
       const Ensemble& e = BATCH ? p.ens_table[s.ens] : p.ens;
-      if (!s.done) group_step<K, PROD, ADAPT>(p, s, e, thr, s_hist, errors);
+      if (!s.done) group_step<K, PROD, ADAPT, LANE>(p, s, e, thr, s_hist, errors);
       if (s.done) {
-        group_finish<K, PROD>(p, s, e);
+        group_finish<K, PROD, LANE>(p, s, e, s_hist);
         active = false;
       }
     }

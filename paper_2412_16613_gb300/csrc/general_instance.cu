@@ -46,9 +46,14 @@ int BITSSA_CAT(general_occupancy_k, BITSSA_K)(int variant, int block, int smem, 
   return with_kernel(variant, [&](auto kern) {
     if (smem > 48 * 1024) {
       const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      if (e != cudaSuccess) return (int)e;
+      if (e != cudaSuccess) {
+        cudaGetLastError();  // the caller reports it; leave no error pending for later calls
+        return (int)e;
+      }
     }
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, block, (size_t)smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, block, (size_t)smem);
+    if (e != cudaSuccess) cudaGetLastError();
+    return (int)e;
   });
 }
 

@@ -175,6 +175,9 @@ struct FrankLaunch {
   int adapt;                      // one-thread Frank kernel: 1 runs the instantiation with the
                                   // state-following bound (each step's bound 2^p, p the bit length
                                   // of the largest S_R over the group's live lanes; 2^K its ceiling)
+  int lane_clock;                 // one-thread Frank kernel, single ensemble: 1 gives every run its own
+                                  // clock (its records in dynamic shared memory from word lane_offset)
+  int lane_offset;
   int tail_groups;                // one-thread Frank kernel: once the work queue is drained, a warp
                                   // with at most this many running groups (1..kTailSlots) finishes them with
                                   // one run per thread; 0 never

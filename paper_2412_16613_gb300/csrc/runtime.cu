@@ -406,7 +406,14 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.step_budget < 0) return (*why = "step_budget must be >= 0", SSA_EINVAL);
   if (o.first_run < 0 || (o.first_run % 32) != 0) return (*why = "first_run must be a multiple of 32", SSA_EINVAL);
   if (o.clock != SSA_CLOCK_GROUP && o.clock != SSA_CLOCK_LANE) return (*why = "unknown clock", SSA_EINVAL);
-  if (o.clock == SSA_CLOCK_LANE) return (*why = "the per-run clock is not built", SSA_EUNSUPPORTED);
+  if (o.clock == SSA_CLOCK_LANE &&
+      (o.engine != SSA_ENGINE_BITSLICED || o.layout == SSA_LAYOUT_WARPS || o.shared_n || o.pad_pow2 == 2))
+    return (*why = "the per-run clock (SSA_CLOCK_LANE) runs Frank's model on one thread per group, with the "
+                   "paper's or the padded bound",
+            SSA_EUNSUPPORTED);
+  if (o.clock == SSA_CLOCK_LANE && o.block_size > 128)
+    return (*why = "per-run clocks keep 544 bytes of shared memory per thread: blocks of at most 128 threads",
+            SSA_EUNSUPPORTED);
   if (o.word_width != 0 && o.word_width != 32 && o.word_width != 64)
     return (*why = "word_width must be 0, 32 or 64", SSA_EINVAL);
   if (o.word_width == 64)
@@ -501,6 +508,8 @@ int create_common(const int32_t* reac, const int32_t* prod, int32_t S, int32_t R
     return fail(nullptr, SSA_EUNSUPPORTED, "a general network runs one thread per group");
   if (general && o.pad_pow2 == 2)
     return fail(nullptr, SSA_EUNSUPPORTED, "the state-following bound (pad_pow2 = 2) runs Frank's model only");
+  if (general && o.clock == SSA_CLOCK_LANE)
+    return fail(nullptr, SSA_EUNSUPPORTED, "the per-run clock (SSA_CLOCK_LANE) runs Frank's model only");
   ssa_ctx* c = new ssa_ctx();
   c->opt = o;
   c->S = S;
@@ -601,6 +610,7 @@ bool use_warps_layout(const ssa_options& o, long long groups, int sm_count) {
 // rule above.
 bool ctx_warps(const ssa_ctx* c, long long groups) {
   if (c->general) return false;      // the general kernel has one layout
+  if (c->opt.clock == SSA_CLOCK_LANE) return false;  // per-run clocks are built into one thread only
   if (c->opt.pad_pow2 == 2) return false;  // the state-following bound is built into one thread only
   if (c->opt.shared_n) return true;  // Frank's kernels: the shared draw is built into three warps only
   if (c->opt.layout == SSA_LAYOUT_AUTO && c->tuned_layout == SSA_LAYOUT_THREAD) return false;
@@ -697,6 +707,9 @@ int launch_runs(ssa_ctx* c) {
   // the tail hand-off of the one-thread kernel: a fixed option wins, then the tuner's choice
   fl.tail_groups = c->opt.tail_groups < 0 ? 0 : (c->opt.tail_groups > 0 ? c->opt.tail_groups
                                                  : (c->tuned_tail >= 0 ? c->tuned_tail : kDefaultTailGroups));
+  // per-run clocks: the records follow the histogram and the staging rows (no tail hand-off)
+  fl.lane_clock = c->opt.clock == SSA_CLOCK_LANE ? 1 : 0;
+  if (fl.lane_clock) fl.tail_groups = 0;
   fl.n_runs_total = c->n_runs_total;
   fl.counters = c->d_counters;
   fl.status = c->d_status;
@@ -771,7 +784,13 @@ int launch_runs(ssa_ctx* c) {
       fl.stage_offset = ((smem / (int)sizeof(unsigned int)) + 3) & ~3;
       tsmem = (fl.stage_offset + block * kStageStride) * (int)sizeof(unsigned int);
     }
-    if (frank_max_active_blocks(K, clock_variant | adapt_variant, block, tsmem, &occ) != 0 || occ < 1)
+    int lane_variant = 0;
+    if (fl.lane_clock) {  // 32 records of 16 bytes and 32 bytes of next time points per thread
+      fl.lane_offset = ((tsmem / (int)sizeof(unsigned int)) + 3) & ~3;
+      tsmem = (fl.lane_offset + block * 32 * 4 + block * 32 / 4) * (int)sizeof(unsigned int);
+      lane_variant = 8;
+    }
+    if (frank_max_active_blocks(K, clock_variant | adapt_variant | lane_variant, block, tsmem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the bit-sliced kernel");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
     const long long need = (groups + block - 1) / block;
@@ -972,6 +991,7 @@ int ssa_create_batch(const int32_t* reactants, const int32_t* products, int32_t 
   if (!N0_ens || !rates_ens || !runs_ens || !seed_ens) return bail(SSA_EINVAL, "null batch array");
   if (c->opt.first_run != 0) return bail(SSA_EINVAL, "first_run must be 0 for a batch");
   if (c->opt.engine == SSA_ENGINE_THREAD_PER_RUN) return bail(SSA_EUNSUPPORTED, "batches run on the bit-sliced engines");
+  if (c->opt.clock == SSA_CLOCK_LANE) return bail(SSA_EUNSUPPORTED, "the per-run clock runs single ensembles");
   c->batch = true;
   c->n_ens = n_ens;
   long long offset = 0;
@@ -1152,7 +1172,8 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
   std::vector<Candidate> cands;
   if (!c->general) {
     for (const Candidate& f : frank_cands)
-      if (c->opt.pad_pow2 != 2 || f.layout == SSA_LAYOUT_THREAD) cands.push_back(f);
+      if ((c->opt.pad_pow2 != 2 && c->opt.clock != SSA_CLOCK_LANE) || f.layout == SSA_LAYOUT_THREAD)
+        cands.push_back(f);
   } else
     for (const Candidate& g : general_cands)
       if (c->opt.recompute == 0 || g.products == (c->opt.recompute == 1 ? 1 : 0)) cands.push_back(g);
@@ -1207,7 +1228,8 @@ int ssa_tune(ssa_ctx* c, double t_end, const double* snapshot_times, int32_t n_s
   c->tuned_block = win.block;
   c->tuned_products = c->general ? win.products : -1;
   // Frank's model on one thread per group: the tail hand-off threshold, on the chosen layout
-  if (!c->general && c->opt.tail_groups == 0 && !ctx_warps(c, c->n_runs_total / 32)) {
+  if (!c->general && c->opt.tail_groups == 0 && c->opt.clock != SSA_CLOCK_LANE &&
+      !ctx_warps(c, c->n_runs_total / 32)) {
     const int old_tail = c->tuned_tail;
     int best_tail = kDefaultTailGroups;
     float best_ms = -1.0f;

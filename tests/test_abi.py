@@ -108,6 +108,13 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
     (dict(reac=F_R, prod=F_P, word_width=16), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, word_width=64), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, tail_groups=5), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, clock=pkg.SSA_CLOCK_LANE, layout=pkg.SSA_LAYOUT_WARPS), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, clock=pkg.SSA_CLOCK_LANE, pad_pow2=2), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, clock=pkg.SSA_CLOCK_LANE, shared_n=1), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, clock=pkg.SSA_CLOCK_LANE, engine=pkg.SSA_ENGINE_GENERAL), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, clock=pkg.SSA_CLOCK_LANE, engine=pkg.SSA_ENGINE_THREAD_PER_RUN), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=F_R, prod=F_P, clock=pkg.SSA_CLOCK_LANE, block_size=256), pkg.SSA_EUNSUPPORTED),
+    (dict(reac=[[1, 1], [1, 1]], prod=[[2, 0], [0, 2]], N0=(3, 3), clock=pkg.SSA_CLOCK_LANE), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, tail_groups=-2), pkg.SSA_EINVAL),
 ])
 def test_validation_before_any_cuda_call(lib, kw, status):
@@ -173,7 +180,8 @@ def test_product_path_has_no_cpu_fallback():
 
 
 @pytest.mark.parametrize("kw", [dict(pad_pow2=2, layout=pkg.SSA_LAYOUT_WARPS), dict(pad_pow2=2, shared_n=1),
-                                dict(pad_pow2=2, engine=pkg.SSA_ENGINE_GENERAL), dict(pad_pow2=3)])
+                                dict(pad_pow2=2, engine=pkg.SSA_ENGINE_GENERAL), dict(pad_pow2=3),
+                                dict(clock=pkg.SSA_CLOCK_LANE)])
 def test_batch_validates_the_bound_option(lib, kw):
     """A batch goes through the same option checks, before any CUDA call."""
     init = np.array([[16, 16, 32], [25, 25, 50]])
