@@ -49,8 +49,9 @@ L2_BYTES = 129 * 2**20
 # DRAM bytes (read + write) of one launch of the one-thread bit-sliced kernel on the default
 # workload, from one ncu capture, keyed by a fingerprint of the kernel's sources (below): a
 # kernel changed since its capture has no entry and reports null.
-TRAFFIC_BYTES_PER_LAUNCH = {}
-KERNEL_SOURCES = ("frank_kernel.cuh", "bitslice.cuh", "philox.cuh", "internal.h", "frank_instance.cu")
+KERNEL_SOURCES = ("frank_kernel.cuh", "frank_tail.cuh", "bitslice.cuh", "philox.cuh", "internal.h",
+                  "frank_instance.cu")
+TRAFFIC_BYTES_PER_LAUNCH = {"c23af68050df54d3": 3_193_344 + 1_005_056}
 
 
 def kernel_fingerprint() -> str:
@@ -289,6 +290,9 @@ def main():
                          "power-of-two bound that follows each group's state")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 2],
                     help="0: Frank's kernels; 2: the general-network kernel on the same workload")
+    ap.add_argument("--budget", type=int, default=0,
+                    help="stop every group after this many steps (profiling one phase of a launch; the "
+                         "line then covers that phase only and says so)")
     ap.add_argument("--runs", type=int, default=0,
                     help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
@@ -328,7 +332,7 @@ def main():
     first_run = sharding.weak_shard(RUNS_PER_GPU, rank)[0] if WORKLOAD != "c3" else 0
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                   block_size=args.block, first_run=first_run, layout=args.layout,
-                                  pad_pow2=PAD, engine=ENGINE, tail_groups=args.tail)
+                                  pad_pow2=PAD, engine=ENGINE, tail_groups=args.tail, step_budget=args.budget)
     if WORKLOAD == "c3":
         opt.first_run = 0
         ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],
@@ -343,17 +347,25 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    def run(ctx_, snaps=None):
+        """ssa_run; with --budget every group stops at its budget, which the library reports."""
+        try:
+            pkg.ssa_run(ctx_, T_END, SNAPS if snaps is None else snaps)
+        except pkg.SSAError as e:
+            if not (args.budget and e.status == pkg.SSA_ETIMEOUT):
+                raise
+
     def time_runs(ctx_, steps, snaps=None):
         """One warm-up run, then `steps` runs each timed with CUDA events after an L2 flush:
         mean ms per run, lane-reactions/s, the counters of the last run."""
         snaps = SNAPS if snaps is None else snaps
-        pkg.ssa_run(ctx_, T_END, snaps)
+        run(ctx_, snaps)
         ms, react = [], 0
         for k in range(steps):
             flush.fill_(k + 7)
             a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a_.record(stream)
-            pkg.ssa_run(ctx_, T_END, snaps)
+            run(ctx_, snaps)
             b_.record(stream)
             torch.cuda.synchronize()
             ms.append(a_.elapsed_time(b_))
@@ -362,10 +374,10 @@ def main():
         return statistics.mean(ms), react / (sum(ms) / 1e3), cnt
 
     tuned = None
-    if not args.no_tune and WORKLOAD != "c3" and args.layout == 0 and args.block == 0:
+    if not args.no_tune and not args.budget and WORKLOAD != "c3" and args.layout == 0 and args.block == 0:
         tuned = pkg.ssa_tune(ctx, T_END, SNAPS, probe_steps=0)
     for _ in range(args.warmup):
-        pkg.ssa_run(ctx, T_END, SNAPS)
+        run(ctx)
     barrier()
     # the raw samples go to BENCH_CLOCKS_DIR when it is set (a summary is in the JSON line)
     clocks_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
@@ -378,7 +390,7 @@ def main():
     for k in range(args.steps):
         flush.fill_(k)  # L2 flush, outside the kernel's event pair
         ev[k][0].record(stream)
-        pkg.ssa_run(ctx, T_END, SNAPS)
+        run(ctx)
         ev[k][1].record(stream)
         c = pkg.ssa_fetch(ctx, pkg.SSA_FIELD_COUNTERS)
         reactions += int(c[2])
@@ -454,6 +466,10 @@ def main():
               "tuned": None if tuned is None else {"layout": {0: "rule", 1: "thread", 2: "warps"}[tuned[0]],
                                                    "block": tuned[1]}}
 
+    if args.budget:  # a profiling line: the first args.budget steps of every group only
+        result["config"]["step_budget"] = args.budget
+        result["config"]["workload"] += f"_first{args.budget}steps"
+
     # ---- end to end through the C ABI with host buffers (create from host arrays, run, read every
     # per-run output into pinned host memory, destroy), rank-local
     pinned = {f: torch.empty(pkg.ssa_field_bytes(ctx, f), dtype=torch.uint8, pin_memory=True)
@@ -478,7 +494,7 @@ def main():
         else:
             c2 = pkg.ssa_create(host_in["reac"], host_in["prod"], host_in["rates"], host_in["init"], RUNS_PER_GPU,
                                 SEED, opt)
-        pkg.ssa_run(c2, T_END, SNAPS)
+        run(c2)
         for f, t in pinned.items():
             pkg.ssa_fetch(c2, f, t.numpy())
         e2e_react += int(pkg.ssa_fetch(c2, pkg.SSA_FIELD_COUNTERS)[2])
