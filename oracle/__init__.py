@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_LATTICE = os.path.join(_HERE, "lattice.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
@@ -35,11 +36,11 @@ MAX_REACTIONS = 8
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (no fp contraction, so hosts agree)."""
     stale = (not os.path.exists(_LIB)) or any(
-        os.path.getmtime(f) > os.path.getmtime(_LIB) for f in (_SRC, _HDR))
+        os.path.getmtime(f) > os.path.getmtime(_LIB) for f in (_SRC, _SRC_LATTICE, _HDR))
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm", "-lpthread"]
+               "-Wall", "-Wextra", "-o", tmp, _SRC, _SRC_LATTICE, "-lm", "-lpthread"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -54,6 +55,22 @@ class Problem(C.Structure):
         ("snap_times", C.POINTER(C.c_double)), ("n_snap", C.c_int32),
         ("step_budget", C.c_int64), ("shared_n", C.c_int32), ("pad_pow2", C.c_int32),
         ("ensemble_runs", C.c_int64), ("lane_clock", C.c_int32),
+    ]
+
+
+class Lattice(C.Structure):
+    _fields_ = [
+        ("lx", C.c_int32), ("ly", C.c_int32), ("rates", C.POINTER(C.c_double)), ("hop", C.c_double),
+        ("seed", C.c_uint64), ("precision", C.c_int32), ("thin_bits", C.c_int32), ("t_end", C.c_double),
+        ("snap_times", C.POINTER(C.c_double)), ("n_snap", C.c_int32), ("step_budget", C.c_int64),
+    ]
+
+
+class LatticeResult(C.Structure):
+    _fields_ = [
+        ("t_homochiral", C.c_double), ("outcome", C.c_int32), ("status", C.c_int32), ("steps", C.c_int64),
+        ("reactions", C.c_int64), ("hops", C.c_int64), ("cap_bits", C.c_int32), ("pad", C.c_int32),
+        ("margin", C.c_double),
     ]
 
 
@@ -95,6 +112,10 @@ def lib():
                                        C.c_int64, C.POINTER(C.c_int64), C.c_int32,
                                        C.POINTER(Result), C.POINTER(C.c_int64), C.c_int32]
             L.orc_run_many.restype = C.c_int
+            L.orc_lattice_group.argtypes = [C.POINTER(Lattice), C.c_uint64, C.c_int32, C.POINTER(C.c_int64),
+                                            C.POINTER(LatticeResult), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                            C.POINTER(C.c_int64)]
+            L.orc_lattice_group.restype = C.c_int
             L.orc_ee_bin.argtypes = [C.c_int64, C.c_int64]
             L.orc_ee_bin.restype = C.c_int32
             _lib = L
@@ -246,3 +267,63 @@ def ee_histogram(snap_counts, iL=0, iD=1):
         for L, D in zip(snap_counts[s, :, iL].tolist(), snap_counts[s, :, iD].tolist()):
             hist[s, f(L, D)] += 1
     return hist
+
+
+def lattice_run(lx, ly, init, n_runs=None, *, rates=(1.0, 1.0, 1.0), hop=0.1, seed=0, precision=P64,
+                thin_bits=32, t_end=1.0, snap_times=(), step_budget=0, groups=None, threads=None, check=True,
+                lanes=32):
+    """Frank's model on a periodic lx x ly lattice (orc_lattice_group), group by group.
+
+    init: [M][3] counts shared by every run, or [n_runs][M][3] per run (site index x + lx y).
+    lanes: runs per group (32 as on the GPU; 1 gives every run its own group and stream).
+    groups: the group indices to run (runs lanes g .. lanes g + lanes - 1, the last group of n_runs
+    ragged); default every group of n_runs.  Returns per-run arrays for the runs of those groups.
+    """
+    import concurrent.futures as cf
+    M = lx * ly
+    init = np.ascontiguousarray(init, dtype=np.int64)
+    per_run = init.ndim == 3
+    if n_runs is None:
+        n_runs = init.shape[0] if per_run else 32
+    if groups is None:
+        groups = range((n_runs + lanes - 1) // lanes)
+    groups = list(groups)
+    per_group = lanes
+    k = np.ascontiguousarray(rates, dtype=np.float64)
+    snaps = np.ascontiguousarray(snap_times, dtype=np.float64)
+    S = len(snaps)
+
+    def one(g):
+        lanes = min(per_group, n_runs - per_group * g)
+        if per_run:
+            ini = np.ascontiguousarray(init[per_group * g:per_group * g + lanes])
+        else:
+            ini = np.ascontiguousarray(np.broadcast_to(init, (lanes, M, 3)))
+        p = Lattice(lx, ly, _ptr(k, C.c_double), float(hop), int(seed) & (2**64 - 1), int(precision),
+                    int(thin_bits), float(t_end), _ptr(snaps, C.c_double) if S else None, S, int(step_budget))
+        out = (LatticeResult * lanes)()
+        fin = np.zeros((lanes, M, 3), dtype=np.int64)
+        st_tot = np.zeros((lanes, max(S, 1), 3), dtype=np.int64)
+        st_dom = np.zeros((lanes, max(S, 1), 2), dtype=np.int64)
+        status = lib().orc_lattice_group(C.byref(p), int(g), lanes, _ptr(ini, C.c_int64), out,
+                                         _ptr(fin, C.c_int64), _ptr(st_tot, C.c_int64), _ptr(st_dom, C.c_int64))
+        res = np.ctypeslib.as_array(out)[:lanes].copy()
+        return status, res, fin, st_tot[:, :S], st_dom[:, :S]
+
+    threads = threads or os.cpu_count() or 1
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(one, groups))
+    status = min((p[0] for p in parts), default=OK)
+    if check and status not in (OK,):
+        raise RuntimeError(f"lattice oracle failed with status {status}")
+    res = np.concatenate([p[1] for p in parts]) if parts else np.zeros(0, dtype=LatticeResult)
+    return {
+        "status": status,
+        "final_counts": np.concatenate([p[2] for p in parts]),
+        "snap_totals": np.concatenate([p[3] for p in parts]),
+        "snap_domains": np.concatenate([p[4] for p in parts]),
+        "t_homochiral": np.array(res["t_homochiral"]), "outcome": np.array(res["outcome"]),
+        "run_status": np.array(res["status"]), "steps": np.array(res["steps"]),
+        "reactions": np.array(res["reactions"]), "hops": np.array(res["hops"]),
+        "cap_bits": np.array(res["cap_bits"]), "margin": np.array(res["margin"]),
+    }

@@ -150,6 +150,71 @@ int orc_run_many(const orc_problem* p, int64_t first_run, const int64_t* run_ids
                  const int64_t* init, int32_t init_per_run, orc_result* out,
                  int64_t* snap_counts, int32_t n_threads);
 
+/* ------------------------------------------------------------------------ */
+/* Frank's model on a periodic lattice (non-well-mixed; the paper's Sec. 1   */
+/* and Sec. 6 motivate compartments but give no algorithm: this is the      */
+/* library's reading, stated here in full).                                  */
+/* ------------------------------------------------------------------------ */
+/* Sites (x, y), x < lx, y < ly, both powers of two, M = lx ly sites, site index x + lx y.  Each
+ * site holds counts (L, D, A) and runs Frank's three reactions with propensities k_r h_r
+ * (h_1 = A L, h_2 = A D, h_3 = L D; Omega = 1 per site); every molecule hops to each of its four
+ * neighbours (x +- 1 mod lx, y) and (x, y +- 1 mod ly) at rate d.  The total count is conserved
+ * over the lattice, not per site.
+ *
+ * Uniformisation, exact: with u = min(k_max, d), rho_r = k_max / u and rho_h = d / u must be
+ * integers.  The runs of a group of 32 share an occupancy cap m = 2^b with every site count of
+ * every run <= m; c(m) = 4 rho_h m + rho_r m (m - 1) / 2, K = bit_length(c(m) - 1), and the rate
+ * of a step is Lambda = M 2^K u.  One step of group g at step s uses word k = element k % 4 of
+ * Philox4x32-10(key = seed, ctr = (g, s lo 32, s hi 16 | 2 << 24, k / 4)):
+ *   w0, w1: the waiting time, as for the well-mixed group clock (u53 or its top 24 bits);
+ *   w2: the site, sigma = w2 & (M - 1), shared by the runs of the group;
+ *   w3 .. w3+K-1: the planes of n (run l: n = sum_i bit_l(w_{3+i}) 2^i), uniform on [0, 2^K);
+ *   w35 ..: thinning, U = the q-bit number whose bit q-1-i is bit_l(w_{35+i}).
+ * Run l with counts (L, D, A) at sigma, n_s = L + D + A:
+ *   n < 4 rho_h m: a hop: direction n & 3 (x+1, x-1, y+1, y-1), molecule i = (n >> 2) & (m - 1);
+ *     i < L: an L hops, i < L + D: a D, i < n_s: an A, else nothing;
+ *   else the reaction r with 4 rho_h m + rho_r S_{r-1} <= n < 4 rho_h m + rho_r S_r (S_r = sum_{p<=r}
+ *     h_p), kept iff U < T_r = floor(k_r / k_max 2^q) (always when k_r = k_max); none if n is
+ *     at or above 4 rho_h m + rho_r S_3.
+ * A run then jumps by reaction r at sigma at rate (Lambda / M)(rho_r h_r / 2^K)(k_r / k_max) =
+ * k_r h_r and moves a given molecule in a given direction at rate (Lambda / M)(1 / 2^K) = d.  After
+ * the step, if a hop left a site of any run above m, b grows by one for the next steps (a bound
+ * that changes with the state, between steps).  Initially m is the smallest power of two at or
+ * above every site count of the group's runs.  Runs do not stop before t_end: the output keeps
+ * the time at which a run's whole lattice first holds a single species (global homochirality). */
+typedef struct {
+  int32_t lx, ly;           /* sides, powers of two, lx ly <= 65536 */
+  const double* rates;      /* [3] k_r >= 0, max > 0 */
+  double hop;               /* d > 0 */
+  uint64_t seed;
+  int32_t precision;        /* ORC_P64 | ORC_P32_KAHAN | ORC_P32_D64ACC | ORC_P32_PLAIN */
+  int32_t thin_bits;        /* q, 1..64 */
+  double t_end;             /* finite */
+  const double* snap_times; /* [n_snap] ascending, <= t_end */
+  int32_t n_snap;
+  int64_t step_budget;      /* 0 = unlimited */
+} orc_lattice;
+
+typedef struct {
+  double t_homochiral;      /* first event time at which the lattice holds one species; +inf */
+  int32_t outcome;          /* that species (0 L, 1 D, 2 A), -1 none */
+  int32_t status;
+  int64_t steps;            /* the group's steps */
+  int64_t reactions;        /* this run's reactions */
+  int64_t hops;             /* this run's hops */
+  int32_t cap_bits;         /* b of the group's final cap m = 2^b */
+  int32_t pad;
+  double margin;            /* smallest relative gap between a snapshot / t_end and an event time */
+} orc_lattice_result;
+
+/* The `lanes` runs of group g.  init: int64[lanes][M][3]; out: [lanes]; final: int64[lanes][M][3];
+ * snap_totals: int64[lanes][n_snap][3] lattice totals of (L, D, A) at each snapshot;
+ * snap_domains: int64[lanes][n_snap][2] sites with L > D and sites with D > L.  The last three
+ * may be NULL. */
+int orc_lattice_group(const orc_lattice* p, uint64_t group, int32_t lanes, const int64_t* init,
+                      orc_lattice_result* out, int64_t* final_counts, int64_t* snap_totals,
+                      int64_t* snap_domains);
+
 /* Enantiomeric-excess bin of (L, D): 64 bins over [-1, 1] by floor(64 L / (L + D)),
  * the top edge folded into bin 63; bin 64 holds L + D == 0. */
 int32_t orc_ee_bin(int64_t L, int64_t D);
