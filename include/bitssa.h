@@ -316,6 +316,109 @@ typedef void* (*ssa_alloc_fn)(size_t bytes, int device, void* stream, void* user
 typedef void (*ssa_free_fn)(void* ptr, size_t bytes, int device, void* stream, void* user);
 int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
 
+/* ------------------------------------------------------------------------------------------ */
+/* Frank's model on a periodic lattice (non-well-mixed).                                        */
+/*                                                                                              */
+/* The paper motivates compartments and systems that are not well mixed (Sec. 1, Sec. 6) but    */
+/* gives no algorithm for them; what follows is this library's exact extension of the method.  */
+/* ------------------------------------------------------------------------------------------ */
+/*
+ * Sites (x, y) with x < lx, y < ly (both powers of two; M = lx ly <= 16384 sites; site index
+ * x + lx y) each hold counts (L, D, A) and run Frank's reactions A+L->2L, A+D->2D, L+D->2A (Eqs.
+ * 1-3) with propensities k_r h_r per site (h = A L, A D, L D; Omega = 1 per site); every molecule
+ * hops to each of its four neighbours (x +- 1 mod lx, y), (x, y +- 1 mod ly) at rate d.  The total
+ * count is conserved over the lattice.
+ *
+ * The 32 runs of a group share one word per count plane per site (Sec. 4's binary words, one
+ * set per site) and the site of every step; each run picks its own event there.  Uniformisation
+ * is exact: with u = min(k_max, d), rho_r = k_max / u and rho_h = d / u must be integers
+ * (rho_r < 65536); the group keeps an occupancy cap m = 2^b at or above every site count of its
+ * runs (initially the smallest such power of two), c(m) = 4 rho_h m + rho_r m (m - 1) / 2 slots
+ * per site, K = bit_length(c(m) - 1) <= 32, and its steps come at rate Lambda = M 2^K u.  Step s of
+ * group g uses word k = element k % 4 of Philox4x32-10(key = seed, counter = (g, s lo 32,
+ * s hi 16 | 2 << 24, k / 4)):
+ *   w0, w1: the waiting time tau = -ln(u) / Lambda, u = (x + 1) 2^-53 from x = w1 2^21 + (w0 >> 11),
+ *     or u = ((w1 >> 8) + 1) 2^-24 in the fp32 modes;
+ *   w2: the site sigma = w2 & (M - 1) of every run of the group;
+ *   w3 .. w3+K-1: plane i of run l's n is bit l of w_{3+i};
+ *   w35 ..: thinning, the q-bit U whose bit q-1-i is bit l of w_{35+i}.
+ * Run l with counts (L, D, A) at sigma: if n < 4 rho_h m, a hop in direction n & 3 (x+1, x-1, y+1,
+ * y-1) of molecule i = (n >> 2) & (m - 1): an L if i < L, a D if i < L + D, an A if i < L + D + A,
+ * else nothing; otherwise reaction r if 4 rho_h m + rho_r S_{r-1} <= n < 4 rho_h m + rho_r S_r
+ * (S_r = h_1 + .. + h_r), kept iff U < floor(k_r / k_max 2^q) when k_r < k_max, nothing above S_3.
+ * A run thus jumps by reaction r at rate k_r h_r and moves a given molecule in a given direction at
+ * rate d.  If a hop leaves a site of any run above m, m doubles from the next step.  Runs go on to
+ * t_end; the time at which a run's lattice first holds a single species is kept.
+ *
+ * The steps of a group run in windows of block_size consecutive steps: a step waits only for
+ * earlier steps of its window whose site or neighbours meet its own, so every run follows the
+ * serial definition above exactly; results do not depend on the block size.
+ */
+typedef struct ssa_lattice ssa_lattice;
+
+/* Fields for ssa_lattice_fetch (n_runs, M and n_snap of the context and its last run). */
+enum {
+  SSA_LAT_FINAL_COUNTS = 0,   /* int32[n_runs][M][3]: (L, D, A) of every site at t_end */
+  SSA_LAT_HOMOCHIRAL_TIME = 1,/* double[n_runs]: first event time at which the run's lattice holds
+                                 one species (0 if it did at the start); +inf if never by t_end */
+  SSA_LAT_OUTCOME = 2,        /* int8[n_runs]: that species (0 L, 1 D, 2 A); -1 none */
+  SSA_LAT_EVENTS = 3,         /* int64[n_runs][2]: reactions and hops of the run */
+  SSA_LAT_SNAP_TOTALS = 4,    /* int64[n_snap][n_runs][3]: lattice totals of (L, D, A) at each
+                                 snapshot (the state after every event with time <= t_snap) */
+  SSA_LAT_SNAP_DOMAINS = 5,   /* int32[n_snap][n_runs][2]: sites with L > D and sites with D > L */
+  SSA_LAT_GROUPS = 6,         /* int64[n_groups][3]: steps of the group, its final cap bits b, and
+                                 its stop status (0 t_end, 1 step budget, 2 K above 32 planes,
+                                 3 cap above the context's planes) */
+  SSA_LAT_COUNTERS = 7        /* uint64[8]: group steps, windows, waves, reactions, hops, cap
+                                 doublings, groups stopped by an error, windows cut short before a
+                                 possible cap doubling */
+};
+#define SSA_LAT_N_COUNTERS 8
+
+/*
+ * Create a lattice context.
+ *   lx, ly: powers of two, lx ly <= 16384.
+ *   rates: double[3] (k_1, k_2, k_3) >= 0, max > 0; hop: d > 0.  max(k) / d or d / max(k) must be
+ *     an integer (within 1e-9 relative).
+ *   N0: int64[M][3] counts per site shared by every run (n0_per_run = 0) or int64[n_runs][M][3]
+ *     (n0_per_run = 1); each site count in [0, 32768].
+ *   n_runs >= 0, seed: as in ssa_create (run j is lane j % 32 of group j / 32).
+ *   opt: precision (SSA_P64 and SSA_P64_LOGSUM both give tau = -log(u) / Lambda summed in fp64;
+ *     SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P32_PLAIN as for ssa_create), thin_bits, block_size (steps
+ *     of a window, a multiple of 32 up to 256; 0 = 128), step_budget, first_run, cuda_stream, device.
+ *     Other fields must keep their defaults (SSA_EUNSUPPORTED otherwise).
+ *   cap_bits_max: the largest cap bits b the runs may reach, 0 = the initial cap (no doubling
+ *     beyond what the planes chosen for it hold); at most 15.  The planes per count are the
+ *     smallest of 4, 8, 12, 16 above it; a run whose cap would outgrow them stops with
+ *     SSA_EOVERFLOW.
+ * Returns SSA_EINVAL for bad arguments, SSA_EUNSUPPORTED beyond the limits above.
+ */
+int ssa_lattice_create(int32_t lx, int32_t ly, const double* rates, double hop, const int64_t* N0,
+                       int32_t n0_per_run, int64_t n_runs, uint64_t seed, const ssa_options* opt,
+                       int32_t cap_bits_max, ssa_lattice** out);
+
+/*
+ * Run every run from its initial state to t_end (each call starts again from t = 0).
+ * snapshot_times: double[n_snap] ascending in [0, t_end], n_snap in [0, 64].  Blocks until done.
+ * SSA_ETIMEOUT if a group hit the step budget, SSA_EOVERFLOW if a group's K left the stream's 32
+ * planes or its cap outgrew the context's planes; the fields are still written (SSA_LAT_GROUPS
+ * says which group stopped and why).
+ */
+int ssa_lattice_run(ssa_lattice* ctx, double t_end, const double* snapshot_times, int32_t n_snap);
+
+/* Bytes of a field after the last run (0 for an unknown field). */
+int ssa_lattice_field_bytes(const ssa_lattice* ctx, int32_t field, size_t* bytes);
+
+/* Copy a field into dst (host memory, or device memory on the context's device when
+ * dst_on_device = 1; complete on return). */
+int ssa_lattice_fetch(ssa_lattice* ctx, int32_t field, void* dst, size_t dst_bytes, int32_t dst_on_device);
+
+/* Free the context and its device memory.  NULL is allowed. */
+int ssa_lattice_destroy(ssa_lattice* ctx);
+
+/* Message of the last failed call on ctx; NULL: the calling thread's last failed create. */
+const char* ssa_lattice_last_error(const ssa_lattice* ctx);
+
 /*
  * ssa_run_frank_noalloc: one run of Frank's model that allocates no device memory.
  *

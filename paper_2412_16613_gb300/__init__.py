@@ -34,6 +34,17 @@ SSA_N_COUNTERS = 10
 COUNTER_NAMES = ["group_steps", "lane_steps", "reactions", "null_lane_steps", "redraw_rounds",
                  "absorbed", "groups_done", "error_flags", "max_group_steps", "layout"]
 
+SSA_LAT_FINAL_COUNTS, SSA_LAT_HOMOCHIRAL_TIME, SSA_LAT_OUTCOME, SSA_LAT_EVENTS = 0, 1, 2, 3
+SSA_LAT_SNAP_TOTALS, SSA_LAT_SNAP_DOMAINS, SSA_LAT_GROUPS, SSA_LAT_COUNTERS = 4, 5, 6, 7
+SSA_LAT_N_COUNTERS = 8
+LAT_COUNTER_NAMES = ["group_steps", "windows", "waves", "reactions", "hops", "cap_raises", "group_errors",
+                     "cut_windows"]
+_LAT_FIELD_DTYPE = {
+    SSA_LAT_FINAL_COUNTS: np.int32, SSA_LAT_HOMOCHIRAL_TIME: np.float64, SSA_LAT_OUTCOME: np.int8,
+    SSA_LAT_EVENTS: np.int64, SSA_LAT_SNAP_TOTALS: np.int64, SSA_LAT_SNAP_DOMAINS: np.int32,
+    SSA_LAT_GROUPS: np.int64, SSA_LAT_COUNTERS: np.uint64,
+}
+
 _FIELD_DTYPE = {
     SSA_FIELD_FINAL_COUNTS: np.int32, SSA_FIELD_ABSORB_TIME: np.float64,
     SSA_FIELD_ABSORB_OUTCOME: np.int8, SSA_FIELD_EE_HIST: np.uint64,
@@ -104,6 +115,15 @@ def lib():
                                                 C.c_int32, C.c_double, P(C.c_double), C.c_int32,
                                                 C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                                 C.c_void_p, P(C.c_uint64), C.c_void_p]
+            L.ssa_lattice_create.argtypes = [C.c_int32, C.c_int32, P(C.c_double), C.c_double, P(C.c_int64),
+                                             C.c_int32, C.c_int64, C.c_uint64, P(ssa_options), C.c_int32,
+                                             P(C.c_void_p)]
+            L.ssa_lattice_run.argtypes = [C.c_void_p, C.c_double, P(C.c_double), C.c_int32]
+            L.ssa_lattice_field_bytes.argtypes = [C.c_void_p, C.c_int32, P(C.c_size_t)]
+            L.ssa_lattice_fetch.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32]
+            L.ssa_lattice_destroy.argtypes = [C.c_void_p]
+            L.ssa_lattice_last_error.argtypes = [C.c_void_p]
+            L.ssa_lattice_last_error.restype = C.c_char_p
             L.bitssa_test_philox.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32), C.c_int64, C.c_int32]
             L.bitssa_test_bitslice.argtypes = [C.c_int32, P(C.c_int64), P(C.c_int64), P(C.c_int64), C.c_int64]
             L.bitssa_bench_alu.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_double)]
@@ -264,6 +284,80 @@ def ssa_last_error(ctx=None):
 
 def ssa_version():
     return lib().ssa_version()
+
+
+# --------------------------------------------------------------------------
+# Frank's model on a periodic lattice (ssa_lattice_* in include/bitssa.h)
+# --------------------------------------------------------------------------
+def _lat_check(status, ctx=None):
+    if status != SSA_OK:
+        msg = lib().ssa_lattice_last_error(ctx)
+        raise SSAError(status, msg.decode() if msg else "")
+    return status
+
+
+def ssa_lattice_create(lx, ly, rates, hop, N0, n_runs, seed, options=None, cap_bits_max=0):
+    """C ssa_lattice_create.  N0: [M][3] counts per site shared by every run, or [n_runs][M][3]."""
+    k = np.ascontiguousarray(rates, dtype=np.float64)
+    n0 = np.ascontiguousarray(N0, dtype=np.int64)
+    ctx = C.c_void_p()
+    opt = options if options is not None else ssa_default_options()
+    st = lib().ssa_lattice_create(int(lx), int(ly), _p(k, C.c_double), float(hop), _p(n0, C.c_int64),
+                                  1 if n0.ndim == 3 else 0, int(n_runs), int(seed) & (2**64 - 1), C.byref(opt),
+                                  int(cap_bits_max), C.byref(ctx))
+    _lat_check(st)
+    return ctx
+
+
+def ssa_lattice_run(ctx, t_end, snapshot_times=()):
+    snaps = np.ascontiguousarray(snapshot_times, dtype=np.float64)
+    ptr = _p(snaps, C.c_double) if len(snaps) else None
+    return _lat_check(lib().ssa_lattice_run(ctx, float(t_end), ptr, len(snaps)), ctx)
+
+
+def ssa_lattice_field_bytes(ctx, field):
+    n = C.c_size_t()
+    _lat_check(lib().ssa_lattice_field_bytes(ctx, field, C.byref(n)), ctx)
+    return n.value
+
+
+def ssa_lattice_fetch(ctx, field, out=None):
+    """Copy a lattice field into `out` (numpy array, or a CUDA torch tensor) or a new numpy array."""
+    nbytes = ssa_lattice_field_bytes(ctx, field)
+    if out is None:
+        out = np.empty(nbytes // np.dtype(_LAT_FIELD_DTYPE[field]).itemsize, dtype=_LAT_FIELD_DTYPE[field])
+    if isinstance(out, np.ndarray):
+        assert out.flags.c_contiguous and out.nbytes >= nbytes
+        _lat_check(lib().ssa_lattice_fetch(ctx, field, out.ctypes.data, out.nbytes, 0), ctx)
+    else:
+        assert out.is_contiguous() and out.is_cuda
+        _lat_check(lib().ssa_lattice_fetch(ctx, field, out.data_ptr(), out.numel() * out.element_size(), 1), ctx)
+    return out
+
+
+def ssa_lattice_destroy(ctx):
+    return _lat_check(lib().ssa_lattice_destroy(ctx))
+
+
+def ssa_lattice_last_error(ctx=None):
+    m = lib().ssa_lattice_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lattice_fetch_all(ctx, M, n_snap=0):
+    """Every lattice field as numpy arrays (per-run arrays in run order)."""
+    out = {
+        "final_counts": ssa_lattice_fetch(ctx, SSA_LAT_FINAL_COUNTS).reshape(-1, M, 3),
+        "t_homochiral": ssa_lattice_fetch(ctx, SSA_LAT_HOMOCHIRAL_TIME),
+        "outcome": ssa_lattice_fetch(ctx, SSA_LAT_OUTCOME),
+        "events": ssa_lattice_fetch(ctx, SSA_LAT_EVENTS).reshape(-1, 2),
+        "groups": ssa_lattice_fetch(ctx, SSA_LAT_GROUPS).reshape(-1, 3),
+        "counters": dict(zip(LAT_COUNTER_NAMES, ssa_lattice_fetch(ctx, SSA_LAT_COUNTERS).tolist())),
+    }
+    if n_snap:
+        out["snap_totals"] = ssa_lattice_fetch(ctx, SSA_LAT_SNAP_TOTALS).reshape(n_snap, -1, 3)
+        out["snap_domains"] = ssa_lattice_fetch(ctx, SSA_LAT_SNAP_DOMAINS).reshape(n_snap, -1, 2)
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -4,7 +4,8 @@ The bit-sliced kernel is instantiated once per number of propensity planes K
 (1..31); each instantiation is its own object file built from
 ``csrc/frank_instance.cu`` with ``-DBITSSA_K=<K>`` so that they compile in
 parallel.  Objects go to ``_build/`` next to this file; the library is
-``libbitssa.so`` in the package directory.
+``libbitssa.so`` in the package directory.  The lattice kernel is instantiated once
+per count-plane width (4, 8, 12, 16) from ``csrc/lattice_instance.cu``.
 """
 from __future__ import annotations
 
@@ -21,6 +22,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbitssa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 K_VALUES = list(range(1, 32))
+LATTICE_PLANES = (4, 8, 12, 16)  # count planes of the lattice kernel's instantiations
 
 
 def nvcc_path() -> str:
@@ -49,7 +51,10 @@ def _jobs():
                      [f"-DBITSSA_K={k}"]))
         jobs.append((os.path.join(CSRC, "general_instance.cu"), os.path.join(BUILD, f"general_k{k:02d}.o"),
                      [f"-DBITSSA_K={k}"]))
-    for name in ("frank_dispatch", "thread_per_run", "runtime", "selftest", "noalloc"):
+    for p in LATTICE_PLANES:
+        jobs.append((os.path.join(CSRC, "lattice_instance.cu"), os.path.join(BUILD, f"lattice_p{p:02d}.o"),
+                     [f"-DBITSSA_LAT_P={p}"]))
+    for name in ("frank_dispatch", "thread_per_run", "runtime", "selftest", "noalloc", "lattice"):
         jobs.append((os.path.join(CSRC, name + ".cu"), os.path.join(BUILD, name + ".o"), []))
     return jobs
 

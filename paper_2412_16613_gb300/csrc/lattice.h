@@ -1,0 +1,97 @@
+// lattice.h -- structures shared by the host runtime and the sm_103a kernel of Frank's model on
+// a periodic lattice (ssa_lattice_* in bitssa.h).  Not part of the C ABI.
+//
+// The paper motivates compartments and non-well-mixed systems (Sec. 1, Sec. 6) without giving an
+// algorithm.  The library's reading: sites (x, y) of an lx x ly torus, both powers of two, each
+// with counts (L, D, A) and Frank's three reactions (Eqs. 1-3, Omega = 1 per site); every
+// molecule hops to each of its four neighbours at rate d.  A group of 32 runs shares the site of
+// each step, and each run draws its own event at that site from its bit of the step's words, the
+// binary-word representation of Sec. 4 with one word per count plane per site.  Uniformisation
+// is exact: with u = min(k_max, d), rho_r = k_max / u and rho_h = d / u integers and an
+// occupancy cap m = 2^b at or above every site count of the group's runs, a site holds
+// c(m) = 4 rho_h m + rho_r m (m - 1) / 2 slots, the group draws K = bit_length(c(m) - 1) planes,
+// and its steps come at rate Lambda = M 2^K u.  A hop that leaves a site of a run above m doubles
+// m from the next step on.
+#pragma once
+
+#include <cstdint>
+
+namespace bitssa {
+
+constexpr int kLatMaxPlanes = 16;   // count planes of the widest instantiation (caps up to 2^15)
+constexpr int kLatMaxSites = 16384; // per-site shared-memory tables of one block
+constexpr int kLatMaxSnap = 64;
+constexpr int kLatMaxBlock = 256;   // steps of a window (threads of a block)
+constexpr int kLatRhoBits = 16;     // rho_r below 2^16
+constexpr int kLatCounters = 8;
+
+// Indices into the lattice kernel's counter array (uint64).
+enum LatCounter {
+  kLatGroupSteps = 0,   // steps of every group
+  kLatWindows = 1,      // windows (blocks of consecutive steps taken together)
+  kLatWaves = 2,        // waves of mutually independent steps inside the windows
+  kLatReactions = 3,    // reactions of every run
+  kLatHops = 4,         // hops of every run
+  kLatCapRaises = 5,    // doublings of a group's occupancy cap
+  kLatErrors = 6,       // groups that stopped with an error
+  kLatCutWindows = 7    // windows shortened by a possible cap overflow
+};
+
+// Per-group stop status (LatticeLaunch::group_status).
+enum LatStatus {
+  kLatOk = 0,
+  kLatTimeout = 1,   // the step budget ran out
+  kLatRange = 2,     // the cap's K left the stream's 32 planes of n
+  kLatCapacity = 3,  // the cap outgrew the planes of this launch
+  kLatBadInit = 4    // an initial site count above the launch's capacity
+};
+
+// Constants of one occupancy cap m = 2^b.
+struct LatCap {
+  double lambda;          // M 2^K u
+  float inv_lambda_f;     // (float)(1 / lambda)
+  int K;                  // bit length of c(m) - 1; above 32: outside the stream
+  unsigned int hop_slots; // 4 rho_h m
+};
+
+struct LatticeLaunch {
+  int lx, ly, lx_log, M;          // lattice; site index x + lx y
+  int rec;                        // words of a site record (3 P, padded to a multiple of 4)
+  int block;                      // threads of a block = steps of a window
+  long long n_runs, n_groups;     // runs of the context, groups of 32
+  long long group_base;           // stream index of the context's group 0
+  unsigned long long seed;
+  unsigned int rho_r, rho_h;
+  int thin;                       // some k_r < k_max
+  unsigned int always;            // bit r: k_r == k_max
+  unsigned long long thin_T[3];   // floor(k_r / k_max 2^q)
+  int q;
+  int precision;                  // kP64LogSum (fp64), kP32Kahan, kP32D64Acc, kP32Plain
+  double t_end;
+  const double* snap;             // [n_snap]
+  int n_snap;
+  long long step_budget;          // 0 = none
+  LatCap cap[kLatMaxPlanes + 1];  // b = 0 .. P
+  const int* init;                // [n_runs][M][3] or [M][3]
+  int init_per_run;
+  uint32_t* planes;               // [n_groups][M][rec] words of the group's count planes
+  // outputs
+  int* final_counts;              // [n_runs][M][3]
+  double* t_homochiral;           // [n_runs]
+  signed char* outcome;           // [n_runs]
+  long long* events;              // [n_runs][2]: reactions, hops
+  long long* group_info;          // [n_groups][3]: steps, cap bits, LatStatus
+  long long* snap_totals;         // [n_snap][n_runs][3]
+  int* snap_domains;              // [n_snap][n_runs][2]
+  unsigned long long* counters;   // [kLatCounters]
+};
+
+// Launcher of the instantiation with P count planes (4, 8, 12 or 16); -1 if none.
+int lattice_launch(int P, const LatticeLaunch& p, int grid, int block, int smem, void* stream);
+// Draw planes the instantiation with P count planes handles (K above it is refused at create).
+int lattice_draw_planes(int P);
+// Dynamic shared memory of a block of `block` threads for a lattice of M sites.
+int lattice_smem_bytes(int M, int block);
+int lattice_max_active_blocks(int P, int block, int smem, int* blocks);
+
+}  // namespace bitssa

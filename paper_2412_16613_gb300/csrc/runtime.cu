@@ -856,6 +856,12 @@ size_t field_bytes(const ssa_ctx* c, int field) {
 
 namespace bitssa {
 void set_thread_error(const std::string& msg) { t_err = msg; }
+void current_allocator(ssa_alloc_fn* alloc, ssa_free_fn* release, void** user) {
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  *alloc = g_alloc.alloc;
+  *release = g_alloc.release;
+  *user = g_alloc.user;
+}
 }  // namespace bitssa
 
 extern "C" {

@@ -39,3 +39,11 @@ def multinomial_init(n_runs: int, n_tot: int, p=(0.25, 0.25, 0.5), seed: int = 7
     """Independent multinomial initial states around the racemic point."""
     rng = np.random.default_rng(seed)
     return rng.multinomial(n_tot, p, size=n_runs).astype(np.int64)
+
+
+def lattice_init(lx: int, ly: int, n_runs: int, mean=(8.0, 8.0, 16.0), seed: int = 0x1A77) -> np.ndarray:
+    """Per-run, per-site counts of (L, D, A) on an lx x ly lattice, independent Poisson draws with
+    the given means: Poisson(sum(mean)) molecules per site split multinomially in the ratio of the
+    means (L:D:A = 1:1:2 by default).  Shape [n_runs][lx ly][3], site index x + lx y."""
+    rng = np.random.default_rng(seed)
+    return rng.poisson(mean, size=(n_runs, lx * ly, 3)).astype(np.int64)

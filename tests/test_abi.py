@@ -37,7 +37,9 @@ def test_headers_declare_the_boundary():
     names = declared_functions()
     for n in ["ssa_create", "ssa_create_batch", "ssa_run", "ssa_fetch", "ssa_destroy", "ssa_last_error",
               "ssa_set_allocator", "ssa_default_options", "ssa_field_bytes", "ssa_version", "ssa_tune",
-              "bitssa_test_philox", "bitssa_test_bitslice", "bitssa_bench_alu"]:
+              "bitssa_test_philox", "bitssa_test_bitslice", "bitssa_bench_alu", "ssa_lattice_create",
+              "ssa_lattice_run", "ssa_lattice_fetch", "ssa_lattice_field_bytes", "ssa_lattice_destroy",
+              "ssa_lattice_last_error"]:
         assert n in names, n
 
 
@@ -189,3 +191,55 @@ def test_batch_validates_the_bound_option(lib, kw):
         pkg.ssa_create_batch(F_R, F_P, init, np.ones((2, 3)), np.array([64, 32]), np.array([1, 2], dtype=np.uint64),
                              pkg.ssa_default_options(**kw))
     assert ei.value.status == (pkg.SSA_EINVAL if kw.get("pad_pow2") == 3 else pkg.SSA_EUNSUPPORTED)
+
+
+def _lattice_create(lx=4, ly=4, rates=(1.0, 1.0, 1.0), hop=0.1, N0=None, n_runs=32, cap_bits_max=0, **opt):
+    if N0 is None:
+        N0 = np.full((lx * ly if lx > 0 and ly > 0 else 1, 3), 2, dtype=np.int64)
+    return pkg.ssa_lattice_create(lx, ly, rates, hop, N0, n_runs, 0, pkg.ssa_default_options(**opt),
+                                  cap_bits_max=cap_bits_max)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(lx=3), pkg.SSA_EINVAL),                                   # sides are powers of two
+    (dict(ly=0), pkg.SSA_EINVAL),
+    (dict(lx=256, ly=128), pkg.SSA_EUNSUPPORTED),                   # more than 16384 sites
+    (dict(rates=(0.0, 0.0, 0.0)), pkg.SSA_EINVAL),
+    (dict(rates=(-1.0, 1.0, 1.0)), pkg.SSA_EINVAL),
+    (dict(hop=0.0), pkg.SSA_EINVAL),
+    (dict(hop=0.3), pkg.SSA_EINVAL),                                # k_max / d not an integer
+    (dict(hop=1.0 / 70000), pkg.SSA_EUNSUPPORTED),                  # rho_r above 2^16
+    (dict(N0=np.full((16, 3), -1)), pkg.SSA_EINVAL),
+    (dict(N0=np.full((16, 3), 40000)), pkg.SSA_EINVAL),
+    (dict(cap_bits_max=16), pkg.SSA_EINVAL),
+    (dict(n_runs=-1), pkg.SSA_EINVAL),
+    (dict(precision=7), pkg.SSA_EINVAL),
+    (dict(thin_bits=0), pkg.SSA_EINVAL),
+    (dict(block_size=48), pkg.SSA_EINVAL),
+    (dict(block_size=512), pkg.SSA_EINVAL),
+    (dict(first_run=5), pkg.SSA_EINVAL),
+    (dict(clock=pkg.SSA_CLOCK_LANE), pkg.SSA_EUNSUPPORTED),
+    (dict(pad_pow2=1), pkg.SSA_EUNSUPPORTED),
+    (dict(engine=pkg.SSA_ENGINE_GENERAL), pkg.SSA_EUNSUPPORTED),
+])
+def test_lattice_validation_before_any_cuda_call(lib, kw, status):
+    """ssa_lattice_create checks every argument before it touches the GPU."""
+    with pytest.raises(pkg.SSAError) as ei:
+        _lattice_create(**kw)
+    assert ei.value.status == status
+    assert pkg.ssa_lattice_last_error()
+    assert pkg.ssa_last_error()  # the thread's message is shared with ssa_create's
+
+
+def test_lattice_valid_arguments_reach_the_device(lib):
+    """Valid arguments pass validation; without a GPU the call stops at the device."""
+    try:
+        ctx = _lattice_create(8, 8, N0=np.random.default_rng(0).poisson(3, size=(40, 64, 3)), n_runs=40)
+    except pkg.SSAError as e:
+        assert e.status == pkg.SSA_ECUDA
+    else:
+        pkg.ssa_lattice_destroy(ctx)
+    L = lib
+    assert L.ssa_lattice_run(None, 1.0, None, 0) == pkg.SSA_EINVAL
+    assert L.ssa_lattice_fetch(None, 0, None, 0, 0) == pkg.SSA_EINVAL
+    assert L.ssa_lattice_destroy(None) == pkg.SSA_OK
