@@ -350,9 +350,9 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
  * rate d.  If a hop leaves a site of any run above m, m doubles from the next step.  Runs go on to
  * t_end; the time at which a run's lattice first holds a single species is kept.
  *
- * The steps of a group run in windows of block_size consecutive steps: a step waits only for
- * earlier steps of its window whose site or neighbours meet its own, so every run follows the
- * serial definition above exactly; results do not depend on the block size.
+ * Up to block_size consecutive steps of a group are pending at once; a step waits only for
+ * earlier pending steps whose site or neighbours meet its own, so every run follows the serial
+ * definition above exactly; results do not depend on the block size.
  */
 typedef struct ssa_lattice ssa_lattice;
 
@@ -369,9 +369,10 @@ enum {
   SSA_LAT_GROUPS = 6,         /* int64[n_groups][3]: steps of the group, its final cap bits b, and
                                  its stop status (0 t_end, 1 step budget, 2 K above 32 planes,
                                  3 cap above the context's planes) */
-  SSA_LAT_COUNTERS = 7        /* uint64[8]: group steps, windows, waves, reactions, hops, cap
-                                 doublings, groups stopped by an error, windows cut short before a
-                                 possible cap doubling */
+  SSA_LAT_COUNTERS = 7        /* uint64[8]: group steps, rounds (one wave of ready steps each),
+                                 rounds whose new steps might pass a snapshot or t_end (the clock
+                                 ran before admission), reactions, hops, cap doublings, groups
+                                 stopped by an error, steps admitted as possible cap doublings */
 };
 #define SSA_LAT_N_COUNTERS 8
 
@@ -385,7 +386,7 @@ enum {
  *   n_runs >= 0, seed: as in ssa_create (run j is lane j % 32 of group j / 32).
  *   opt: precision (SSA_P64 and SSA_P64_LOGSUM both give tau = -log(u) / Lambda summed in fp64;
  *     SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P32_PLAIN as for ssa_create), thin_bits, block_size (steps
- *     of a window, a multiple of 32 up to 256; 0 = 128), step_budget, first_run, cuda_stream, device.
+ *     pending at once, a multiple of 32 up to 224; 0 = 224), step_budget, first_run, cuda_stream, device.
  *     Other fields must keep their defaults (SSA_EUNSUPPORTED otherwise).
  *   cap_bits_max: the largest cap bits b the runs may reach, 0 = the initial cap (no doubling
  *     beyond what the planes chosen for it hold); at most 15.  The planes per count are the

@@ -37,8 +37,8 @@ COUNTER_NAMES = ["group_steps", "lane_steps", "reactions", "null_lane_steps", "r
 SSA_LAT_FINAL_COUNTS, SSA_LAT_HOMOCHIRAL_TIME, SSA_LAT_OUTCOME, SSA_LAT_EVENTS = 0, 1, 2, 3
 SSA_LAT_SNAP_TOTALS, SSA_LAT_SNAP_DOMAINS, SSA_LAT_GROUPS, SSA_LAT_COUNTERS = 4, 5, 6, 7
 SSA_LAT_N_COUNTERS = 8
-LAT_COUNTER_NAMES = ["group_steps", "windows", "waves", "reactions", "hops", "cap_raises", "group_errors",
-                     "cut_windows"]
+LAT_COUNTER_NAMES = ["group_steps", "rounds", "clock_rounds", "reactions", "hops", "cap_raises", "group_errors",
+                     "flagged"]
 _LAT_FIELD_DTYPE = {
     SSA_LAT_FINAL_COUNTS: np.int32, SSA_LAT_HOMOCHIRAL_TIME: np.float64, SSA_LAT_OUTCOME: np.int8,
     SSA_LAT_EVENTS: np.int64, SSA_LAT_SNAP_TOTALS: np.int64, SSA_LAT_SNAP_DOMAINS: np.int32,

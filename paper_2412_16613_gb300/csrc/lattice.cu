@@ -62,8 +62,11 @@ int lattice_max_active_blocks(int P, int block, int smem, int* blocks) {
   }
 }
 
-int lattice_smem_bytes(int M, int block) {
-  return 4 * M + 4 * M + 2 * ((M + 3) & ~3) + block * (8 + 8 + 4 + 4 + 4 + 4 + 4 + 16 + 4 + 4);
+// Per site: stamp and hop-count (uint32), cap table (uint16); per step in the ring of 512: the clock
+// after it, the waiting time in fp64 and fp32, the fp32 clock state, the site, plane 0 of n, four
+// event masks and the done flag; per step thread: the ready list.
+int lattice_smem_bytes(int M, int T) {
+  return 4 * M + 4 * M + 2 * ((M + 3) & ~3) + 512 * (8 + 8 + 4 + 4 + 4 + 4 + 4 + 16 + 4) + 4 * T;
 }
 
 }  // namespace bitssa
@@ -233,7 +236,7 @@ int ssa_lattice_create(int32_t lx, int32_t ly, const double* rates, double hop, 
   if (o.step_budget < 0) return lfail(nullptr, SSA_EINVAL, "step_budget must be >= 0");
   if (o.first_run < 0 || o.first_run % 32 != 0) return lfail(nullptr, SSA_EINVAL, "first_run must be a non-negative multiple of 32");
   if (o.block_size != 0 && (o.block_size < 32 || o.block_size > kLatMaxBlock || o.block_size % 32 != 0))
-    return lfail(nullptr, SSA_EINVAL, "block_size must be a multiple of 32 in [32, 256]");
+    return lfail(nullptr, SSA_EINVAL, "block_size must be a multiple of 32 in [32, 224]");
   if (o.blocks_per_sm < 0) return lfail(nullptr, SSA_EINVAL, "blocks_per_sm must be >= 0");
   if (o.engine != SSA_ENGINE_BITSLICED || o.layout != SSA_LAYOUT_AUTO || o.shared_n || o.pad_pow2 ||
       o.recompute || o.clock != SSA_CLOCK_GROUP || (o.word_width != 0 && o.word_width != 32) || o.tail_groups ||
@@ -431,10 +434,11 @@ int ssa_lattice_run(ssa_lattice* c, double t_end, const double* snapshot_times, 
   lp.n_snap = n_snap;
   lp.snap_totals = n_snap > 0 ? c->d_snap_tot : nullptr;
   lp.snap_domains = n_snap > 0 ? c->d_snap_dom : nullptr;
-  const int block = c->opt.block_size ? c->opt.block_size : 128;
-  lp.block = block;
+  const int T = c->opt.block_size ? c->opt.block_size : kLatDefaultWindow;
+  const int block = T + 32;  // T step threads and the service warp
+  lp.block = T;
   if (c->n_groups > 0) {
-    const int smem = lattice_smem_bytes(c->M, block);
+    const int smem = lattice_smem_bytes(c->M, T);
     int per_sm = 0;
     if (lattice_max_active_blocks(c->P, block, smem, &per_sm) != 0 || per_sm < 1)
       return lfail(c, SSA_EUNSUPPORTED, "the lattice kernel does not fit an SM at this lattice and block size");

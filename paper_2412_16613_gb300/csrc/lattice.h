@@ -21,20 +21,21 @@ namespace bitssa {
 constexpr int kLatMaxPlanes = 16;   // count planes of the widest instantiation (caps up to 2^15)
 constexpr int kLatMaxSites = 16384; // per-site shared-memory tables of one block
 constexpr int kLatMaxSnap = 64;
-constexpr int kLatMaxBlock = 256;   // steps of a window (threads of a block)
+constexpr int kLatMaxBlock = 224;   // pending steps of a group at most (step threads of a block; one more warp serves)
+constexpr int kLatDefaultWindow = 224;
 constexpr int kLatRhoBits = 16;     // rho_r below 2^16
 constexpr int kLatCounters = 8;
 
 // Indices into the lattice kernel's counter array (uint64).
 enum LatCounter {
   kLatGroupSteps = 0,   // steps of every group
-  kLatWindows = 1,      // windows (blocks of consecutive steps taken together)
-  kLatWaves = 2,        // waves of mutually independent steps inside the windows
+  kLatRounds = 1,       // rounds (admission of new steps and one wave of the ready ones)
+  kLatClockRounds = 2,  // rounds whose new steps might pass a time point: the clock ran first
   kLatReactions = 3,    // reactions of every run
   kLatHops = 4,         // hops of every run
   kLatCapRaises = 5,    // doublings of a group's occupancy cap
   kLatErrors = 6,       // groups that stopped with an error
-  kLatCutWindows = 7    // windows shortened by a possible cap overflow
+  kLatFlagged = 7       // steps admitted as possible cap doublings (nothing after them until they ran)
 };
 
 // Per-group stop status (LatticeLaunch::group_status).
@@ -57,7 +58,7 @@ struct LatCap {
 struct LatticeLaunch {
   int lx, ly, lx_log, M;          // lattice; site index x + lx y
   int rec;                        // words of a site record (3 P, padded to a multiple of 4)
-  int block;                      // threads of a block = steps of a window
+  int block;                      // pending steps at most (step threads; the block has one more warp)
   long long n_runs, n_groups;     // runs of the context, groups of 32
   long long group_base;           // stream index of the context's group 0
   unsigned long long seed;
@@ -90,8 +91,8 @@ struct LatticeLaunch {
 int lattice_launch(int P, const LatticeLaunch& p, int grid, int block, int smem, void* stream);
 // Draw planes the instantiation with P count planes handles (K above it is refused at create).
 int lattice_draw_planes(int P);
-// Dynamic shared memory of a block of `block` threads for a lattice of M sites.
-int lattice_smem_bytes(int M, int block);
+// Dynamic shared memory of a block with T step threads for a lattice of M sites.
+int lattice_smem_bytes(int M, int T);
 int lattice_max_active_blocks(int P, int block, int smem, int* blocks);
 
 }  // namespace bitssa

@@ -9,24 +9,18 @@
 // at counter (group, s, tag 2), among them the site sigma_s shared by the group's runs and, per
 // run, the K-bit number n that picks its event at sigma_s (a hop of one molecule to one of the
 // four neighbours, one of Frank's three reactions, or nothing).  The site sequence does not
-// depend on the state, so a window of consecutive steps (one per thread) is drawn at once:
-//   A. every thread draws its step's first Philox call: the waiting time and the site;
-//   B. one thread adds the waiting times in step order (the group clock of Eq. equation-tau and
-//      Eq. eq-update-time) and cuts the window before the first step whose event would pass a
-//      snapshot or t_end, or that the step budget forbids;
-//   C. the window is cut after the first step that might push a neighbour above the cap m (only
-//      such a step can raise the cap, which changes K and the rate of every later step);
-//   D. the steps run in waves: a step waits for every earlier step of the window whose closed
-//      neighbourhood (the site and its four neighbours) meets its own, found with per-site
-//      stamps in shared memory, so steps of one wave touch disjoint sites and commute with every
-//      step left for later waves.  Each step is the bit-sliced event of Sec. 4 at its site:
-//      comparisons of n with the hop slots and with the cumulative slots rho_r S_r (S_r from
-//      bit-sliced schoolbook products of the site's count planes, Sec. 4.1), masked count updates
-//      at the site (Eq. equation-v) and masked increments at the neighbours;
-//   E. warp 0, thread l = run l, replays the window's event masks in step order to keep run l's
-//      lattice totals and the time it first holds one species.
-// Every run therefore takes exactly the trajectory of the serial definition; only independent
-// steps are reordered.
+// depend on the state, so a window of consecutive steps (one per step thread) is drawn at once.
+// A step changes only its site and the neighbours its runs hop to, so two steps whose closed
+// neighbourhoods (the site and its four neighbours) are disjoint commute: the window's steps run
+// in waves, a step waiting for every earlier step of the window whose neighbourhood meets its own
+// (per-site stamps in shared memory find them).  Each step is the bit-sliced event of Sec. 4 at
+// its site: comparisons of n with the hop slots and with the cumulative slots rho_r S_r (S_r
+// from bit-sliced schoolbook products of the site's count planes, Sec. 4.1), masked count updates
+// at the site (Eq. equation-v) and masked increments at the neighbours.  The group clock is summed
+// in step order by a service warp, which also replays each window's event masks in step order to
+// keep every run's lattice totals and the time its lattice first holds one species.  Every run
+// therefore takes exactly the trajectory of the serial definition; only independent steps are
+// reordered.  (The window's phases are listed above lattice_kernel.)
 #pragma once
 
 #include <cstdint>
@@ -337,68 +331,226 @@ __device__ __forceinline__ StepOut step(const LatticeLaunch& p, const StepArgs& 
 
 }  // namespace lat
 
+// Steps of a group held at once: the pending steps (at most one per step thread) and the steps
+// finished but not yet replayed into the runs' totals.  A power of two, at least twice the
+// largest window.
+constexpr int kLatRing = 512;
+static_assert(kLatRing >= 2 * kLatMaxBlock, "the ring must hold two windows");
+
 // Shared-memory layout of a block: per site, the stamp and hop-count tables (uint32) and the cap
-// table ub (uint16, the largest site total over the group's runs); per step of a window, the clock
-// and the event masks.
+// table ub (uint16, the largest site total over the group's runs); per step, in a ring indexed by
+// the step's index modulo kLatRing, its waiting time, site and plane 0 of n, the clock after it,
+// its event masks and its done flag; the ready list of a wave.
 struct LatSmem {
   uint32_t* stamp;
   uint32_t* hopcnt;
   uint16_t* ub;
-  double* tnew;   // time after step i's event
-  double* taud;   // fp64 waiting times
-  float* tauf;    // fp32 waiting times
-  float* tf;      // fp32 clock after step i (Kahan sum or plain sum)
-  float* cf;      // Kahan compensation after step i
+  double* tnew;   // time after the step's event
+  double* taud;   // fp64 waiting time
+  float* tauf;    // fp32 waiting time
+  float* tf;      // fp32 clock after the step (Kahan sum or plain sum)
+  float* cf;      // Kahan compensation after the step
   int* sigma;
   uint32_t* w3;
   uint32_t* x1;
   uint32_t* x2;
   uint32_t* x3;
   uint32_t* hop;
-  int* ready;
   int* done;
+  int* ready;     // [T]
 };
 
-__device__ __forceinline__ LatSmem lat_smem(unsigned char* base, int M, int T) {
+__device__ __forceinline__ LatSmem lat_smem(unsigned char* base, int M) {
+  constexpr int R = kLatRing;
   LatSmem s;
   s.stamp = reinterpret_cast<uint32_t*>(base);
   s.hopcnt = s.stamp + M;
   s.ub = reinterpret_cast<uint16_t*>(s.hopcnt + M);
   unsigned char* w = reinterpret_cast<unsigned char*>(s.ub + ((M + 3) & ~3));
   s.tnew = reinterpret_cast<double*>(w);
-  s.taud = s.tnew + T;
-  s.tauf = reinterpret_cast<float*>(s.taud + T);
-  s.tf = s.tauf + T;
-  s.cf = s.tf + T;
-  s.sigma = reinterpret_cast<int*>(s.cf + T);
-  s.w3 = reinterpret_cast<uint32_t*>(s.sigma + T);
-  s.x1 = s.w3 + T;
-  s.x2 = s.x1 + T;
-  s.x3 = s.x2 + T;
-  s.hop = s.x3 + T;
-  s.ready = reinterpret_cast<int*>(s.hop + T);
-  s.done = s.ready + T;
+  s.taud = s.tnew + R;
+  s.tauf = reinterpret_cast<float*>(s.taud + R);
+  s.tf = s.tauf + R;
+  s.cf = s.tf + R;
+  s.sigma = reinterpret_cast<int*>(s.cf + R);
+  s.w3 = reinterpret_cast<uint32_t*>(s.sigma + R);
+  s.x1 = s.w3 + R;
+  s.x2 = s.x1 + R;
+  s.x3 = s.x2 + R;
+  s.hop = s.x3 + R;
+  s.done = reinterpret_cast<int*>(s.hop + R);
+  s.ready = s.done + R;
   return s;
 }
 
-__host__ __device__ constexpr int lat_smem_bytes(int M, int T) {
-  return 4 * M + 4 * M + 2 * ((M + 3) & ~3) + T * (8 + 8 + 4 + 4 + 4 + 4 + 4 + 16 + 4 + 4);
+namespace lat {
+
+constexpr long long kNoStop = 0x7FFFFFFFFFFFFFFFll;
+enum StopReason { kStopNone = 0, kStopFlag = 1, kStopCross = 2, kStopBudget = 3 };
+
+__device__ __forceinline__ int slot(long long s) { return (int)(s & (kLatRing - 1)); }
+
+// Barrier of the step warps only; the service warp runs on meanwhile.
+__device__ __forceinline__ void step_sync(int T) { asm volatile("bar.sync 1, %0;" ::"r"(T) : "memory"); }
+
+// Run `lane` of the group, kept by the service warp: lattice totals, events, first single-species time.
+struct RunBook {
+  long long tot[3];
+  long long reactions, hops;
+  double t_h;
+  int outcome;
+};
+
+// Column `lane` of the 32 x 32 bit matrix whose row j is lane j's word v: bit j of the result is bit
+// `lane` of row j.  Five butterfly stages swap the off-diagonal blocks of width 16, 8, 4, 2, 1.
+__device__ __forceinline__ uint32_t transpose32(uint32_t v, int lane) {
+  const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0, k = 16; s < 5; ++s, k >>= 1) {
+    const uint32_t m = masks[s];
+    const uint32_t o = __shfl_xor_sync(kFull, v, k);
+    v = (lane & k) ? ((v & ~m) | ((o >> k) & m)) : ((v & m) | ((o << k) & ~m));
+  }
+  return v;
 }
 
+// Adds the events of steps [a, b) to run `lane`'s book (every lane of the warp calls it; `mine` =
+// the lane is a run of the group).  Each run's events over 32 steps are one column of the masks,
+// so a bit transpose and a population count give the run's counts.  A species whose lattice total
+// reaches zero stays at zero, so a run that still holds two species after the range held two
+// throughout it; only a run left with one species replays the range in step order, to find the
+// event after which its lattice first held one species.
+__device__ __forceinline__ void replay(RunBook& r, const LatSmem& S, long long a, long long b, int lane, bool mine) {
+  int n1 = 0, n2 = 0, n3 = 0, nh = 0;
+  for (long long base = a; base < b; base += 32) {
+    const long long i = base + lane;
+    const bool in = i < b;
+    const int k = slot(i);
+    n1 += __popc(transpose32(in ? S.x1[k] : 0u, lane));
+    n2 += __popc(transpose32(in ? S.x2[k] : 0u, lane));
+    n3 += __popc(transpose32(in ? S.x3[k] : 0u, lane));
+    nh += __popc(transpose32(in ? S.hop[k] : 0u, lane));
+  }
+  if (!mine) return;
+  const long long start[3] = {r.tot[0], r.tot[1], r.tot[2]};
+  r.tot[0] += n1 - n3;
+  r.tot[1] += n2 - n3;
+  r.tot[2] += 2 * n3 - n1 - n2;
+  r.reactions += n1 + n2 + n3;
+  r.hops += nh;
+  if (r.outcome != -1 || (r.tot[0] > 0) + (r.tot[1] > 0) + (r.tot[2] > 0) > 1) return;
+  // the range holds the run's last extinction before a single species: find it in step order
+  const uint32_t bit = 1u << lane;
+  long long t0 = start[0], t1 = start[1], t2 = start[2];
+  for (long long i = a; i < b; ++i) {
+    const int k = slot(i);
+    const uint32_t r1 = S.x1[k] & bit, r2 = S.x2[k] & bit, r3 = S.x3[k] & bit;
+    if (!(r1 | r2 | r3)) continue;
+    if (r1) {
+      ++t0;
+      --t2;
+    } else if (r2) {
+      ++t1;
+      --t2;
+    } else {
+      --t0;
+      --t1;
+      t2 += 2;
+    }
+    if ((t0 > 0) + (t1 > 0) + (t2 > 0) == 1) {
+      r.t_h = S.tnew[k];
+      r.outcome = t0 ? 0 : (t1 ? 1 : 2);
+      break;
+    }
+  }
+}
+
+struct Clock {
+  double t;   // fp64 modes: the time; fp32 modes: (double) of the fp32 sum
+  float tf;   // fp32 sum (Kahan or plain)
+  float cf;   // Kahan compensation
+};
+
+// The group clock over steps [from, from + n), in step order (Eq. equation-tau, Eq.
+// eq-update-time), from state c; records the time and the fp32 state after each step.  With
+// `detect`, stops before the first step whose event would pass the next snapshot (if any) or t_end
+// and returns its offset with its time in *t_cut; otherwise returns n.
+__device__ __forceinline__ int clock_run(const LatticeLaunch& p, const LatSmem& S, long long from, int n, bool detect,
+                                         bool has_snap, double snap_next, Clock c, double* t_cut) {
+  for (int i = 0; i < n; ++i) {
+    const int k = slot(from + i);
+    double tn;
+    float tfn = 0.0f, cfn = 0.0f;
+    if (p.precision == kP64LogSum) {
+      tn = c.t + S.taud[k];
+    } else {
+      const float tau = S.tauf[k];
+      if (p.precision == kP32Kahan) {
+        const float yk = tau - c.cf;
+        const float sum = c.tf + yk;
+        cfn = (sum - c.tf) - yk;
+        tfn = sum;
+        tn = (double)sum;
+      } else if (p.precision == kP32Plain) {
+        tfn = c.tf + tau;
+        tn = (double)tfn;
+      } else {
+        tn = c.t + (double)tau;
+      }
+    }
+    if (detect && ((has_snap && snap_next < tn) || tn > p.t_end)) {
+      *t_cut = tn;
+      return i;
+    }
+    S.tnew[k] = tn;
+    S.tf[k] = tfn;
+    S.cf[k] = cfn;
+    c.t = tn;
+    c.tf = tfn;
+    c.cf = cfn;
+  }
+  return n;
+}
+
+}  // namespace lat
+
+// Block: T step threads and one service warp.  The group's pending steps (at most T, with
+// consecutive indices [lo, hi)) sit in a ring; each round:
+//   A  (step threads) admits new steps up to T pending: the first Philox call of each (waiting
+//      time, site, plane 0 of n) and the sum of their waiting times, from which a bound on the
+//      last new event time tells whether they can pass a snapshot or t_end at all;
+//   B  (only if they can: the service warp, others waiting) the clock in step order up to the
+//      first step that would pass it: no step from there on is admitted until the snapshot;
+//   C  (step threads) the cap check: the first new step that might push a neighbour above the cap
+//      m is the last admitted until it has run (only it can double the cap, which changes K and
+//      the rate of every later step);
+//   D  (step threads) one wave: every pending step that no earlier pending step's closed
+//      neighbourhood (site and four neighbours) meets runs, all of them at once; lo moves to the
+//      first step still pending;
+//   meanwhile the service warp sums the clock of the new steps (when B did not) and replays the
+//   steps finished before this round into the runs' totals.
+// When every step before a stop (snapshot or t_end, a possible cap doubling, the step budget) has
+// run, the stop is handled and admission resumes.
 template <int P, int KW>
-__global__ void __launch_bounds__(kLatMaxBlock) lattice_kernel(const __grid_constant__ LatticeLaunch p) {
+__global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid_constant__ LatticeLaunch p) {
   using namespace lat;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int NT = blockDim.x, T = NT - 32, W = T >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool service = warp == W;
   const int M = p.M;
-  const LatSmem S = lat_smem(smem_raw, M, T);
+  const LatSmem S = lat_smem(smem_raw, M);
   __shared__ int s_wcnt[kLatMaxBlock / 32];
+  __shared__ double s_wsum[kLatMaxBlock / 32];
   __shared__ unsigned s_dom[32][2];
   __shared__ struct {
-    int cut, reason, ovcut, overflow, n_max;
+    int fcut, overflow, n_max, ncut, newlo, hadm;
     double t_cut;
+    Clock clk;
   } sh;
   const PhiloxKey key{(uint32_t)p.seed, (uint32_t)(p.seed >> 32)};
+  const double eps = p.precision == kP64LogSum || p.precision == kP32D64Acc ? 0x1p-52 : 0x1p-23;
+  const long long budget_stop = p.step_budget > 0 ? p.step_budget : kNoStop;
 
   for (long long gi = blockIdx.x; gi < p.n_groups; gi += gridDim.x) {
     const long long run0 = gi * 32;
@@ -408,9 +560,15 @@ __global__ void __launch_bounds__(kLatMaxBlock) lattice_kernel(const __grid_cons
     uint32_t* planes = p.planes + (size_t)gi * (size_t)M * (size_t)p.rec;
 
     // ---- initial state: planes from the counts, the cap table, the cap
-    if (tid == 0) sh.n_max = 0;
+    if (tid == 0) {
+      sh.n_max = 0;
+      sh.overflow = 0;
+      sh.clk.t = 0.0;
+      sh.clk.tf = 0.0f;
+      sh.clk.cf = 0.0f;
+    }
     __syncthreads();
-    for (int i = tid; i < M; i += T) {
+    for (int i = tid; i < M; i += NT) {
       uint32_t L[P], D[P], A[P];
 #pragma unroll
       for (int k = 0; k < P; ++k) L[k] = D[k] = A[k] = 0u;
@@ -433,36 +591,95 @@ __global__ void __launch_bounds__(kLatMaxBlock) lattice_kernel(const __grid_cons
       S.hopcnt[i] = 0u;
       atomicMax(&sh.n_max, (int)mx);
     }
-    // run `lane` of the group, kept by warp 0
-    long long tot[3] = {0, 0, 0}, reactions = 0, hops = 0;
-    double t_h = __longlong_as_double(0x7FF0000000000000ll);  // +inf
-    int outcome = -1;
-    if (warp == 0 && lane < lanes) {
+    RunBook rb;
+    rb.tot[0] = rb.tot[1] = rb.tot[2] = 0;
+    rb.reactions = rb.hops = 0;
+    rb.t_h = __longlong_as_double(0x7FF0000000000000ll);  // +inf
+    rb.outcome = -1;
+    if (service && lane < lanes) {
       for (int i = 0; i < M; ++i) {
         const int* c = p.init_per_run ? p.init + ((size_t)(run0 + lane) * M + i) * 3 : p.init + (size_t)i * 3;
-        tot[0] += c[0];
-        tot[1] += c[1];
-        tot[2] += c[2];
+        rb.tot[0] += c[0];
+        rb.tot[1] += c[1];
+        rb.tot[2] += c[2];
       }
-      const int kinds = (tot[0] > 0) + (tot[1] > 0) + (tot[2] > 0);
+      const int kinds = (rb.tot[0] > 0) + (rb.tot[1] > 0) + (rb.tot[2] > 0);
       if (kinds <= 1) {
-        t_h = 0.0;
-        outcome = tot[0] ? 0 : (tot[1] ? 1 : (tot[2] ? 2 : -1));
+        rb.t_h = 0.0;
+        rb.outcome = rb.tot[0] ? 0 : (rb.tot[1] ? 1 : (rb.tot[2] ? 2 : -1));
       }
     }
     __syncthreads();
     const int n_max = sh.n_max;
     int b = n_max > 1 ? bit_length((long long)(n_max - 1)) : 0;
     int status = b > P - 1 ? kLatBadInit : kLatOk;
-    long long s0 = 0, windows = 0, waves = 0, cuts = 0;
+    long long lo = 0, hi = 0, rep_lo = 0, stop = budget_stop;
+    int reason = p.step_budget > 0 ? kStopBudget : kStopNone;
+    double t_cut = 0.0;
+    long long rounds = 0, flags = 0, slow_rounds = 0;
     int raises = 0, next_snap = 0;
-    double t = 0.0;
-    float t_f = 0.0f, c_f = 0.0f;
 
     while (status == kLatOk) {
-      if (p.step_budget > 0 && s0 >= p.step_budget) {
-        status = kLatTimeout;
-        break;
+      // ---- a stop whose every earlier step has run
+      if (lo == hi && hi == stop) {
+        if (sh.overflow) {  // the possible doubling admitted last did push a site above m
+          ++b;
+          ++raises;
+        }
+        if (reason == kStopBudget) {
+          status = kLatTimeout;
+          break;
+        }
+        if (reason == kStopCross) {
+          // snapshots before the crossing step's event, after every earlier step's events
+          if (service) replay(rb, S, rep_lo, lo, lane, lane < lanes);
+          rep_lo = lo;
+          while (next_snap < p.n_snap && p.snap[next_snap] < t_cut) {
+            if (tid < 32) s_dom[tid][0] = s_dom[tid][1] = 0u;
+            __syncthreads();
+            unsigned myL = 0, myD = 0;
+            for (int base_s = warp * 32; base_s < M; base_s += NT) {
+              const int i = base_s + lane;
+              uint32_t gtL = 0u, gtD = 0u;
+              if (i < M) {
+                uint32_t L[P], D[P], A[P];
+                load_site<P>(planes + (size_t)i * p.rec, L, D, A);
+                gtL = bs::less_than<P>(D, L);
+                gtD = bs::less_than<P>(L, D);
+              }
+              for (int l = 0; l < 32; ++l) {
+                const unsigned cL = __popc(__ballot_sync(kFull, (gtL >> l) & 1u));
+                const unsigned cD = __popc(__ballot_sync(kFull, (gtD >> l) & 1u));
+                if (lane == l) {
+                  myL += cL;
+                  myD += cD;
+                }
+              }
+            }
+            atomicAdd(&s_dom[lane][0], myL);
+            atomicAdd(&s_dom[lane][1], myD);
+            __syncthreads();
+            if (service && lane < lanes) {
+              const size_t row = (size_t)next_snap * (size_t)p.n_runs + (size_t)(run0 + lane);
+              if (p.snap_totals) {
+                p.snap_totals[row * 3 + 0] = rb.tot[0];
+                p.snap_totals[row * 3 + 1] = rb.tot[1];
+                p.snap_totals[row * 3 + 2] = rb.tot[2];
+              }
+              if (p.snap_domains) {
+                p.snap_domains[row * 2 + 0] = (int)s_dom[lane][0];
+                p.snap_domains[row * 2 + 1] = (int)s_dom[lane][1];
+              }
+            }
+            __syncthreads();
+            ++next_snap;
+          }
+          if (t_cut > p.t_end) break;
+        }
+        __syncthreads();  // every thread has read sh.overflow
+        if (tid == 0) sh.overflow = 0;
+        stop = budget_stop;
+        reason = p.step_budget > 0 ? kStopBudget : kStopNone;
       }
       const LatCap cp = p.cap[b];
       if (cp.K > 32) {
@@ -473,102 +690,99 @@ __global__ void __launch_bounds__(kLatMaxBlock) lattice_kernel(const __grid_cons
         status = kLatCapacity;
         break;
       }
-      // ---- A: the waiting time, the site and plane 0 of n of each step of the window
-      {
-        const unsigned long long s = (unsigned long long)(s0 + tid);
-        const uint4 w = philox4x32_10(stream_counter(g, s, 0u, 2u, 0u), key);
-        if (p.precision == kP64LogSum) {
-          const unsigned long long x = ((unsigned long long)w.y << 21) | (unsigned long long)(w.x >> 11);
-          const double u = (double)(x + 1ull) * 0x1p-53;
-          S.taud[tid] = -log(u) / cp.lambda;
-        } else {
-          const float u = (float)((w.y >> 8) + 1u) * 0x1p-24f;
-          S.tauf[tid] = -logf(u) * cp.inv_lambda_f;
-        }
-        S.sigma[tid] = (int)(w.z & (uint32_t)(M - 1));
-        S.w3[tid] = w.w;
-        S.done[tid] = 0;
-      }
-      __syncthreads();
-      // ---- B: the group clock in step order; the window ends before a crossing or the budget
-      if (tid == 0) {
-        int cut = T, reason = 0;
-        double tc = 0.0, tt = t;
-        float ttf = t_f, tcf = c_f;
-        const double snap_next = next_snap < p.n_snap ? p.snap[next_snap] : 0.0;
-        for (int i = 0; i < T; ++i) {
-          if (p.step_budget > 0 && s0 + i >= p.step_budget) {
-            cut = i;
-            break;
-          }
-          double tn;
-          float tfn = 0.0f, cfn = 0.0f;
+      // ---- A: admit new steps
+      long long room = (long long)T - (hi - lo);
+      if (stop - hi < room) room = stop - hi;
+      int n_new = (int)room;
+      if (!service) {
+        double tau = 0.0;
+        if (tid < n_new) {
+          const long long s = hi + tid;
+          const int k = slot(s);
+          const uint4 w = philox4x32_10(stream_counter(g, (unsigned long long)s, 0u, 2u, 0u), key);
           if (p.precision == kP64LogSum) {
-            tn = tt + S.taud[i];
+            const unsigned long long x = ((unsigned long long)w.y << 21) | (unsigned long long)(w.x >> 11);
+            const double u = (double)(x + 1ull) * 0x1p-53;
+            tau = -log(u) / cp.lambda;
+            S.taud[k] = tau;
           } else {
-            const float tau = S.tauf[i];
-            if (p.precision == kP32Kahan) {
-              const float yk = tau - tcf;
-              const float sum = ttf + yk;
-              cfn = (sum - ttf) - yk;
-              tfn = sum;
-              tn = (double)sum;
-            } else if (p.precision == kP32Plain) {
-              tfn = ttf + tau;
-              tn = (double)tfn;
-            } else {
-              tn = tt + (double)tau;
-            }
+            const float u = (float)((w.y >> 8) + 1u) * 0x1p-24f;
+            const float tf = -logf(u) * cp.inv_lambda_f;
+            S.tauf[k] = tf;
+            tau = (double)tf;
           }
-          if ((next_snap < p.n_snap && snap_next < tn) || tn > p.t_end) {
-            cut = i;
-            reason = kCross;
-            tc = tn;
-            break;
-          }
-          S.tnew[i] = tn;
-          S.tf[i] = tfn;
-          S.cf[i] = tcf = cfn;
-          tt = tn;
-          ttf = tfn;
+          S.sigma[k] = (int)(w.z & (uint32_t)(M - 1));
+          S.w3[k] = w.w;
+          S.done[k] = 0;
         }
-        sh.cut = cut;
-        sh.reason = reason;
-        sh.t_cut = tc;
-        sh.overflow = 0;
-        sh.ovcut = T;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tau += __shfl_xor_sync(kFull, tau, o);
+        if (lane == 0) s_wsum[warp] = tau;
+        if (tid == 0) {
+          sh.fcut = T;
+          sh.newlo = T;
+        }
       }
       __syncthreads();
-      const int cut = sh.cut;
+      // a bound on the last new event time, above the sequential sum's rounding
+      const Clock c0 = sh.clk;
+      double sum = 0.0;
+      for (int w = 0; w < W; ++w) sum += s_wsum[w];
+      const double base = (p.precision == kP64LogSum || p.precision == kP32D64Acc) ? c0.t
+                                                                                     : (double)c0.tf + fabs((double)c0.cf);
+      const double bound = (base + sum) * (1.0 + (double)(T + 2) * eps);
+      const bool has_snap = next_snap < p.n_snap;
+      const double snap_next = has_snap ? p.snap[next_snap] : 0.0;
+      const bool slow = n_new > 0 && ((has_snap && !(bound <= snap_next)) || !(bound <= p.t_end));
+      if (slow) {
+        ++slow_rounds;
+        // ---- B: the exact clock finds the first new step that would pass a time point
+        if (service && lane == 0) {
+          double tc = 0.0;
+          sh.ncut = clock_run(p, S, hi, n_new, true, has_snap, snap_next, c0, &tc);
+          sh.t_cut = tc;
+        }
+        __syncthreads();
+        if (sh.ncut < n_new) {
+          n_new = sh.ncut;
+          stop = hi + n_new;
+          reason = kStopCross;
+          t_cut = sh.t_cut;
+        }
+      }
       const int m = 1 << b;
-      // ---- C: the first step that might raise the cap ends the window
-      int nb[4] = {0, 0, 0, 0};
-      if (tid < cut) {
-        neighbours(p, S.sigma[tid], nb);
+      const long long lo0 = lo, hi0 = hi;
+      if (!service) {
+        // ---- C: the cap check of the new steps
+        int nb[4] = {0, 0, 0, 0};
+        if (tid < n_new) {
+          neighbours(p, S.sigma[slot(hi0 + tid)], nb);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) atomicAdd(&S.hopcnt[nb[k]], 1u);
-      }
-      __syncthreads();
-      if (tid < cut) {
-        bool flag = false;
+          for (int k = 0; k < 4; ++k) atomicAdd(&S.hopcnt[nb[k]], 1u);
+        }
+        step_sync(T);
+        if (tid < n_new) {
+          bool flag = false;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) flag |= (unsigned)S.ub[nb[k]] + S.hopcnt[nb[k]] > (unsigned)m;
-        if (flag) atomicMin(&sh.ovcut, tid);
-      }
-      __syncthreads();
-      if (tid < cut) {
+          for (int k = 0; k < 4; ++k) flag |= (unsigned)S.ub[nb[k]] + S.hopcnt[nb[k]] > (unsigned)m;
+          if (flag) atomicMin(&sh.fcut, tid);
+        }
+        step_sync(T);
+        const int f = sh.fcut;
+        const int n_adm = f < n_new ? f + 1 : n_new;
+        if (tid >= n_adm && tid < n_new) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) S.hopcnt[nb[k]] = 0u;
-      }
-      const int e = sh.ovcut + 1 < cut ? sh.ovcut + 1 : cut;
-      if (e < cut) ++cuts;
-      // ---- D: waves of steps whose closed neighbourhoods meet no earlier pending step's
-      int done_n = 0;
-      while (done_n < e) {
-        const bool mine = tid < e && !S.done[tid];
+          for (int k = 0; k < 4; ++k) atomicSub(&S.hopcnt[nb[k]], 1u);
+        }
+        if (tid == 0) sh.hadm = n_adm;
+        const long long hi1 = hi0 + n_adm;
+        // ---- D: one wave over the pending steps [lo, hi1)
+        const int np = (int)(hi1 - lo0);
+        const int ks = slot(lo0 + tid);
+        const bool mine = tid < np && !S.done[ks];
         int c5[5];
         if (mine) {
-          c5[0] = S.sigma[tid];
+          c5[0] = S.sigma[ks];
           int n4[4];
           neighbours(p, c5[0], n4);
 #pragma unroll
@@ -576,7 +790,7 @@ __global__ void __launch_bounds__(kLatMaxBlock) lattice_kernel(const __grid_cons
 #pragma unroll
           for (int k = 0; k < 5; ++k) atomicMin(&S.stamp[c5[k]], (uint32_t)tid);
         }
-        __syncthreads();
+        step_sync(T);
         bool ready = false;
         if (mine) {
           ready = true;
@@ -585,140 +799,89 @@ __global__ void __launch_bounds__(kLatMaxBlock) lattice_kernel(const __grid_cons
         }
         const uint32_t bal = __ballot_sync(kFull, ready);
         if (lane == 0) s_wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int base = 0, total = 0;
-        for (int w = 0; w < (T >> 5); ++w) {
+        step_sync(T);
+        int base_w = 0, total = 0;
+        for (int w = 0; w < W; ++w) {
           const int cw = s_wcnt[w];
-          base += w < warp ? cw : 0;
+          base_w += w < warp ? cw : 0;
           total += cw;
         }
-        if (ready) S.ready[base + __popc(bal & ((1u << lane) - 1u))] = tid;
+        if (ready) S.ready[base_w + __popc(bal & ((1u << lane) - 1u))] = tid;
         if (mine) {
 #pragma unroll
           for (int k = 0; k < 5; ++k) S.stamp[c5[k]] = kNoStamp;
         }
-        __syncthreads();
+        step_sync(T);
         if (tid < total) {
-          const int i = S.ready[tid];
+          const long long s = lo0 + S.ready[tid];
+          const int k = slot(s);
           StepArgs a;
           a.group = g;
-          a.step = s0 + i;
-          a.sigma = S.sigma[i];
-          a.w3 = S.w3[i];
+          a.step = s;
+          a.sigma = S.sigma[k];
+          a.w3 = S.w3[k];
           a.b = b;
           a.K = cp.K;
           a.hop_slots = cp.hop_slots;
           a.planes = planes;
           const StepOut o = step<P, KW>(p, a, S.ub);
-          S.x1[i] = o.x1 & active;
-          S.x2[i] = o.x2 & active;
-          S.x3[i] = o.x3 & active;
-          S.hop[i] = o.hop & active;
-          S.done[i] = 1;
+          S.x1[k] = o.x1 & active;
+          S.x2[k] = o.x2 & active;
+          S.x3[k] = o.x3 & active;
+          S.hop[k] = o.hop & active;
+          S.done[k] = 1;
+          int n4[4];
+          neighbours(p, a.sigma, n4);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) atomicSub(&S.hopcnt[n4[j]], 1u);
           if (o.overflow) atomicOr(&sh.overflow, 1);
         }
-        __syncthreads();
-        done_n += total;
-        ++waves;
+        step_sync(T);
+        if (mine && !S.done[ks]) atomicMin(&sh.newlo, tid);
+      } else {
+        // the service warp: the clock of the new steps (unless B summed it), then the steps
+        // finished before this round into the runs' totals
+        if (!slow && lane == 0) {
+          double tc = 0.0;
+          clock_run(p, S, hi0, n_new, false, false, 0.0, c0, &tc);
+        }
+        __syncwarp();
+        if (lo0 > rep_lo) replay(rb, S, rep_lo, lo0, lane, lane < lanes);
       }
-      // ---- E: run `lane`'s totals and first single-species time, in step order
-      if (warp == 0 && lane < lanes) {
-        const uint32_t bit = 1u << lane;
-        for (int i = 0; i < e; ++i) {
-          const uint32_t r1 = S.x1[i] & bit, r2 = S.x2[i] & bit, r3 = S.x3[i] & bit;
-          hops += (S.hop[i] & bit) ? 1 : 0;
-          if (r1 | r2 | r3) {
-            ++reactions;
-            if (r1) {
-              ++tot[0];
-              --tot[2];
-            } else if (r2) {
-              ++tot[1];
-              --tot[2];
-            } else {
-              --tot[0];
-              --tot[1];
-              tot[2] += 2;
-            }
-            if (outcome == -1 && (tot[0] > 0) + (tot[1] > 0) + (tot[2] > 0) == 1) {
-              t_h = S.tnew[i];
-              outcome = tot[0] ? 0 : (tot[1] ? 1 : 2);
-            }
-          }
+      __syncthreads();
+      // ---- advance
+      const int n_adm = sh.hadm;
+      hi = hi0 + n_adm;
+      lo = sh.newlo < T ? lo0 + sh.newlo : hi;
+      rep_lo = lo0;
+      if (n_adm < n_new) {  // a possible cap doubling: admit nothing after it until it has run
+        ++flags;
+        if (hi < stop) {
+          stop = hi;
+          reason = kStopFlag;
         }
       }
-      // ---- F: advance the group
-      if (tid == 0 && e > 0) {
-        t = S.tnew[e - 1];
-        t_f = S.tf[e - 1];
-        c_f = S.cf[e - 1];
+      if (service && lane == 0 && n_adm > 0) {
+        const int k = slot(hi - 1);
+        sh.clk.t = S.tnew[k];
+        sh.clk.tf = S.tf[k];
+        sh.clk.cf = S.cf[k];
       }
-      s0 += e;
-      ++windows;
-      const bool overflow = sh.overflow != 0;
-      const bool cross = e == cut && !overflow && sh.reason == kCross;
-      const double t_cut = sh.t_cut;
-      __syncthreads();  // every thread has read sh before thread 0 writes it again
-      if (overflow) {
-        ++b;
-        ++raises;
-        continue;
-      }
-      if (!cross) continue;
-      // snapshots before the crossing step's event: lattice totals and domain counts of every run
-      while (next_snap < p.n_snap && p.snap[next_snap] < t_cut) {
-        if (tid < 32) s_dom[tid][0] = s_dom[tid][1] = 0u;
-        __syncthreads();
-        unsigned myL = 0, myD = 0;
-        for (int base = warp * 32; base < M; base += T) {
-          const int i = base + lane;
-          uint32_t gtL = 0u, gtD = 0u;
-          if (i < M) {
-            uint32_t L[P], D[P], A[P];
-            load_site<P>(planes + (size_t)i * p.rec, L, D, A);
-            gtL = bs::less_than<P>(D, L);
-            gtD = bs::less_than<P>(L, D);
-          }
-          for (int l = 0; l < 32; ++l) {
-            const unsigned cL = __popc(__ballot_sync(kFull, (gtL >> l) & 1u));
-            const unsigned cD = __popc(__ballot_sync(kFull, (gtD >> l) & 1u));
-            if (lane == l) {
-              myL += cL;
-              myD += cD;
-            }
-          }
-        }
-        atomicAdd(&s_dom[lane][0], myL);
-        atomicAdd(&s_dom[lane][1], myD);
-        __syncthreads();
-        if (warp == 0 && lane < lanes) {
-          const size_t row = (size_t)next_snap * (size_t)p.n_runs + (size_t)(run0 + lane);
-          if (p.snap_totals) {
-            p.snap_totals[row * 3 + 0] = tot[0];
-            p.snap_totals[row * 3 + 1] = tot[1];
-            p.snap_totals[row * 3 + 2] = tot[2];
-          }
-          if (p.snap_domains) {
-            p.snap_domains[row * 2 + 0] = (int)s_dom[lane][0];
-            p.snap_domains[row * 2 + 1] = (int)s_dom[lane][1];
-          }
-        }
-        __syncthreads();
-        ++next_snap;
-      }
-      if (t_cut > p.t_end) break;
+      ++rounds;
+      __syncthreads();  // every thread has read sh before it is written again
     }
+    if (service && lo > rep_lo) replay(rb, S, rep_lo, lo, lane, lane < lanes);
 
     // ---- outputs of the group
-    if (warp == 0) {
+    if (service) {
       if (lane < lanes) {
         const size_t r = (size_t)(run0 + lane);
-        p.t_homochiral[r] = t_h;
-        p.outcome[r] = (signed char)outcome;
-        p.events[2 * r] = reactions;
-        p.events[2 * r + 1] = hops;
+        p.t_homochiral[r] = rb.t_h;
+        p.outcome[r] = (signed char)rb.outcome;
+        p.events[2 * r] = rb.reactions;
+        p.events[2 * r + 1] = rb.hops;
       }
-      long long rs = lane < lanes ? reactions : 0, hs = lane < lanes ? hops : 0;
+      long long rs = lane < lanes ? rb.reactions : 0, hs = lane < lanes ? rb.hops : 0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         rs += __shfl_xor_sync(kFull, rs, o);
@@ -730,18 +893,18 @@ __global__ void __launch_bounds__(kLatMaxBlock) lattice_kernel(const __grid_cons
       }
     }
     if (tid == 0) {
-      p.group_info[3 * gi] = s0;
+      p.group_info[3 * gi] = lo;
       p.group_info[3 * gi + 1] = b;
       p.group_info[3 * gi + 2] = status;
-      atomicAdd(&p.counters[kLatGroupSteps], (unsigned long long)s0);
-      atomicAdd(&p.counters[kLatWindows], (unsigned long long)windows);
-      atomicAdd(&p.counters[kLatWaves], (unsigned long long)waves);
+      atomicAdd(&p.counters[kLatGroupSteps], (unsigned long long)lo);
+      atomicAdd(&p.counters[kLatRounds], (unsigned long long)rounds);
+      atomicAdd(&p.counters[kLatClockRounds], (unsigned long long)slow_rounds);
       atomicAdd(&p.counters[kLatCapRaises], (unsigned long long)raises);
-      atomicAdd(&p.counters[kLatCutWindows], (unsigned long long)cuts);
+      atomicAdd(&p.counters[kLatFlagged], (unsigned long long)flags);
       if (status != kLatOk) atomicAdd(&p.counters[kLatErrors], 1ull);
     }
     if (p.final_counts) {
-      for (int i = tid; i < M; i += T) {
+      for (int i = tid; i < M; i += NT) {
         uint32_t L[P], D[P], A[P];
         load_site<P>(planes + (size_t)i * p.rec, L, D, A);
         for (int l = 0; l < lanes; ++l) {
