@@ -107,6 +107,20 @@ def algorithmic_ops_per_group_step(K: int, b: int, pad: int = 0) -> int:
     return {0: 27, 1: 26, 2: 28}[int(pad)] * K + 6 * b + 20 * ((K + 2 + 3) // 4)
 
 
+def lattice_ops_per_group_step(K: int, b: int, rho_r: int) -> int:
+    """Word operations of one group step of the lattice kernel, with B = b + 1 count planes (the
+    cap m = 2^b needs them) and K planes of n: the hop test (K), the molecule's species by two
+    adds and three comparisons over B planes (7B), the three products A L, A (L + D) and L D by
+    schoolbook (3 x 3B^2: AND, sum, carry) and S_3's add (4B), n minus the hop slots (2K), rho_r S_r
+    for the three sums (2K an add per further set bit of rho_r), three comparisons over K planes
+    (3K), the changer words (6), the masked updates of three counts (12B), and 20 LOP3 per Philox
+    call for the ceil((K + 3) / 4) calls of the step's words."""
+    B = b + 1
+    extra_bits = max(0, bin(int(rho_r)).count("1") - 1)
+    return (K + 7 * B + 9 * B * B + 4 * B + 2 * K + 3 * 2 * K * extra_bits + 3 * K + 6 + 12 * B
+            + 20 * ((K + 3 + 3) // 4))
+
+
 def bit_length(v: int) -> int:
     return int(v).bit_length()
 
@@ -257,6 +271,60 @@ def workload_config_single(world):
             "l2": "L2 flushed between timed steps (256 MiB write)"}
 
 
+C5_SIDE, C5_RUNS, C5_HOP = 64, 4096, 0.1
+
+
+def lattice_leg(pkg, stream, local, t_end, rank, world, flush, runs=C5_RUNS):
+    """Frank's model on the 64 x 64 periodic lattice: 4096 runs per GPU from per-site Poisson
+    counts of means (8, 8, 16), unit rates, hops at d = 0.1, fp32 Kahan clock, one snapshot at
+    t_end / 2; one warm-up run, then two runs timed with CUDA events after an L2 flush.  Lane
+    steps count every run of every group step; the roofline counts the word operations of each
+    group's steps at its final cap."""
+    import torch
+    from paper_2412_16613_gb300 import sharding, workloads
+    M = C5_SIDE * C5_SIDE
+    init = workloads.lattice_init(C5_SIDE, C5_SIDE, runs)
+    o = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=pkg.SSA_P32_KAHAN,
+                                first_run=sharding.weak_shard(runs, rank)[0])
+    ctx = pkg.ssa_lattice_create(C5_SIDE, C5_SIDE, [1.0, 1.0, 1.0], C5_HOP, init, runs, SEED, o)
+    snaps = [t_end / 2]
+    pkg.ssa_lattice_run(ctx, t_end, snaps)
+    ms, steps_total, react, hops, ops = [], 0, 0, 0, 0.0
+    rho_r = int(round(1.0 / C5_HOP))
+    for k in range(2):
+        flush.fill_(k + 11)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pkg.ssa_lattice_run(ctx, t_end, snaps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        cnt = pkg.ssa_lattice_fetch(ctx, pkg.SSA_LAT_COUNTERS)
+        groups = pkg.ssa_lattice_fetch(ctx, pkg.SSA_LAT_GROUPS).reshape(-1, 3)
+        steps_total += int(cnt[0])
+        react += int(cnt[3])
+        hops += int(cnt[4])
+        for steps_g, b_g, _ in groups.tolist():
+            m = 1 << int(b_g)
+            K = bit_length(4 * m + rho_r * (m * (m - 1) // 2) - 1)
+            ops += steps_g * lattice_ops_per_group_step(K, int(b_g), rho_r)
+    pkg.ssa_lattice_destroy(ctx)
+    t = sum(ms) / 1e3
+    sms, max_mhz, basis = device_sm_count_and_max_mhz(local)
+    peak = sms * 64 * max_mhz * 1e6 / 1e9
+    caps = np.bincount(groups[:, 1].astype(np.int64)).tolist()
+    return {"workload": f"lattice_{C5_SIDE}x{C5_SIDE}_poisson8-8-16_runs{runs}xgpu_d{C5_HOP:g}_tend{t_end:g}_p32kahan",
+            "t_end": t_end, "t_end_of_the_workload": 50.0, "steps": 2, "warmup": 1,
+            "ms_per_step": statistics.mean(ms), "group_steps_per_s": steps_total * world / t,
+            "lane_steps_per_s": 32 * steps_total * world / t, "lane_reactions_per_s": react * world / t,
+            "lane_hops_per_s": hops * world / t, "groups_by_cap_bits": caps,
+            "rounds_per_group": int(cnt[1]) / max(1, len(groups)),
+            "roofline": {"bound": "alu", "achieved": ops / t / 1e9, "peak": peak, "unit": "Gop/s",
+                         "frac": ops / t / 1e9 / peak,
+                         "ops_per_group_step_at_b6": lattice_ops_per_group_step(15, 6, rho_r),
+                         "peak_basis": f"{sms} SMs x 64 LOP3 lanes/clk/SM x {max_mhz:g} MHz ({basis})"}}
+
+
 ENGINE_NAMES = {0: "Frank kernels (cumulative propensities, App. A increments)",
                 2: "general kernel (propensities by bit-sliced products every step)"}
 
@@ -274,6 +342,9 @@ def main():
     ap.add_argument("--c4-steps", type=int, default=3,
                     help="timed runs of the N_tot = 10 000, 2^22-run workload per bound after the main "
                          "measurement (0: skip)")
+    ap.add_argument("--c5-tend", type=float, default=0.05,
+                    help="t_end of the lattice leg (64 x 64 sites, 4096 runs, d = 0.1, fp32 Kahan clock) "
+                         "timed after the main measurement (0: skip); the workload's own t_end is 50")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--layout", type=int, default=0,
                     help="0 auto, 1 one thread per group of 32 runs, 2 three warps per 32 groups")
@@ -295,10 +366,12 @@ def main():
                          "line then covers that phase only and says so)")
     ap.add_argument("--runs", type=int, default=0,
                     help="runs per GPU (smaller cases are for profiling; the metric is quoted at 2^20)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: N_tot=1024, 2^20 runs (the metric's workload); c3: 4096 ensembles "
                          "with log-uniform N_tot in [16, 65536] and rates in [0.5, 2], 1024 runs each; "
-                         "c4: N_tot=10000, 2^22 runs")
+                         "c4: N_tot=10000, 2^22 runs; c5: the lattice leg alone (--c5-tend, --c5-runs), "
+                         "for profiling it")
+    ap.add_argument("--c5-runs", type=int, default=0, help="runs of the lattice leg (default 4096)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     set_workload(args.workload, args.runs)
@@ -321,6 +394,15 @@ def main():
     import torch
     import paper_2412_16613_gb300 as pkg
     torch.cuda.set_device(local)
+    if WORKLOAD == "c5":  # the lattice leg alone, on rank 0's GPU (a profiling line)
+        pkg.build()
+        pkg.use_torch_allocator()
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+        line = lattice_leg(pkg, torch.cuda.current_stream(), local, args.c5_tend or 0.05, 0, 1, flush,
+                           runs=args.c5_runs or C5_RUNS)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -598,6 +680,9 @@ def main():
                 "value": val4 * world, "unit": "lane-reactions/s", "max_group_steps": int(cnt4[8]),
                 "layout": layout_name(int(cnt4[9])),
                 "roofline": roofline_of(10000, pad, float(cnt4[0]), ms4, engine=0, layout_bits=int(cnt4[9]))}
+    # ---- the lattice workload (Frank's model on a 64 x 64 torus with hops), to a short t_end
+    if args.c5_tend > 0 and WORKLOAD == "c2" and ENGINE == 0 and PRECISION == 0:
+        result["c5"] = lattice_leg(pkg, stream, local, args.c5_tend, rank, world, flush)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
