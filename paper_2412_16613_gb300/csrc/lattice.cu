@@ -181,6 +181,13 @@ int bitlen(unsigned long long v) {
 
 bool pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// The largest float at or below v (finite v >= 0).
+float float_at_or_below(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+
 size_t field_bytes(const ssa_lattice* c, int field) {
   const size_t nr = (size_t)c->n_runs, M = (size_t)c->M, ns = (size_t)c->n_snap;
   switch (field) {
@@ -430,6 +437,8 @@ int ssa_lattice_run(ssa_lattice* c, double t_end, const double* snapshot_times, 
     return lcuda(c, e, "clear counters");
   LatticeLaunch lp = c->lp;
   lp.t_end = t_end;
+  lp.t_end_f = float_at_or_below(t_end);
+  for (int i = 0; i < n_snap; ++i) lp.snap_f[i] = float_at_or_below(snapshot_times[i]);
   lp.snap = n_snap > 0 ? c->d_snap : nullptr;
   lp.n_snap = n_snap;
   lp.snap_totals = n_snap > 0 ? c->d_snap_tot : nullptr;

@@ -71,6 +71,8 @@ struct LatticeLaunch {
   double t_end;
   const double* snap;             // [n_snap]
   int n_snap;
+  float t_end_f;                  // the largest float <= t_end: for an fp32 clock value f,
+  float snap_f[kLatMaxSnap];      // f > t_end_f <=> (double)f > t_end; likewise each snapshot time
   long long step_budget;          // 0 = none
   LatCap cap[kLatMaxPlanes + 1];  // b = 0 .. P
   const int* init;                // [n_runs][M][3] or [M][3]

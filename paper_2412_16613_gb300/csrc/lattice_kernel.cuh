@@ -185,32 +185,35 @@ struct StepOut {
   unsigned ub_sigma;         // largest site total at sigma after the step
 };
 
+// Planes 1 .. 4 NC of n (those below K; the rest stay zero) from calls 1 .. NC of the step's stream.
+template <int KW, int NC>
+__device__ __forceinline__ void draw_planes(uint32_t (&n)[KW], const StepArgs& a, PhiloxKey key) {
+  uint32_t w[4 * NC];
+  philox4x32_10_block<NC>(w, stream_counter(a.group, (unsigned long long)a.step, 0u, 2u, 0u), 1u, key);
+#pragma unroll
+  for (int j = 0; j < 4 * NC; ++j) {
+    const int i = 1 + j;
+    if (i < KW) n[i] = i < a.K ? w[j] : 0u;
+  }
+}
+
 // One step of the group at its site, all 32 runs at once; updates the site and the neighbours
 // a run hops to, and the cap table ub.
 template <int P, int KW>
 __device__ __forceinline__ StepOut step(const LatticeLaunch& p, const StepArgs& a, uint16_t* ub) {
   constexpr int SW = 2 * P - 1;  // S_3 <= m^2 / 3 < 2^(2P - 2)
   const PhiloxKey key{(uint32_t)p.seed, (uint32_t)(p.seed >> 32)};
-  // (1) the planes of n: word 3 + i is plane i, i < K; planes at and above K are zero
+  // (1) the planes of n: word 3 + i is plane i, i < K; planes at and above K are zero.  The calls
+  //     beyond the first (planes 1 .. K - 1: calls 1 .. (K + 2) / 4) run as one interleaved block.
   uint32_t n[KW];
+#pragma unroll
+  for (int i = 0; i < KW; ++i) n[i] = 0u;
   n[0] = a.K > 0 ? a.w3 : 0u;
-#pragma unroll
-  for (int c = 1; 4 * c - 3 < KW; ++c) {
-    if (4 * c - 3 < a.K) {
-      const uint4 w = philox4x32_10(stream_counter(a.group, (unsigned long long)a.step, 0u, 2u, (uint32_t)c), key);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int i = 4 * c - 3 + e;
-        if (i < KW) n[i] = i < a.K ? word_of(w, e) : 0u;
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int i = 4 * c - 3 + e;
-        if (i < KW) n[i] = 0u;
-      }
-    }
-  }
+  const int nc = (a.K + 2) / 4;
+  if (nc <= 2) draw_planes<KW, 2>(n, a, key);
+  else if (nc <= 4) draw_planes<KW, 4>(n, a, key);
+  else if (nc <= 6) draw_planes<KW, 6>(n, a, key);
+  else draw_planes<KW, 8>(n, a, key);
   uint32_t* rec = a.planes + (size_t)a.sigma * p.rec;
   uint32_t L[P], D[P], A[P];
   load_site<P>(rec, L, D, A);
@@ -420,7 +423,8 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t v, int lane) {
 // reaches zero stays at zero, so a run that still holds two species after the range held two
 // throughout it; only a run left with one species replays the range in step order, to find the
 // event after which its lattice first held one species.
-__device__ __forceinline__ void replay(RunBook& r, const LatSmem& S, long long a, long long b, int lane, bool mine) {
+__device__ __forceinline__ void replay(RunBook& r, const LatSmem& S, long long a, long long b, int lane, bool mine,
+                                      bool f32) {
   int n1 = 0, n2 = 0, n3 = 0, nh = 0;
   for (long long base = a; base < b; base += 32) {
     const long long i = base + lane;
@@ -458,7 +462,7 @@ __device__ __forceinline__ void replay(RunBook& r, const LatSmem& S, long long a
       t2 += 2;
     }
     if ((t0 > 0) + (t1 > 0) + (t2 > 0) == 1) {
-      r.t_h = S.tnew[k];
+      r.t_h = f32 ? (double)S.tf[k] : S.tnew[k];
       r.outcome = t0 ? 0 : (t1 ? 1 : 2);
       break;
     }
@@ -472,42 +476,50 @@ struct Clock {
 };
 
 // The group clock over steps [from, from + n), in step order (Eq. equation-tau, Eq.
-// eq-update-time), from state c; records the time and the fp32 state after each step.  With
-// `detect`, stops before the first step whose event would pass the next snapshot (if any) or t_end
-// and returns its offset with its time in *t_cut; otherwise returns n.
+// eq-update-time), from state c; records the clock after each step (the fp32 sum and its
+// compensation in the fp32 modes, else the fp64 time).  With `detect`, stops before the first step
+// whose event would pass the next snapshot (if any) or t_end and returns its offset with its time
+// in *t_cut; otherwise returns n.  The fp32 sums compare against the largest floats at or below the
+// time points, which decides exactly as comparing (double) of the sum with the time point.
 __device__ __forceinline__ int clock_run(const LatticeLaunch& p, const LatSmem& S, long long from, int n, bool detect,
-                                         bool has_snap, double snap_next, Clock c, double* t_cut) {
+                                         bool has_snap, int next_snap, Clock c, double* t_cut) {
+  if (p.precision == kP32Kahan || p.precision == kP32Plain) {
+    const bool kahan = p.precision == kP32Kahan;
+    const float snap_f = has_snap ? p.snap_f[next_snap] : 0.0f;
+    float tf = c.tf, cf = c.cf;
+    for (int i = 0; i < n; ++i) {
+      const int k = slot(from + i);
+      const float tau = S.tauf[k];
+      float tfn, cfn = 0.0f;
+      if (kahan) {
+        const float yk = tau - cf;
+        const float sum = tf + yk;
+        cfn = (sum - tf) - yk;
+        tfn = sum;
+      } else {
+        tfn = tf + tau;
+      }
+      if (detect && ((has_snap && tfn > snap_f) || tfn > p.t_end_f)) {
+        *t_cut = (double)tfn;
+        return i;
+      }
+      S.tf[k] = tfn;
+      S.cf[k] = cfn;
+      tf = tfn;
+      cf = cfn;
+    }
+    return n;
+  }
+  const double snap_next = has_snap ? p.snap[next_snap] : 0.0;
   for (int i = 0; i < n; ++i) {
     const int k = slot(from + i);
-    double tn;
-    float tfn = 0.0f, cfn = 0.0f;
-    if (p.precision == kP64LogSum) {
-      tn = c.t + S.taud[k];
-    } else {
-      const float tau = S.tauf[k];
-      if (p.precision == kP32Kahan) {
-        const float yk = tau - c.cf;
-        const float sum = c.tf + yk;
-        cfn = (sum - c.tf) - yk;
-        tfn = sum;
-        tn = (double)sum;
-      } else if (p.precision == kP32Plain) {
-        tfn = c.tf + tau;
-        tn = (double)tfn;
-      } else {
-        tn = c.t + (double)tau;
-      }
-    }
+    const double tn = p.precision == kP64LogSum ? c.t + S.taud[k] : c.t + (double)S.tauf[k];
     if (detect && ((has_snap && snap_next < tn) || tn > p.t_end)) {
       *t_cut = tn;
       return i;
     }
     S.tnew[k] = tn;
-    S.tf[k] = tfn;
-    S.cf[k] = cfn;
     c.t = tn;
-    c.tf = tfn;
-    c.cf = cfn;
   }
   return n;
 }
@@ -542,6 +554,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
   const LatSmem S = lat_smem(smem_raw, M);
   __shared__ int s_wcnt[kLatMaxBlock / 32];
   __shared__ double s_wsum[kLatMaxBlock / 32];
+  __shared__ float s_wsumf[kLatMaxBlock / 32];
   __shared__ unsigned s_dom[32][2];
   __shared__ struct {
     int fcut, overflow, n_max, ncut, newlo, hadm;
@@ -549,7 +562,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
     Clock clk;
   } sh;
   const PhiloxKey key{(uint32_t)p.seed, (uint32_t)(p.seed >> 32)};
-  const double eps = p.precision == kP64LogSum || p.precision == kP32D64Acc ? 0x1p-52 : 0x1p-23;
+  const bool f32 = p.precision == kP32Kahan || p.precision == kP32Plain;  // the clock is an fp32 sum
   const long long budget_stop = p.step_budget > 0 ? p.step_budget : kNoStop;
 
   for (long long gi = blockIdx.x; gi < p.n_groups; gi += gridDim.x) {
@@ -632,7 +645,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
         }
         if (reason == kStopCross) {
           // snapshots before the crossing step's event, after every earlier step's events
-          if (service) replay(rb, S, rep_lo, lo, lane, lane < lanes);
+          if (service) replay(rb, S, rep_lo, lo, lane, lane < lanes, f32);
           rep_lo = lo;
           while (next_snap < p.n_snap && p.snap[next_snap] < t_cut) {
             if (tid < 32) s_dom[tid][0] = s_dom[tid][1] = 0u;
@@ -696,6 +709,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       int n_new = (int)room;
       if (!service) {
         double tau = 0.0;
+        float tauf = 0.0f;
         if (tid < n_new) {
           const long long s = hi + tid;
           const int k = slot(s);
@@ -707,39 +721,52 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
             S.taud[k] = tau;
           } else {
             const float u = (float)((w.y >> 8) + 1u) * 0x1p-24f;
-            const float tf = -logf(u) * cp.inv_lambda_f;
-            S.tauf[k] = tf;
-            tau = (double)tf;
+            tauf = -logf(u) * cp.inv_lambda_f;
+            S.tauf[k] = tauf;
           }
           S.sigma[k] = (int)(w.z & (uint32_t)(M - 1));
           S.w3[k] = w.w;
           S.done[k] = 0;
         }
+        if (f32) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tau += __shfl_xor_sync(kFull, tau, o);
-        if (lane == 0) s_wsum[warp] = tau;
+          for (int o = 16; o > 0; o >>= 1) tauf += __shfl_xor_sync(kFull, tauf, o);
+          if (lane == 0) s_wsumf[warp] = tauf;
+        } else {
+          if (p.precision == kP32D64Acc) tau = (double)tauf;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) tau += __shfl_xor_sync(kFull, tau, o);
+          if (lane == 0) s_wsum[warp] = tau;
+        }
         if (tid == 0) {
           sh.fcut = T;
           sh.newlo = T;
         }
       }
       __syncthreads();
-      // a bound on the last new event time, above the sequential sum's rounding
+      // a bound on the last new event time, above the sequential sum's rounding (at most one
+      // rounding a step, and the tree sum's own, well inside the margin)
       const Clock c0 = sh.clk;
-      double sum = 0.0;
-      for (int w = 0; w < W; ++w) sum += s_wsum[w];
-      const double base = (p.precision == kP64LogSum || p.precision == kP32D64Acc) ? c0.t
-                                                                                     : (double)c0.tf + fabs((double)c0.cf);
-      const double bound = (base + sum) * (1.0 + (double)(T + 2) * eps);
       const bool has_snap = next_snap < p.n_snap;
-      const double snap_next = has_snap ? p.snap[next_snap] : 0.0;
-      const bool slow = n_new > 0 && ((has_snap && !(bound <= snap_next)) || !(bound <= p.t_end));
+      bool slow;
+      if (f32) {
+        float sum = 0.0f;
+        for (int w = 0; w < W; ++w) sum += s_wsumf[w];
+        const float bound = (c0.tf + fabsf(c0.cf) + sum) * (1.0f + (float)(T + 2) * 0x1p-21f);
+        slow = n_new > 0 && ((has_snap && !(bound <= p.snap_f[next_snap])) || !(bound <= p.t_end_f));
+      } else {
+        double sum = 0.0;
+        for (int w = 0; w < W; ++w) sum += s_wsum[w];
+        const double bound = (c0.t + sum) * (1.0 + (double)(T + 2) * 0x1p-50);
+        const double snap_next = has_snap ? p.snap[next_snap] : 0.0;
+        slow = n_new > 0 && ((has_snap && !(bound <= snap_next)) || !(bound <= p.t_end));
+      }
       if (slow) {
         ++slow_rounds;
         // ---- B: the exact clock finds the first new step that would pass a time point
         if (service && lane == 0) {
           double tc = 0.0;
-          sh.ncut = clock_run(p, S, hi, n_new, true, has_snap, snap_next, c0, &tc);
+          sh.ncut = clock_run(p, S, hi, n_new, true, has_snap, next_snap, c0, &tc);
           sh.t_cut = tc;
         }
         __syncthreads();
@@ -788,7 +815,13 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
 #pragma unroll
           for (int k = 0; k < 4; ++k) c5[k + 1] = n4[k];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) atomicMin(&S.stamp[c5[k]], (uint32_t)tid);
+          for (int k = 0; k < 5; ++k) {
+            atomicMin(&S.stamp[c5[k]], (uint32_t)tid);
+            // the records the step will read, brought to L1 while the wave is sorted out
+            const uint32_t* r = planes + (size_t)c5[k] * p.rec;
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(r + p.rec - 1));
+          }
         }
         step_sync(T);
         bool ready = false;
@@ -843,10 +876,10 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
         // finished before this round into the runs' totals
         if (!slow && lane == 0) {
           double tc = 0.0;
-          clock_run(p, S, hi0, n_new, false, false, 0.0, c0, &tc);
+          clock_run(p, S, hi0, n_new, false, false, 0, c0, &tc);
         }
         __syncwarp();
-        if (lo0 > rep_lo) replay(rb, S, rep_lo, lo0, lane, lane < lanes);
+        if (lo0 > rep_lo) replay(rb, S, rep_lo, lo0, lane, lane < lanes, f32);
       }
       __syncthreads();
       // ---- advance
@@ -863,14 +896,17 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       }
       if (service && lane == 0 && n_adm > 0) {
         const int k = slot(hi - 1);
-        sh.clk.t = S.tnew[k];
-        sh.clk.tf = S.tf[k];
-        sh.clk.cf = S.cf[k];
+        if (f32) {
+          sh.clk.tf = S.tf[k];
+          sh.clk.cf = S.cf[k];
+        } else {
+          sh.clk.t = S.tnew[k];
+        }
       }
       ++rounds;
       __syncthreads();  // every thread has read sh before it is written again
     }
-    if (service && lo > rep_lo) replay(rb, S, rep_lo, lo, lane, lane < lanes);
+    if (service && lo > rep_lo) replay(rb, S, rep_lo, lo, lane, lane < lanes, f32);
 
     // ---- outputs of the group
     if (service) {
