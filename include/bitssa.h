@@ -350,8 +350,8 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
  * rate d.  If a hop leaves a site of any run above m, m doubles from the next step.  Runs go on to
  * t_end; the time at which a run's lattice first holds a single species is kept.
  *
- * Up to block_size consecutive steps of a group are pending at once; a step waits only for
- * earlier pending steps whose site or neighbours meet its own, so every run follows the serial
+ * Up to twice block_size consecutive steps of a group are pending at once; a step waits only
+ * for earlier pending steps whose site or neighbours meet its own, so every run follows the serial
  * definition above exactly; results do not depend on the block size.
  */
 typedef struct ssa_lattice ssa_lattice;
@@ -385,8 +385,8 @@ enum {
  *     (n0_per_run = 1); each site count in [0, 32768].
  *   n_runs >= 0, seed: as in ssa_create (run j is lane j % 32 of group j / 32).
  *   opt: precision (SSA_P64 and SSA_P64_LOGSUM both give tau = -log(u) / Lambda summed in fp64;
- *     SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P32_PLAIN as for ssa_create), thin_bits, block_size (steps
- *     pending at once, a multiple of 32 up to 224; 0 = 224), step_budget, first_run, cuda_stream, device.
+ *     SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P32_PLAIN as for ssa_create), thin_bits, block_size (step
+ *     threads, each holding two pending steps; a multiple of 32 up to 224; 0 = 224), step_budget, first_run, cuda_stream, device.
  *     Other fields must keep their defaults (SSA_EUNSUPPORTED otherwise).
  *   cap_bits_max: the largest cap bits b the runs may reach, 0 = the initial cap (no doubling
  *     beyond what the planes chosen for it hold); at most 15.  The planes per count are the

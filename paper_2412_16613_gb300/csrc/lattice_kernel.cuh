@@ -334,11 +334,12 @@ __device__ __forceinline__ StepOut step(const LatticeLaunch& p, const StepArgs& 
 
 }  // namespace lat
 
-// Steps of a group held at once: the pending steps (at most one per step thread) and the steps
-// finished but not yet replayed into the runs' totals.  A power of two, at least twice the
-// largest window.
-constexpr int kLatRing = 512;
-static_assert(kLatRing >= 2 * kLatMaxBlock, "the ring must hold two windows");
+// Pending steps per step thread (the pool of a group holds kLatSlots T steps).
+constexpr int kLatSlots = 2;
+// Steps of a group held at once: the pending steps and the steps finished but not yet replayed
+// into the runs' totals.  A power of two, at least twice the largest pool.
+constexpr int kLatRing = 1024;
+static_assert(kLatRing >= 2 * kLatSlots * kLatMaxBlock, "the ring must hold two pools");
 
 // Shared-memory layout of a block: per site, the stamp and hop-count tables (uint32) and the cap
 // table ub (uint16, the largest site total over the group's runs); per step, in a ring indexed by
@@ -360,7 +361,7 @@ struct LatSmem {
   uint32_t* x3;
   uint32_t* hop;
   int* done;
-  int* ready;     // [T]
+  int* ready;     // [kLatSlots T]
 };
 
 __device__ __forceinline__ LatSmem lat_smem(unsigned char* base, int M) {
@@ -526,9 +527,9 @@ __device__ __forceinline__ int clock_run(const LatticeLaunch& p, const LatSmem& 
 
 }  // namespace lat
 
-// Block: T step threads and one service warp.  The group's pending steps (at most T, with
-// consecutive indices [lo, hi)) sit in a ring; each round:
-//   A  (step threads) admits new steps up to T pending: the first Philox call of each (waiting
+// Block: T step threads and one service warp.  The group's pending steps (at most 2T, with
+// consecutive indices [lo, hi), two pool offsets per step thread) sit in a ring; each round:
+//   A  (step threads) admits new steps up to 2T pending: the first Philox call of each (waiting
 //      time, site, plane 0 of n) and the sum of their waiting times, from which a bound on the
 //      last new event time tells whether they can pass a snapshot or t_end at all;
 //   B  (only if they can: the service warp, others waiting) the clock in step order up to the
@@ -537,8 +538,8 @@ __device__ __forceinline__ int clock_run(const LatticeLaunch& p, const LatSmem& 
 //      m is the last admitted until it has run (only it can double the cap, which changes K and
 //      the rate of every later step);
 //   D  (step threads) one wave: every pending step that no earlier pending step's closed
-//      neighbourhood (site and four neighbours) meets runs, all of them at once; lo moves to the
-//      first step still pending;
+//      neighbourhood (site and four neighbours) meets runs, up to one per step thread, all at
+//      once; lo moves to the first step still pending;
 //   meanwhile the service warp sums the clock of the new steps (when B did not) and replays the
 //   steps finished before this round into the runs' totals.
 // When every step before a stop (snapshot or t_end, a possible cap doubling, the step budget) has
@@ -547,7 +548,7 @@ template <int P, int KW>
 __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid_constant__ LatticeLaunch p) {
   using namespace lat;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int NT = blockDim.x, T = NT - 32, W = T >> 5;
+  const int NT = blockDim.x, T = NT - 32, W = T >> 5, C = kLatSlots * T;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool service = warp == W;
   const int M = p.M;
@@ -703,44 +704,50 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
         status = kLatCapacity;
         break;
       }
-      // ---- A: admit new steps
-      long long room = (long long)T - (hi - lo);
+      // ---- A: admit new steps (pool offsets tid and tid + T of each step thread)
+      long long room = (long long)C - (hi - lo);
       if (stop - hi < room) room = stop - hi;
       int n_new = (int)room;
       if (!service) {
         double tau = 0.0;
         float tauf = 0.0f;
-        if (tid < n_new) {
-          const long long s = hi + tid;
-          const int k = slot(s);
-          const uint4 w = philox4x32_10(stream_counter(g, (unsigned long long)s, 0u, 2u, 0u), key);
-          if (p.precision == kP64LogSum) {
-            const unsigned long long x = ((unsigned long long)w.y << 21) | (unsigned long long)(w.x >> 11);
-            const double u = (double)(x + 1ull) * 0x1p-53;
-            tau = -log(u) / cp.lambda;
-            S.taud[k] = tau;
-          } else {
-            const float u = (float)((w.y >> 8) + 1u) * 0x1p-24f;
-            tauf = -logf(u) * cp.inv_lambda_f;
-            S.tauf[k] = tauf;
+#pragma unroll
+        for (int j = 0; j < kLatSlots; ++j) {
+          const int idx = tid + j * T;
+          if (idx < n_new) {
+            const long long s = hi + idx;
+            const int k = slot(s);
+            const uint4 w = philox4x32_10(stream_counter(g, (unsigned long long)s, 0u, 2u, 0u), key);
+            if (p.precision == kP64LogSum) {
+              const unsigned long long x = ((unsigned long long)w.y << 21) | (unsigned long long)(w.x >> 11);
+              const double u = (double)(x + 1ull) * 0x1p-53;
+              const double td = -log(u) / cp.lambda;
+              S.taud[k] = td;
+              tau += td;
+            } else {
+              const float u = (float)((w.y >> 8) + 1u) * 0x1p-24f;
+              const float tf = -logf(u) * cp.inv_lambda_f;
+              S.tauf[k] = tf;
+              tauf += tf;
+              if (p.precision == kP32D64Acc) tau += (double)tf;
+            }
+            S.sigma[k] = (int)(w.z & (uint32_t)(M - 1));
+            S.w3[k] = w.w;
+            S.done[k] = 0;
           }
-          S.sigma[k] = (int)(w.z & (uint32_t)(M - 1));
-          S.w3[k] = w.w;
-          S.done[k] = 0;
         }
         if (f32) {
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) tauf += __shfl_xor_sync(kFull, tauf, o);
           if (lane == 0) s_wsumf[warp] = tauf;
         } else {
-          if (p.precision == kP32D64Acc) tau = (double)tauf;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) tau += __shfl_xor_sync(kFull, tau, o);
           if (lane == 0) s_wsum[warp] = tau;
         }
         if (tid == 0) {
-          sh.fcut = T;
-          sh.newlo = T;
+          sh.fcut = C;
+          sh.newlo = C;
         }
       }
       __syncthreads();
@@ -752,12 +759,12 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       if (f32) {
         float sum = 0.0f;
         for (int w = 0; w < W; ++w) sum += s_wsumf[w];
-        const float bound = (c0.tf + fabsf(c0.cf) + sum) * (1.0f + (float)(T + 2) * 0x1p-21f);
+        const float bound = (c0.tf + fabsf(c0.cf) + sum) * (1.0f + (float)(C + 2) * 0x1p-21f);
         slow = n_new > 0 && ((has_snap && !(bound <= p.snap_f[next_snap])) || !(bound <= p.t_end_f));
       } else {
         double sum = 0.0;
         for (int w = 0; w < W; ++w) sum += s_wsum[w];
-        const double bound = (c0.t + sum) * (1.0 + (double)(T + 2) * 0x1p-50);
+        const double bound = (c0.t + sum) * (1.0 + (double)(C + 2) * 0x1p-50);
         const double snap_next = has_snap ? p.snap[next_snap] : 0.0;
         slow = n_new > 0 && ((has_snap && !(bound <= snap_next)) || !(bound <= p.t_end));
       }
@@ -781,57 +788,80 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       const long long lo0 = lo, hi0 = hi;
       if (!service) {
         // ---- C: the cap check of the new steps
-        int nb[4] = {0, 0, 0, 0};
-        if (tid < n_new) {
-          neighbours(p, S.sigma[slot(hi0 + tid)], nb);
+        int nb[kLatSlots][4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) atomicAdd(&S.hopcnt[nb[k]], 1u);
+        for (int j = 0; j < kLatSlots; ++j) {
+          const int idx = tid + j * T;
+          if (idx < n_new) {
+            neighbours(p, S.sigma[slot(hi0 + idx)], nb[j]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(&S.hopcnt[nb[j][k]], 1u);
+          }
         }
         step_sync(T);
-        if (tid < n_new) {
-          bool flag = false;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) flag |= (unsigned)S.ub[nb[k]] + S.hopcnt[nb[k]] > (unsigned)m;
-          if (flag) atomicMin(&sh.fcut, tid);
+        for (int j = 0; j < kLatSlots; ++j) {
+          const int idx = tid + j * T;
+          if (idx < n_new) {
+            bool flag = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) flag |= (unsigned)S.ub[nb[j][k]] + S.hopcnt[nb[j][k]] > (unsigned)m;
+            if (flag) atomicMin(&sh.fcut, idx);
+          }
         }
         step_sync(T);
         const int f = sh.fcut;
         const int n_adm = f < n_new ? f + 1 : n_new;
-        if (tid >= n_adm && tid < n_new) {
 #pragma unroll
-          for (int k = 0; k < 4; ++k) atomicSub(&S.hopcnt[nb[k]], 1u);
+        for (int j = 0; j < kLatSlots; ++j) {
+          const int idx = tid + j * T;
+          if (idx >= n_adm && idx < n_new) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicSub(&S.hopcnt[nb[j][k]], 1u);
+          }
         }
         if (tid == 0) sh.hadm = n_adm;
         const long long hi1 = hi0 + n_adm;
-        // ---- D: one wave over the pending steps [lo, hi1)
+        // ---- D: one wave over the pending steps [lo, hi1) (offsets tid and tid + T)
         const int np = (int)(hi1 - lo0);
-        const int ks = slot(lo0 + tid);
-        const bool mine = tid < np && !S.done[ks];
-        int c5[5];
-        if (mine) {
-          c5[0] = S.sigma[ks];
-          int n4[4];
-          neighbours(p, c5[0], n4);
+        int ks[kLatSlots], c5[kLatSlots][5];
+        bool mine[kLatSlots], ready[kLatSlots];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) c5[k + 1] = n4[k];
+        for (int j = 0; j < kLatSlots; ++j) {
+          const int off = tid + j * T;
+          ks[j] = slot(lo0 + off);
+          mine[j] = off < np && !S.done[ks[j]];
+          if (mine[j]) {
+            c5[j][0] = S.sigma[ks[j]];
+            int n4[4];
+            neighbours(p, c5[j][0], n4);
 #pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            atomicMin(&S.stamp[c5[k]], (uint32_t)tid);
-            // the records the step will read, brought to L1 while the wave is sorted out
-            const uint32_t* r = planes + (size_t)c5[k] * p.rec;
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(r + p.rec - 1));
+            for (int k = 0; k < 4; ++k) c5[j][k + 1] = n4[k];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              atomicMin(&S.stamp[c5[j][k]], (uint32_t)off);
+              // the records the step will read, brought to L1 while the wave is sorted out
+              const uint32_t* r = planes + (size_t)c5[j][k] * p.rec;
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(r + p.rec - 1));
+            }
           }
         }
         step_sync(T);
-        bool ready = false;
-        if (mine) {
-          ready = true;
+        uint32_t bal[kLatSlots];
+        int mycount = 0;
 #pragma unroll
-          for (int k = 0; k < 5; ++k) ready &= S.stamp[c5[k]] == (uint32_t)tid;
+        for (int j = 0; j < kLatSlots; ++j) {
+          const int off = tid + j * T;
+          ready[j] = mine[j];
+          if (mine[j]) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) ready[j] &= S.stamp[c5[j][k]] == (uint32_t)off;
+          }
+          bal[j] = __ballot_sync(kFull, ready[j]);
+          mycount += __popc(bal[j]);
         }
-        const uint32_t bal = __ballot_sync(kFull, ready);
-        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        if (lane == 0) s_wcnt[warp] = mycount;
         step_sync(T);
         int base_w = 0, total = 0;
         for (int w = 0; w < W; ++w) {
@@ -839,12 +869,17 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
           base_w += w < warp ? cw : 0;
           total += cw;
         }
-        if (ready) S.ready[base_w + __popc(bal & ((1u << lane) - 1u))] = tid;
-        if (mine) {
 #pragma unroll
-          for (int k = 0; k < 5; ++k) S.stamp[c5[k]] = kNoStamp;
+        for (int j = 0; j < kLatSlots; ++j) {
+          if (ready[j]) S.ready[base_w + __popc(bal[j] & ((1u << lane) - 1u))] = tid + j * T;
+          base_w += __popc(bal[j]);
+          if (mine[j]) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) S.stamp[c5[j][k]] = kNoStamp;
+          }
         }
         step_sync(T);
+        // at most one ready step per thread runs; ready steps left over stay ready for the next round
         if (tid < total) {
           const long long s = lo0 + S.ready[tid];
           const int k = slot(s);
@@ -870,7 +905,9 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
           if (o.overflow) atomicOr(&sh.overflow, 1);
         }
         step_sync(T);
-        if (mine && !S.done[ks]) atomicMin(&sh.newlo, tid);
+#pragma unroll
+        for (int j = 0; j < kLatSlots; ++j)
+          if (mine[j] && !S.done[ks[j]]) atomicMin(&sh.newlo, tid + j * T);
       } else {
         // the service warp: the clock of the new steps (unless B summed it), then the steps
         // finished before this round into the runs' totals
@@ -885,7 +922,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       // ---- advance
       const int n_adm = sh.hadm;
       hi = hi0 + n_adm;
-      lo = sh.newlo < T ? lo0 + sh.newlo : hi;
+      lo = sh.newlo < C ? lo0 + sh.newlo : hi;
       rep_lo = lo0;
       if (n_adm < n_new) {  // a possible cap doubling: admit nothing after it until it has run
         ++flags;
