@@ -107,15 +107,14 @@ def algorithmic_ops_per_group_step(K: int, b: int, pad: int = 0) -> int:
     return {0: 27, 1: 26, 2: 28}[int(pad)] * K + 6 * b + 20 * ((K + 2 + 3) // 4)
 
 
-def lattice_ops_per_group_step(K: int, b: int, rho_r: int) -> int:
-    """Word operations of one group step of the lattice kernel, with B = b + 1 count planes (the
-    cap m = 2^b needs them) and K planes of n: the hop test (K), the molecule's species by two
+def lattice_ops_per_group_step(K: int, B: int, rho_r: int) -> int:
+    """Word operations of one group step of the lattice kernel, with B count planes (the bit length
+    of the cap m) and K planes of n: the hop test (K), the molecule's species by two
     adds and three comparisons over B planes (7B), the three products A L, A (L + D) and L D by
     schoolbook (3 x 3B^2: AND, sum, carry) and S_3's add (4B), n minus the hop slots (2K), rho_r S_r
     for the three sums (2K an add per further set bit of rho_r), three comparisons over K planes
     (3K), the changer words (6), the masked updates of three counts (12B), and 20 LOP3 per Philox
     call for the ceil((K + 3) / 4) calls of the step's words."""
-    B = b + 1
     extra_bits = max(0, bin(int(rho_r)).count("1") - 1)
     return (K + 7 * B + 9 * B * B + 4 * B + 2 * K + 3 * 2 * K * extra_bits + 3 * K + 6 + 12 * B
             + 20 * ((K + 3 + 3) // 4))
@@ -306,10 +305,9 @@ def lattice_leg(pkg, stream, local, t_end, rank, world, flush, runs=C5_RUNS, tim
         steps_total += int(cnt[0])
         react += int(cnt[3])
         hops += int(cnt[4])
-        for steps_g, b_g, _ in groups.tolist():
-            m = 1 << int(b_g)
-            K = bit_length(4 * m + rho_r * (m * (m - 1) // 2) - 1)
-            ops += steps_g * lattice_ops_per_group_step(K, int(b_g), rho_r)
+        for steps_g, m, _ in groups.tolist():
+            K = bit_length(4 * (1 << bit_length(m - 1)) + rho_r * (m * (m - 1) // 2) - 1)
+            ops += steps_g * lattice_ops_per_group_step(K, bit_length(m), rho_r)
     # the workload's outputs at the last snapshot: global ee of every run and its domain counts
     tot = pkg.ssa_lattice_fetch(ctx, pkg.SSA_LAT_SNAP_TOTALS).reshape(len(snaps), -1, 3)[-1].astype(np.float64)
     dom = pkg.ssa_lattice_fetch(ctx, pkg.SSA_LAT_SNAP_DOMAINS).reshape(len(snaps), -1, 2)[-1]
@@ -323,16 +321,16 @@ def lattice_leg(pkg, stream, local, t_end, rank, world, flush, runs=C5_RUNS, tim
     t = sum(ms) / 1e3
     sms, max_mhz, basis = device_sm_count_and_max_mhz(local)
     peak = sms * 64 * max_mhz * 1e6 / 1e9
-    caps = np.bincount(groups[:, 1].astype(np.int64)).tolist()
+    caps = {int(m): int(c) for m, c in zip(*np.unique(groups[:, 1], return_counts=True))}
     return {"workload": f"lattice_{C5_SIDE}x{C5_SIDE}_poisson8-8-16_runs{runs}xgpu_d{C5_HOP:g}_tend{t_end:g}_p32kahan",
             "t_end": t_end, "t_end_of_the_workload": 50.0, "steps": timed, "warmup": int(warm),
             "ms_per_step": statistics.mean(ms), "group_steps_per_s": steps_total * world / t,
             "lane_steps_per_s": 32 * steps_total * world / t, "lane_reactions_per_s": react * world / t,
-            "lane_hops_per_s": hops * world / t, "groups_by_cap_bits": caps,
+            "lane_hops_per_s": hops * world / t, "groups_by_cap": caps,
             "rounds_per_group": int(cnt[1]) / max(1, len(groups)), "outputs": outputs,
             "roofline": {"bound": "alu", "achieved": ops / t / 1e9, "peak": peak, "unit": "Gop/s",
                          "frac": ops / t / 1e9 / peak,
-                         "ops_per_group_step_at_b6": lattice_ops_per_group_step(15, 6, rho_r),
+                         "ops_per_group_step_at_cap_64": lattice_ops_per_group_step(15, 7, rho_r),
                          "peak_basis": f"{sms} SMs x 64 LOP3 lanes/clk/SM x {max_mhz:g} MHz ({basis})"}}
 
 

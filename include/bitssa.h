@@ -332,9 +332,10 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
  * The 32 runs of a group share one word per count plane per site (Sec. 4's binary words, one
  * set per site) and the site of every step; each run picks its own event there.  Uniformisation
  * is exact: with u = min(k_max, d), rho_r = k_max / u and rho_h = d / u must be integers
- * (rho_r < 65536); the group keeps an occupancy cap m = 2^b at or above every site count of its
- * runs (initially the smallest such power of two), c(m) = 4 rho_h m + rho_r m (m - 1) / 2 slots
- * per site, K = bit_length(c(m) - 1) <= 32, and its steps come at rate Lambda = M 2^K u.  Step s of
+ * (rho_r < 65536); the group keeps an occupancy cap m at or above every site count of its runs,
+ * one of 1 .. 8 or (4 + j) 2^e (j = 0 .. 3: 10, 12, 14, 16, 20, ...), initially the smallest such
+ * cap; with bh = bit_length(m - 1), a site has c(m) = 4 rho_h 2^bh + rho_r m (m - 1) / 2 slots,
+ * K = bit_length(c(m) - 1) <= 32, and the group's steps come at rate Lambda = M 2^K u.  Step s of
  * group g uses word k = element k % 4 of Philox4x32-10(key = seed, counter = (g, s lo 32,
  * s hi 16 | 2 << 24, k / 4)):
  *   w0, w1: the waiting time tau = -ln(u) / Lambda, u = (x + 1) 2^-53 from x = w1 2^21 + (w0 >> 11),
@@ -342,12 +343,12 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
  *   w2: the site sigma = w2 & (M - 1) of every run of the group;
  *   w3 .. w3+K-1: plane i of run l's n is bit l of w_{3+i};
  *   w35 ..: thinning, the q-bit U whose bit q-1-i is bit l of w_{35+i}.
- * Run l with counts (L, D, A) at sigma: if n < 4 rho_h m, a hop in direction n & 3 (x+1, x-1, y+1,
- * y-1) of molecule i = (n >> 2) & (m - 1): an L if i < L, a D if i < L + D, an A if i < L + D + A,
- * else nothing; otherwise reaction r if 4 rho_h m + rho_r S_{r-1} <= n < 4 rho_h m + rho_r S_r
+ * Run l with counts (L, D, A) at sigma: if n < H = 4 rho_h 2^bh, a hop in direction n & 3 (x+1,
+ * x-1, y+1, y-1) of molecule i = (n >> 2) & (2^bh - 1): an L if i < L, a D if i < L + D, an A if
+ * i < L + D + A, else nothing; otherwise reaction r if H + rho_r S_{r-1} <= n < H + rho_r S_r
  * (S_r = h_1 + .. + h_r), kept iff U < floor(k_r / k_max 2^q) when k_r < k_max, nothing above S_3.
  * A run thus jumps by reaction r at rate k_r h_r and moves a given molecule in a given direction at
- * rate d.  If a hop leaves a site of any run above m, m doubles from the next step.  Runs go on to
+ * rate d.  If a hop leaves a site of any run above m, m moves to the next cap from the next step.  Runs go on to
  * t_end; the time at which a run's lattice first holds a single species is kept.
  *
  * Up to twice block_size consecutive steps of a group are pending at once; a step waits only
@@ -366,9 +367,10 @@ enum {
   SSA_LAT_SNAP_TOTALS = 4,    /* int64[n_snap][n_runs][3]: lattice totals of (L, D, A) at each
                                  snapshot (the state after every event with time <= t_snap) */
   SSA_LAT_SNAP_DOMAINS = 5,   /* int32[n_snap][n_runs][2]: sites with L > D and sites with D > L */
-  SSA_LAT_GROUPS = 6,         /* int64[n_groups][3]: steps of the group, its final cap bits b, and
-                                 its stop status (0 t_end, 1 step budget, 2 K above 32 planes,
-                                 3 cap above the context's planes) */
+  SSA_LAT_GROUPS = 6,         /* int64[n_groups][3]: steps of the group, its final cap m (the cap
+                                 it needed, when it stopped for want of planes), and its stop
+                                 status (0 t_end, 1 step budget, 2 K above 32 planes, 3 cap above
+                                 the context's planes) */
   SSA_LAT_COUNTERS = 7        /* uint64[8]: group steps, rounds (one wave of ready steps each),
                                  rounds whose new steps might pass a snapshot or t_end (the clock
                                  ran before admission), reactions, hops, cap doublings, groups
@@ -388,9 +390,9 @@ enum {
  *     SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P32_PLAIN as for ssa_create), thin_bits, block_size (step
  *     threads, each holding two pending steps; a multiple of 32 up to 224; 0 = 224), step_budget, first_run, cuda_stream, device.
  *     Other fields must keep their defaults (SSA_EUNSUPPORTED otherwise).
- *   cap_bits_max: the largest cap bits b the runs may reach, 0 = the initial cap (no doubling
- *     beyond what the planes chosen for it hold); at most 15.  The planes per count are the
- *     smallest of 4, 8, 12, 16 above it; a run whose cap would outgrow them stops with
+ *   cap_bits_max: the runs may reach caps up to 2^cap_bits_max; 0 = what the count planes chosen
+ *     for the initial cap hold; at most 15.  The planes per count are the smallest of 4, 8, 12, 16
+ *     above it (caps up to 8, 128, 2048, 32768); a run whose cap would outgrow them stops with
  *     SSA_EOVERFLOW.
  * Returns SSA_EINVAL for bad arguments, SSA_EUNSUPPORTED beyond the limits above.
  */

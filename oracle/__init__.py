@@ -69,7 +69,7 @@ class Lattice(C.Structure):
 class LatticeResult(C.Structure):
     _fields_ = [
         ("t_homochiral", C.c_double), ("outcome", C.c_int32), ("status", C.c_int32), ("steps", C.c_int64),
-        ("reactions", C.c_int64), ("hops", C.c_int64), ("cap_bits", C.c_int32), ("pad", C.c_int32),
+        ("reactions", C.c_int64), ("hops", C.c_int64), ("cap", C.c_int32), ("pad", C.c_int32),
         ("margin", C.c_double),
     ]
 
@@ -325,5 +325,5 @@ def lattice_run(lx, ly, init, n_runs=None, *, rates=(1.0, 1.0, 1.0), hop=0.1, se
         "t_homochiral": np.array(res["t_homochiral"]), "outcome": np.array(res["outcome"]),
         "run_status": np.array(res["status"]), "steps": np.array(res["steps"]),
         "reactions": np.array(res["reactions"]), "hops": np.array(res["hops"]),
-        "cap_bits": np.array(res["cap_bits"]), "margin": np.array(res["margin"]),
+        "cap": np.array(res["cap"]), "margin": np.array(res["margin"]),
     }

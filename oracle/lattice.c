@@ -26,6 +26,15 @@ static int lat_bit_length(uint64_t v) {
 
 static int is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
+/* The smallest occupancy cap at or above v >= 1: caps are 1 .. 8 and then the numbers with a two-bit
+ * mantissa, (4 + j) 2^e for j = 0 .. 3 (10, 12, 14, 16, 20, 24, 28, 32, 40, ...). */
+static int64_t lat_cap_at_or_above(int64_t v) {
+  if (v <= 8) return v < 1 ? 1 : v;
+  const int e = lat_bit_length((uint64_t)(v - 1)) - 3; /* 4 2^e < v <= 8 2^e */
+  const int64_t unit = (int64_t)1 << e;
+  return (v + unit - 1) / unit * unit;
+}
+
 /* Word k of the lattice stream of group g at step s (tag 2). */
 typedef struct {
   uint32_t key[2];
@@ -125,7 +134,7 @@ int orc_lattice_group(const orc_lattice* p, uint64_t group, int32_t lanes, const
       out[l].outcome = tot[l][0] ? 0 : (tot[l][1] ? 1 : (tot[l][2] ? 2 : -1));
     }
   }
-  int b = lat_bit_length(n_max > 1 ? (uint64_t)(n_max - 1) : 0); /* m = 2^b >= n_max */
+  int64_t m = lat_cap_at_or_above(n_max); /* the cap: every site count of every run <= m */
 
   lat_words ws;
   memset(&ws, 0, sizeof ws);
@@ -141,8 +150,8 @@ int orc_lattice_group(const orc_lattice* p, uint64_t group, int32_t lanes, const
       status = ORC_ETIMEOUT;
       break;
     }
-    const int64_t m = (int64_t)1 << b;
-    const int64_t hop_slots = 4 * rho_h * m;
+    const int bh = lat_bit_length((uint64_t)(m - 1)); /* molecule index bits: 2^bh >= m */
+    const int64_t hop_slots = 4 * rho_h * ((int64_t)1 << bh);
     const uint64_t c_m = (uint64_t)hop_slots + (uint64_t)rho_r * (uint64_t)(m * (m - 1) / 2);
     const int K = lat_bit_length(c_m - 1);
     if (K > 32) { /* the cap no longer fits the stream's 32 planes of n */
@@ -222,9 +231,9 @@ int orc_lattice_group(const orc_lattice* p, uint64_t group, int32_t lanes, const
       for (int i = 0; i < K; i++)
         draw |= (uint64_t)((lat_word(&ws, group, (uint64_t)step, 3 + (uint32_t)i) >> l) & 1u) << i;
       if (draw < (uint64_t)hop_slots) {
-        /* a hop: direction from the low two bits, the molecule from the next b bits */
+        /* a hop: direction from the low two bits, the molecule from the next bh bits */
         const int dir = (int)(draw & 3u);
-        const int64_t mol = (int64_t)((draw >> 2) & (uint64_t)(m - 1));
+        const int64_t mol = (int64_t)((draw >> 2) & (((uint64_t)1 << bh) - 1));
         int species = -1;
         if (mol < sv[0]) species = 0;
         else if (mol < sv[0] + sv[1]) species = 1;
@@ -272,12 +281,12 @@ int orc_lattice_group(const orc_lattice* p, uint64_t group, int32_t lanes, const
       }
     }
     step++;
-    if (overflow) b++;
+    if (overflow) m = lat_cap_at_or_above(m + 1);
   }
 
   for (int l = 0; l < lanes; l++) {
     out[l].steps = step;
-    out[l].cap_bits = b;
+    out[l].cap = (int32_t)m;
     out[l].status = status;
     if (final_counts)
       memcpy(&final_counts[(int64_t)l * M * 3], &n[(int64_t)l * M * 3], sizeof(int64_t) * (size_t)M * 3);

@@ -162,24 +162,25 @@ int orc_run_many(const orc_problem* p, int64_t first_run, const int64_t* run_ids
  * over the lattice, not per site.
  *
  * Uniformisation, exact: with u = min(k_max, d), rho_r = k_max / u and rho_h = d / u must be
- * integers.  The runs of a group of 32 share an occupancy cap m = 2^b with every site count of
- * every run <= m; c(m) = 4 rho_h m + rho_r m (m - 1) / 2, K = bit_length(c(m) - 1), and the rate
- * of a step is Lambda = M 2^K u.  One step of group g at step s uses word k = element k % 4 of
+ * integers.  The runs of a group of 32 share an occupancy cap m with every site count of every
+ * run <= m, m one of 1 .. 8 or a number with a two-bit mantissa (4 + j) 2^e (j = 0 .. 3: 10, 12,
+ * 14, 16, 20, 24, ...); with bh = bit_length(m - 1) (2^bh >= m), a site has c(m) = 4 rho_h 2^bh +
+ * rho_r m (m - 1) / 2 slots, K = bit_length(c(m) - 1), and the rate of a step is Lambda = M 2^K u.  One step of group g at step s uses word k = element k % 4 of
  * Philox4x32-10(key = seed, ctr = (g, s lo 32, s hi 16 | 2 << 24, k / 4)):
  *   w0, w1: the waiting time, as for the well-mixed group clock (u53 or its top 24 bits);
  *   w2: the site, sigma = w2 & (M - 1), shared by the runs of the group;
  *   w3 .. w3+K-1: the planes of n (run l: n = sum_i bit_l(w_{3+i}) 2^i), uniform on [0, 2^K);
  *   w35 ..: thinning, U = the q-bit number whose bit q-1-i is bit_l(w_{35+i}).
  * Run l with counts (L, D, A) at sigma, n_s = L + D + A:
- *   n < 4 rho_h m: a hop: direction n & 3 (x+1, x-1, y+1, y-1), molecule i = (n >> 2) & (m - 1);
- *     i < L: an L hops, i < L + D: a D, i < n_s: an A, else nothing;
- *   else the reaction r with 4 rho_h m + rho_r S_{r-1} <= n < 4 rho_h m + rho_r S_r (S_r = sum_{p<=r}
- *     h_p), kept iff U < T_r = floor(k_r / k_max 2^q) (always when k_r = k_max); none if n is
- *     at or above 4 rho_h m + rho_r S_3.
+ *   n < H = 4 rho_h 2^bh: a hop: direction n & 3 (x+1, x-1, y+1, y-1), molecule
+ *     i = (n >> 2) & (2^bh - 1); i < L: an L hops, i < L + D: a D, i < n_s: an A, else nothing;
+ *   else the reaction r with H + rho_r S_{r-1} <= n < H + rho_r S_r (S_r = sum_{p<=r} h_p), kept
+ *     iff U < T_r = floor(k_r / k_max 2^q) (always when k_r = k_max); none if n is at or above
+ *     H + rho_r S_3.
  * A run then jumps by reaction r at sigma at rate (Lambda / M)(rho_r h_r / 2^K)(k_r / k_max) =
  * k_r h_r and moves a given molecule in a given direction at rate (Lambda / M)(1 / 2^K) = d.  After
- * the step, if a hop left a site of any run above m, b grows by one for the next steps (a bound
- * that changes with the state, between steps).  Initially m is the smallest power of two at or
+ * the step, if a hop left a site of any run above m, m becomes the next cap for the next steps
+ * (a bound that changes with the state, between steps).  Initially m is the smallest cap at or
  * above every site count of the group's runs.  Runs do not stop before t_end: the output keeps
  * the time at which a run's whole lattice first holds a single species (global homochirality). */
 typedef struct {
@@ -202,7 +203,7 @@ typedef struct {
   int64_t steps;            /* the group's steps */
   int64_t reactions;        /* this run's reactions */
   int64_t hops;             /* this run's hops */
-  int32_t cap_bits;         /* b of the group's final cap m = 2^b */
+  int32_t cap;              /* the group's final cap m */
   int32_t pad;
   double margin;            /* smallest relative gap between a snapshot / t_end and an event time */
 } orc_lattice_result;

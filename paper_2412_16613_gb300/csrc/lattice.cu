@@ -181,6 +181,13 @@ int bitlen(unsigned long long v) {
 
 bool pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// The smallest occupancy cap at or above v >= 1: 1 .. 8, then (4 + j) 2^e, j = 0 .. 3.
+unsigned long long cap_at_or_above(unsigned long long v) {
+  if (v <= 8) return v < 1 ? 1 : v;
+  const unsigned long long unit = 1ull << (bitlen(v - 1) - 3);  // 4 unit < v <= 8 unit
+  return (v + unit - 1) / unit * unit;
+}
+
 // The largest float at or below v (finite v >= 0).
 float float_at_or_below(double v) {
   float f = (float)v;
@@ -274,22 +281,32 @@ int ssa_lattice_create(int32_t lx, int32_t ly, const double* rates, double hop, 
     n_max = std::max(n_max, site);
   }
   if (n_max > 32768) return lfail(nullptr, SSA_EUNSUPPORTED, "site totals above 32768 are not supported");
-  const int b0 = n_max > 1 ? bitlen((unsigned long long)(n_max - 1)) : 0;
-  auto K_of = [&](int b) {
-    const unsigned long long m = 1ull << b;
-    const unsigned long long cm = 4ull * (unsigned long long)rho_h * m + (unsigned long long)rho_r * (m * (m - 1) / 2);
-    return bitlen(cm - 1);
-  };
+  // the caps 1 .. 8 and (4 + j) 2^e, with their slots c(m) = 4 rho_h 2^bh + rho_r m (m - 1) / 2 and K
+  std::vector<LatCap> levels;
+  for (unsigned long long m = 1; m <= 65536 && levels.size() < (size_t)kLatMaxLevels;) {
+    LatCap cp{};
+    cp.m = (unsigned)m;
+    cp.bh = bitlen(m - 1);
+    const unsigned long long hop_slots = 4ull * (unsigned long long)rho_h << cp.bh;
+    const unsigned long long cm = hop_slots + (unsigned long long)rho_r * (m * (m - 1) / 2);
+    cp.K = bitlen(cm - 1);
+    cp.lambda = cp.K <= 32 ? (double)M * std::ldexp(unit, cp.K) : 0.0;
+    cp.inv_lambda_f = cp.K <= 32 ? (float)(1.0 / cp.lambda) : 0.0f;
+    cp.hop_slots = cp.K <= 32 ? (unsigned)hop_slots : 0u;
+    levels.push_back(cp);
+    m = cap_at_or_above(m + 1);  // the next cap above m
+  }
+  const int b0 = n_max > 1 ? bitlen((unsigned long long)(n_max - 1)) : 0;  // 2^b0 >= the first cap
   const int need = std::max(b0, (int)cap_bits_max);
   int P = 0;
   for (int cand : {4, 8, 12, 16}) {
     if (cand - 1 < need) continue;
     const int KW = lattice_draw_planes(cand);
     bool fits = true;
-    for (int b = b0; b <= cand - 1; ++b) {
-      const int K = K_of(b);
-      if (K > 32) break;  // the run stops there, as the definition does
-      if (K > KW || (KW < 32 && K == KW)) fits = false;
+    for (const LatCap& cp : levels) {
+      if (cp.m < (unsigned long long)std::max<long long>(n_max, 1) || cp.m > (1u << (cand - 1))) continue;
+      if (cp.K > 32) break;  // the run stops there, as the definition does
+      if (cp.K > KW || (KW < 32 && cp.K == KW)) fits = false;
     }
     if (fits) {
       P = cand;
@@ -352,14 +369,8 @@ int ssa_lattice_create(int32_t lx, int32_t ly, const double* rates, double hop, 
   }
   lp.precision = precision;
   lp.step_budget = o.step_budget;
-  for (int b = 0; b <= kLatMaxPlanes; ++b) {
-    LatCap& cp = lp.cap[b];
-    const int K = b <= 16 ? K_of(b) : 64;
-    cp.K = K;
-    cp.lambda = K <= 32 ? (double)M * std::ldexp(unit, K) : 0.0;
-    cp.inv_lambda_f = K <= 32 ? (float)(1.0 / cp.lambda) : 0.0f;
-    cp.hop_slots = K <= 32 ? (unsigned)(4ull * (unsigned long long)rho_h << b) : 0u;
-  }
+  lp.n_levels = (int)levels.size();
+  for (size_t i = 0; i < levels.size(); ++i) lp.cap[i] = levels[i];
   lp.init_per_run = n0_per_run;
   {
     LatDeviceGuard guard(c->device);

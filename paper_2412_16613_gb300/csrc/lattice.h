@@ -9,9 +9,10 @@
 // binary-word representation of Sec. 4 with one word per count plane per site.  Uniformisation
 // is exact: with u = min(k_max, d), rho_r = k_max / u and rho_h = d / u integers and an
 // occupancy cap m = 2^b at or above every site count of the group's runs, a site holds
-// c(m) = 4 rho_h m + rho_r m (m - 1) / 2 slots, the group draws K = bit_length(c(m) - 1) planes,
-// and its steps come at rate Lambda = M 2^K u.  A hop that leaves a site of a run above m doubles
-// m from the next step on.
+// c(m) = 4 rho_h 2^bh + rho_r m (m - 1) / 2 slots (2^bh the power of two at or above m), the group
+// draws K = bit_length(c(m) - 1) planes, and its steps come at rate Lambda = M 2^K u.  Caps are 1 .. 8
+// and the numbers with a two-bit mantissa, (4 + j) 2^e; a hop that leaves a site of a run above m
+// moves m to the next cap from the next step on.
 #pragma once
 
 #include <cstdint>
@@ -25,6 +26,7 @@ constexpr int kLatMaxBlock = 224;   // pending steps of a group at most (step th
 constexpr int kLatDefaultWindow = 224;
 constexpr int kLatRhoBits = 16;     // rho_r below 2^16
 constexpr int kLatCounters = 8;
+constexpr int kLatMaxLevels = 64;   // caps 1 .. 8 and four per octave up to 2^16
 
 // Indices into the lattice kernel's counter array (uint64).
 enum LatCounter {
@@ -47,12 +49,14 @@ enum LatStatus {
   kLatBadInit = 4    // an initial site count above the launch's capacity
 };
 
-// Constants of one occupancy cap m = 2^b.
+// Constants of one occupancy cap m.
 struct LatCap {
   double lambda;          // M 2^K u
   float inv_lambda_f;     // (float)(1 / lambda)
   int K;                  // bit length of c(m) - 1; above 32: outside the stream
-  unsigned int hop_slots; // 4 rho_h m
+  unsigned int hop_slots; // 4 rho_h 2^bh
+  unsigned int m;         // the cap
+  int bh;                 // bit length of m - 1: planes of the molecule index
 };
 
 struct LatticeLaunch {
@@ -74,7 +78,8 @@ struct LatticeLaunch {
   float t_end_f;                  // the largest float <= t_end: for an fp32 clock value f,
   float snap_f[kLatMaxSnap];      // f > t_end_f <=> (double)f > t_end; likewise each snapshot time
   long long step_budget;          // 0 = none
-  LatCap cap[kLatMaxPlanes + 1];  // b = 0 .. P
+  LatCap cap[kLatMaxLevels];      // the caps in increasing order, from 1
+  int n_levels;
   const int* init;                // [n_runs][M][3] or [M][3]
   int init_per_run;
   uint32_t* planes;               // [n_groups][M][rec] words of the group's count planes
@@ -83,7 +88,7 @@ struct LatticeLaunch {
   double* t_homochiral;           // [n_runs]
   signed char* outcome;           // [n_runs]
   long long* events;              // [n_runs][2]: reactions, hops
-  long long* group_info;          // [n_groups][3]: steps, cap bits, LatStatus
+  long long* group_info;          // [n_groups][3]: steps, final cap m, LatStatus
   long long* snap_totals;         // [n_snap][n_runs][3]
   int* snap_domains;              // [n_snap][n_runs][2]
   unsigned long long* counters;   // [kLatCounters]

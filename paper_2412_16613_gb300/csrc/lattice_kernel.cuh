@@ -126,19 +126,6 @@ __device__ __forceinline__ unsigned lane_max(const uint32_t (&x)[W]) {
   return v;
 }
 
-// Lanes whose value exceeds 2^b (b < W).
-template <int W>
-__device__ __forceinline__ uint32_t above_pow2(const uint32_t (&x)[W], int b) {
-  uint32_t high = 0u, low = 0u, at = 0u;
-#pragma unroll
-  for (int i = 0; i < W; ++i) {
-    if (i > b) high |= x[i];
-    else if (i == b) at = x[i];
-    else low |= x[i];
-  }
-  return high | (at & low);
-}
-
 // R = rho * S modulo 2^KW, rho < 2^kLatRhoBits: shifted copies of S for the set bits of rho.
 template <int KW, int SW>
 __device__ __forceinline__ void scale(uint32_t (&R)[KW], const uint32_t (&S)[SW], uint32_t rho) {
@@ -174,8 +161,9 @@ struct StepArgs {
   long long step;        // the step's index in the group's sequence
   int sigma;             // its site
   uint32_t w3;           // word 3 of the stream (plane 0 of n)
-  int b, K;              // cap bits, planes of n
-  uint32_t hop_slots;    // 4 rho_h 2^b
+  int bh, K;             // planes of the molecule index, planes of n
+  uint32_t m;            // the cap
+  uint32_t hop_slots;    // 4 rho_h 2^bh
   uint32_t* planes;      // the group's site records
 };
 
@@ -222,7 +210,7 @@ __device__ __forceinline__ StepOut step(const LatticeLaunch& p, const StepArgs& 
   const uint32_t is_hop = bs::less_than_const<KW>(n, a.hop_slots);
   uint32_t mol[P], LD[P], T[P];
 #pragma unroll
-  for (int i = 0; i < P; ++i) mol[i] = i < a.b ? n[2 + i] : 0u;
+  for (int i = 0; i < P; ++i) mol[i] = i < a.bh ? n[2 + i] : 0u;
   add<P>(LD, L, D);
   add<P>(T, LD, A);
   const uint32_t ltL = bs::less_than<P>(mol, L), ltLD = bs::less_than<P>(mol, LD), ltT = bs::less_than<P>(mol, T);
@@ -324,7 +312,7 @@ __device__ __forceinline__ StepOut step(const LatticeLaunch& p, const StepArgs& 
         store_site<P>(r2, L2, D2, A2);
         add<P>(LD2, L2, D2);
         add<P>(T2, LD2, A2);
-        if (above_pow2<P>(T2, a.b)) o.overflow = true;
+        if (~bs::less_than_const<P>(T2, a.m + 1u)) o.overflow = true;  // a site above the cap
         ub[nb[k]] = (uint16_t)lane_max<P>(T2);
       }
     }
@@ -625,8 +613,9 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
     }
     __syncthreads();
     const int n_max = sh.n_max;
-    int b = n_max > 1 ? bit_length((long long)(n_max - 1)) : 0;
-    int status = b > P - 1 ? kLatBadInit : kLatOk;
+    int b = 0;  // the cap's level: the first cap at or above every site count
+    while (b + 1 < p.n_levels && p.cap[b].m < (unsigned)n_max) ++b;
+    int status = p.cap[b].m < (unsigned)n_max || p.cap[b].m > (1u << (P - 1)) ? kLatBadInit : kLatOk;
     long long lo = 0, hi = 0, rep_lo = 0, stop = budget_stop;
     int reason = p.step_budget > 0 ? kStopBudget : kStopNone;
     double t_cut = 0.0;
@@ -636,7 +625,8 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
     while (status == kLatOk) {
       // ---- a stop whose every earlier step has run
       if (lo == hi && hi == stop) {
-        if (sh.overflow) {  // the possible doubling admitted last did push a site above m
+        const bool raised = sh.overflow != 0;  // the last step, a possible cap raise, raised it
+        if (raised) {
           ++b;
           ++raises;
         }
@@ -644,7 +634,8 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
           status = kLatTimeout;
           break;
         }
-        if (reason == kStopCross) {
+        // a crossing found at the old rate is found again at the new one
+        if (reason == kStopCross && !raised) {
           // snapshots before the crossing step's event, after every earlier step's events
           if (service) replay(rb, S, rep_lo, lo, lane, lane < lanes, f32);
           rep_lo = lo;
@@ -695,12 +686,12 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
         stop = budget_stop;
         reason = p.step_budget > 0 ? kStopBudget : kStopNone;
       }
-      const LatCap cp = p.cap[b];
+      const LatCap cp = p.cap[b < p.n_levels ? b : p.n_levels - 1];
       if (cp.K > 32) {
         status = kLatRange;
         break;
       }
-      if (b > P - 1 || cp.K > KW) {
+      if (b >= p.n_levels || cp.m > (1u << (P - 1)) || cp.K > KW) {
         status = kLatCapacity;
         break;
       }
@@ -784,7 +775,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
           t_cut = sh.t_cut;
         }
       }
-      const int m = 1 << b;
+      const int m = (int)cp.m;
       const long long lo0 = lo, hi0 = hi;
       if (!service) {
         // ---- C: the cap check of the new steps
@@ -888,7 +879,8 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
           a.step = s;
           a.sigma = S.sigma[k];
           a.w3 = S.w3[k];
-          a.b = b;
+          a.bh = cp.bh;
+          a.m = cp.m;
           a.K = cp.K;
           a.hop_slots = cp.hop_slots;
           a.planes = planes;
@@ -924,7 +916,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       hi = hi0 + n_adm;
       lo = sh.newlo < C ? lo0 + sh.newlo : hi;
       rep_lo = lo0;
-      if (n_adm < n_new) {  // a possible cap doubling: admit nothing after it until it has run
+      if (sh.fcut < n_new) {  // a possible cap raise, admitted last: nothing after it until it has run
         ++flags;
         if (hi < stop) {
           stop = hi;
@@ -967,7 +959,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
     }
     if (tid == 0) {
       p.group_info[3 * gi] = lo;
-      p.group_info[3 * gi + 1] = b;
+      p.group_info[3 * gi + 1] = b < p.n_levels ? p.cap[b].m : 2 * p.cap[p.n_levels - 1].m;
       p.group_info[3 * gi + 2] = status;
       atomicAdd(&p.counters[kLatGroupSteps], (unsigned long long)lo);
       atomicAdd(&p.counters[kLatRounds], (unsigned long long)rounds);

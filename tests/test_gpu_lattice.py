@@ -72,7 +72,7 @@ def assert_lattice_parity(g, r, n_snap, runs=None, tie=1e-12, rtol=1e-12, min_ok
     assert np.array_equal(g["events"][gr, 0], r["reactions"][ok])
     assert np.array_equal(g["events"][gr, 1], r["hops"][ok])
     assert np.array_equal(g["groups"][gr // 32, 0], r["steps"][ok])
-    assert np.array_equal(g["groups"][gr // 32, 1], r["cap_bits"][ok])
+    assert np.array_equal(g["groups"][gr // 32, 1], r["cap"][ok])
     if n_snap:
         assert np.array_equal(g["snap_totals"][:, gr].transpose(1, 0, 2), r["snap_totals"][ok])
         assert np.array_equal(g["snap_domains"][:, gr].transpose(1, 0, 2), r["snap_domains"][ok])
@@ -137,34 +137,35 @@ def test_lattice_thinning():
 
 
 def test_lattice_cap_doubles():
-    """Sites start at exactly m = 2^b molecules and hops are fast (d = 4): a hop soon pushes a site
-    above m, the cap doubles (K and the rate change from the next step), and the runs still agree."""
+    """Sites start at exactly the cap m = 8 and hops are fast (d = 4): a hop soon pushes a site above
+    m, the cap moves to 10, 12, ... (K and the rate change from the next step), and the runs still
+    agree."""
     M, runs = 16, 64
     init = np.zeros((runs, M, 3), dtype=np.int64)
     init[:, :, 0] = 2
     init[:, :, 1] = 2
-    init[:, :, 2] = 4   # 8 molecules on every site: b = 3
+    init[:, :, 2] = 4   # 8 molecules on every site: m = 8
     kw = dict(rates=(1.0, 1.0, 1.0), hop=4.0, seed=7, t_end=0.2, snaps=[0.1])
     g = gpu_lattice(4, 4, init, runs, cap_bits_max=6, **kw)
     r = orc_lattice(4, 4, init, runs, **kw)
     assert_lattice_parity(g, r, 1)
-    assert np.all(g["groups"][:, 1] > 3)
+    assert np.all(g["groups"][:, 1] > 8)
     assert g["counters"]["cap_raises"] >= 2 and g["counters"]["flagged"] > 0
 
 
 def test_lattice_capacity_error_then_larger_planes():
-    """Site 0 starts with 8 molecules (b = 3), the others with one: the kernel takes 4 count planes
+    """Site 0 starts with 8 molecules (cap 8), the others with one: the kernel takes 4 count planes
     (caps up to 8), fast hops (d = 8) soon bring a ninth molecule to a full site and the run stops
-    with SSA_EOVERFLOW; cap_bits_max = 6 takes 8 planes and the run agrees with the oracle, whose
-    counts have no width."""
+    with SSA_EOVERFLOW; cap_bits_max = 6 takes 8 planes (caps up to 64) and the run agrees with the
+    oracle, whose counts have no width."""
     init = np.zeros((32, 16, 3), dtype=np.int64)
     init[:, :, 0] = 1
     init[:, 0] = (4, 4, 0)
     kw = dict(rates=(1.0, 1.0, 1.0), hop=8.0, seed=8, t_end=1.0)
     g = gpu_lattice(4, 4, init, 32, expect_status=pkg.SSA_EOVERFLOW, **kw)
-    assert g["groups"][0, 2] == 3 and g["groups"][0, 1] == 4  # stopped, needing the cap 2^4
+    assert g["groups"][0, 2] == 3 and g["groups"][0, 1] == 10  # stopped, needing the cap 10
     r = orc_lattice(4, 4, init, 32, **kw)
-    assert r["cap_bits"].max() <= 6
+    assert r["cap"].max() <= 64
     g = gpu_lattice(4, 4, init, 32, cap_bits_max=6, **kw)
     assert_lattice_parity(g, r, 0)
 
@@ -192,10 +193,10 @@ def test_lattice_step_budget():
 
 
 def test_lattice_k_beyond_32_planes():
-    """rho_r = 40000 with 300 molecules on a site needs K = 34 > 32 planes of n: the oracle and the
-    kernel both stop before the first step."""
+    """rho_r = 40000 with 600 molecules on a site (cap 640) needs K = 33 > 32 planes of n: the oracle
+    and the kernel both stop before the first step."""
     init = np.zeros((32, 2, 3), dtype=np.int64)
-    init[:, 0] = (100, 100, 100)
+    init[:, 0] = (200, 200, 200)
     kw = dict(rates=(1.0, 1.0, 1.0), hop=1.0 / 40000, seed=1, t_end=1.0)
     g = gpu_lattice(2, 1, init, 32, expect_status=pkg.SSA_EOVERFLOW, **kw)
     r = orc_lattice(2, 1, init, 32, check=False, **kw)
@@ -248,6 +249,17 @@ def test_lattice_64x64_full_size_sampled():
     tot = init.sum(axis=(1, 2))
     assert np.array_equal(g["final_counts"].sum(axis=(1, 2)), tot)
     assert np.all(g["snap_totals"].sum(axis=2) == tot[None, :])
-    cap = 1 << g["groups"][:, 1]
+    cap = g["groups"][:, 1]
     assert np.all(g["final_counts"].sum(axis=2).max(axis=1) <= np.repeat(cap, 32))
     assert g["counters"]["group_errors"] == 0
+
+
+def test_lattice_largest_lattice():
+    """128 x 128 sites, the most the kernel's per-site shared-memory tables hold (16 384 sites, 218 KB
+    of shared memory a block), 40 runs (a ragged second group), to t_end = 0.001: bit-exact."""
+    init = workloads.lattice_init(128, 128, 40, mean=(1.0, 1.0, 2.0), seed=17)
+    kw = dict(seed=12, t_end=0.001, snaps=[0.0005])
+    g = gpu_lattice(128, 128, init, 40, **kw)
+    r = orc_lattice(128, 128, init, 40, **kw)
+    assert_lattice_parity(g, r, 1, min_ok=0.5)
+    assert g["counters"]["group_steps"] > 1000
