@@ -540,7 +540,7 @@ def main():
     fp = kernel_fingerprint()
     roofline["traffic"] = (TRAFFIC_BYTES_PER_LAUNCH.get(fp) if (WORKLOAD == "c2" and RUNS_PER_GPU == 1 << 20
                                                                  and PRECISION == 0 and PAD == 1 and ENGINE == 0
-                                                                 and layout_used == 1) else None)
+                                                                 and (layout_used & 3) == 1) else None)
     roofline["kernel_sources_sha"] = fp
     if WORKLOAD == "c3":
         roofline = None

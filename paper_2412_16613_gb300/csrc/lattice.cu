@@ -62,12 +62,7 @@ int lattice_max_active_blocks(int P, int block, int smem, int* blocks) {
   }
 }
 
-// Per site: stamp and hop-count (uint32), cap table (uint16); per step in the ring of 1024: the
-// clock after it, the waiting time in fp64 and fp32, the fp32 clock state, the site, plane 0 of n,
-// four event masks and the done flag; two ready-list entries per step thread.
-int lattice_smem_bytes(int M, int T) {
-  return 4 * M + 4 * M + 2 * ((M + 3) & ~3) + 1024 * (8 + 8 + 4 + 4 + 4 + 4 + 4 + 16 + 4) + 4 * 2 * T;
-}
+int lattice_smem_bytes(int M, int T) { return lat_smem_bytes(M, T); }
 
 }  // namespace bitssa
 

@@ -27,6 +27,20 @@ constexpr int kLatDefaultWindow = 224;
 constexpr int kLatRhoBits = 16;     // rho_r below 2^16
 constexpr int kLatCounters = 8;
 constexpr int kLatMaxLevels = 64;   // caps 1 .. 8 and four per octave up to 2^16
+constexpr int kLatSlots = 2;        // pending steps per step thread: a group's pool holds kLatSlots T
+// Steps of a group held at once in shared memory: the pending steps and the steps finished but not
+// yet replayed into the runs' totals.  A power of two, at least twice the largest pool.
+constexpr int kLatRing = 1024;
+static_assert(kLatRing >= 2 * kLatSlots * kLatMaxBlock, "the ring must hold two pools");
+// Bytes of one ring entry: the clock after the step (fp64), its waiting time in fp64 and fp32, the
+// fp32 clock and compensation, the site, plane 0 of n, four event masks, the done flag.
+constexpr int kLatRingEntryBytes = 8 + 8 + 4 + 4 + 4 + 4 + 4 + 16 + 4;
+// Dynamic shared memory of a block with T step threads for a lattice of M sites: per site the stamp
+// and hop-count tables (uint32) and the cap table (uint16), the ring, two ready-list entries per
+// step thread.
+__host__ __device__ constexpr int lat_smem_bytes(int M, int T) {
+  return 4 * M + 4 * M + 2 * ((M + 3) & ~3) + kLatRing * kLatRingEntryBytes + 4 * kLatSlots * T;
+}
 
 // Indices into the lattice kernel's counter array (uint64).
 enum LatCounter {

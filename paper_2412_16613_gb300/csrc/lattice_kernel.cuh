@@ -322,17 +322,10 @@ __device__ __forceinline__ StepOut step(const LatticeLaunch& p, const StepArgs& 
 
 }  // namespace lat
 
-// Pending steps per step thread (the pool of a group holds kLatSlots T steps).
-constexpr int kLatSlots = 2;
-// Steps of a group held at once: the pending steps and the steps finished but not yet replayed
-// into the runs' totals.  A power of two, at least twice the largest pool.
-constexpr int kLatRing = 1024;
-static_assert(kLatRing >= 2 * kLatSlots * kLatMaxBlock, "the ring must hold two pools");
-
-// Shared-memory layout of a block: per site, the stamp and hop-count tables (uint32) and the cap
-// table ub (uint16, the largest site total over the group's runs); per step, in a ring indexed by
-// the step's index modulo kLatRing, its waiting time, site and plane 0 of n, the clock after it,
-// its event masks and its done flag; the ready list of a wave.
+// Shared-memory layout of a block (lat_smem_bytes in lattice.h sizes it): per site, the stamp and
+// hop-count tables (uint32) and the cap table ub (uint16, the largest site total over the group's
+// runs); per step, in a ring indexed by the step's index modulo kLatRing, its waiting time, site
+// and plane 0 of n, the clock after it, its event masks and its done flag; the ready list.
 struct LatSmem {
   uint32_t* stamp;
   uint32_t* hopcnt;
@@ -465,50 +458,86 @@ struct Clock {
 };
 
 // The group clock over steps [from, from + n), in step order (Eq. equation-tau, Eq.
-// eq-update-time), from state c; records the clock after each step (the fp32 sum and its
+// eq-update-time), from state c, computed by the 32 lanes of a warp together: each block of 32
+// steps loads its waiting times in parallel, every lane runs the same recurrence on them (passed
+// by shuffles, so no load waits on the chain), and lane j keeps the state after step j of the
+// block and stores it with the others.  Records the clock after each step (the fp32 sum and its
 // compensation in the fp32 modes, else the fp64 time).  With `detect`, stops before the first step
 // whose event would pass the next snapshot (if any) or t_end and returns its offset with its time
 // in *t_cut; otherwise returns n.  The fp32 sums compare against the largest floats at or below the
 // time points, which decides exactly as comparing (double) of the sum with the time point.
 __device__ __forceinline__ int clock_run(const LatticeLaunch& p, const LatSmem& S, long long from, int n, bool detect,
-                                         bool has_snap, int next_snap, Clock c, double* t_cut) {
+                                         bool has_snap, int next_snap, Clock c, double* t_cut, int lane) {
   if (p.precision == kP32Kahan || p.precision == kP32Plain) {
     const bool kahan = p.precision == kP32Kahan;
     const float snap_f = has_snap ? p.snap_f[next_snap] : 0.0f;
     float tf = c.tf, cf = c.cf;
-    for (int i = 0; i < n; ++i) {
-      const int k = slot(from + i);
-      const float tau = S.tauf[k];
-      float tfn, cfn = 0.0f;
-      if (kahan) {
-        const float yk = tau - cf;
-        const float sum = tf + yk;
-        cfn = (sum - tf) - yk;
-        tfn = sum;
-      } else {
-        tfn = tf + tau;
+    for (int base = 0; base < n; base += 32) {
+      const int cnt = n - base < 32 ? n - base : 32;
+      const int k = slot(from + base + lane);
+      const float tau_l = lane < cnt ? S.tauf[k] : 0.0f;
+      float my_tf = 0.0f, my_cf = 0.0f;
+      int cut = -1;
+      float tcut = 0.0f;
+      for (int j = 0; j < cnt; ++j) {
+        const float tau = __shfl_sync(kFull, tau_l, j);
+        float tfn, cfn = 0.0f;
+        if (kahan) {
+          const float yk = tau - cf;
+          const float sum = tf + yk;
+          cfn = (sum - tf) - yk;
+          tfn = sum;
+        } else {
+          tfn = tf + tau;
+        }
+        if (detect && ((has_snap && tfn > snap_f) || tfn > p.t_end_f)) {
+          cut = j;
+          tcut = tfn;
+          break;
+        }
+        tf = tfn;
+        cf = cfn;
+        if (lane == j) {
+          my_tf = tf;
+          my_cf = cf;
+        }
       }
-      if (detect && ((has_snap && tfn > snap_f) || tfn > p.t_end_f)) {
-        *t_cut = (double)tfn;
-        return i;
+      if (lane < (cut >= 0 ? cut : cnt)) {
+        S.tf[k] = my_tf;
+        S.cf[k] = my_cf;
       }
-      S.tf[k] = tfn;
-      S.cf[k] = cfn;
-      tf = tfn;
-      cf = cfn;
+      if (cut >= 0) {
+        *t_cut = (double)tcut;
+        return base + cut;
+      }
     }
     return n;
   }
   const double snap_next = has_snap ? p.snap[next_snap] : 0.0;
-  for (int i = 0; i < n; ++i) {
-    const int k = slot(from + i);
-    const double tn = p.precision == kP64LogSum ? c.t + S.taud[k] : c.t + (double)S.tauf[k];
-    if (detect && ((has_snap && snap_next < tn) || tn > p.t_end)) {
-      *t_cut = tn;
-      return i;
+  double t = c.t;
+  for (int base = 0; base < n; base += 32) {
+    const int cnt = n - base < 32 ? n - base : 32;
+    const int k = slot(from + base + lane);
+    const double tau_l =
+        lane < cnt ? (p.precision == kP64LogSum ? S.taud[k] : (double)S.tauf[k]) : 0.0;
+    double my_t = 0.0;
+    int cut = -1;
+    double tcut = 0.0;
+    for (int j = 0; j < cnt; ++j) {
+      const double tn = t + __shfl_sync(kFull, tau_l, j);
+      if (detect && ((has_snap && snap_next < tn) || tn > p.t_end)) {
+        cut = j;
+        tcut = tn;
+        break;
+      }
+      t = tn;
+      if (lane == j) my_t = t;
     }
-    S.tnew[k] = tn;
-    c.t = tn;
+    if (lane < (cut >= 0 ? cut : cnt)) S.tnew[k] = my_t;
+    if (cut >= 0) {
+      *t_cut = tcut;
+      return base + cut;
+    }
   }
   return n;
 }
@@ -762,10 +791,13 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       if (slow) {
         ++slow_rounds;
         // ---- B: the exact clock finds the first new step that would pass a time point
-        if (service && lane == 0) {
+        if (service) {
           double tc = 0.0;
-          sh.ncut = clock_run(p, S, hi, n_new, true, has_snap, next_snap, c0, &tc);
-          sh.t_cut = tc;
+          const int nc = clock_run(p, S, hi, n_new, true, has_snap, next_snap, c0, &tc, lane);
+          if (lane == 0) {
+            sh.ncut = nc;
+            sh.t_cut = tc;
+          }
         }
         __syncthreads();
         if (sh.ncut < n_new) {
@@ -903,9 +935,9 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
       } else {
         // the service warp: the clock of the new steps (unless B summed it), then the steps
         // finished before this round into the runs' totals
-        if (!slow && lane == 0) {
+        if (!slow) {
           double tc = 0.0;
-          clock_run(p, S, hi0, n_new, false, false, 0, c0, &tc);
+          clock_run(p, S, hi0, n_new, false, false, 0, c0, &tc, lane);
         }
         __syncwarp();
         if (lo0 > rep_lo) replay(rb, S, rep_lo, lo0, lane, lane < lanes, f32);
