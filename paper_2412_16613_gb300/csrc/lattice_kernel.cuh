@@ -574,6 +574,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
   __shared__ double s_wsum[kLatMaxBlock / 32];
   __shared__ float s_wsumf[kLatMaxBlock / 32];
   __shared__ unsigned s_dom[32][2];
+  __shared__ unsigned long long s_tot[32][3];
   __shared__ struct {
     int fcut, overflow, n_max, ncut, newlo, hadm;
     double t_cut;
@@ -591,6 +592,7 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
     uint32_t* planes = p.planes + (size_t)gi * (size_t)M * (size_t)p.rec;
 
     // ---- initial state: planes from the counts, the cap table, the cap
+    if (tid < 32) s_tot[tid][0] = s_tot[tid][1] = s_tot[tid][2] = 0ull;
     if (tid == 0) {
       sh.n_max = 0;
       sh.overflow = 0;
@@ -627,20 +629,33 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
     rb.reactions = rb.hops = 0;
     rb.t_h = __longlong_as_double(0x7FF0000000000000ll);  // +inf
     rb.outcome = -1;
-    if (service && lane < lanes) {
-      for (int i = 0; i < M; ++i) {
-        const int* c = p.init_per_run ? p.init + ((size_t)(run0 + lane) * M + i) * 3 : p.init + (size_t)i * 3;
-        rb.tot[0] += c[0];
-        rb.tot[1] += c[1];
-        rb.tot[2] += c[2];
+    // each run's lattice totals: warp w sums run `lane`'s counts over its share of the sites
+    {
+      long long part[3] = {0, 0, 0};
+      if (lane < lanes) {
+        const int NW = NT >> 5;
+        for (int i = warp; i < M; i += NW) {
+          const int* c = p.init_per_run ? p.init + ((size_t)(run0 + lane) * M + i) * 3 : p.init + (size_t)i * 3;
+          part[0] += c[0];
+          part[1] += c[1];
+          part[2] += c[2];
+        }
+        atomicAdd(&s_tot[lane][0], (unsigned long long)part[0]);
+        atomicAdd(&s_tot[lane][1], (unsigned long long)part[1]);
+        atomicAdd(&s_tot[lane][2], (unsigned long long)part[2]);
       }
+    }
+    __syncthreads();
+    if (service && lane < lanes) {
+      rb.tot[0] = (long long)s_tot[lane][0];
+      rb.tot[1] = (long long)s_tot[lane][1];
+      rb.tot[2] = (long long)s_tot[lane][2];
       const int kinds = (rb.tot[0] > 0) + (rb.tot[1] > 0) + (rb.tot[2] > 0);
       if (kinds <= 1) {
         rb.t_h = 0.0;
         rb.outcome = rb.tot[0] ? 0 : (rb.tot[1] ? 1 : (rb.tot[2] ? 2 : -1));
       }
     }
-    __syncthreads();
     const int n_max = sh.n_max;
     int b = 0;  // the cap's level: the first cap at or above every site count
     while (b + 1 < p.n_levels && p.cap[b].m < (unsigned)n_max) ++b;
