@@ -348,8 +348,8 @@ int ssa_set_allocator(ssa_alloc_fn alloc, ssa_free_fn release, void* user);
  * i < L + D + A, else nothing; otherwise reaction r if H + rho_r S_{r-1} <= n < H + rho_r S_r
  * (S_r = h_1 + .. + h_r), kept iff U < floor(k_r / k_max 2^q) when k_r < k_max, nothing above S_3.
  * A run thus jumps by reaction r at rate k_r h_r and moves a given molecule in a given direction at
- * rate d.  If a hop leaves a site of any run above m, m moves to the next cap from the next step.  Runs go on to
- * t_end; the time at which a run's lattice first holds a single species is kept.
+ * rate d.  If a hop leaves a site of any run above m, m moves to the next cap from the next step.
+ * Runs go on to t_end; the time at which a run's lattice first holds a single species is kept.
  *
  * Up to twice block_size consecutive steps of a group are pending at once; a step waits only
  * for earlier pending steps whose site or neighbours meet its own, so every run follows the serial
@@ -373,8 +373,8 @@ enum {
                                  the context's planes) */
   SSA_LAT_COUNTERS = 7        /* uint64[8]: group steps, rounds (one wave of ready steps each),
                                  rounds whose new steps might pass a snapshot or t_end (the clock
-                                 ran before admission), reactions, hops, cap doublings, groups
-                                 stopped by an error, steps admitted as possible cap doublings */
+                                 ran before admission), reactions, hops, cap raises, groups
+                                 stopped by an error, steps admitted as possible cap raises */
 };
 #define SSA_LAT_N_COUNTERS 8
 
@@ -388,8 +388,9 @@ enum {
  *   n_runs >= 0, seed: as in ssa_create (run j is lane j % 32 of group j / 32).
  *   opt: precision (SSA_P64 and SSA_P64_LOGSUM both give tau = -log(u) / Lambda summed in fp64;
  *     SSA_P32_KAHAN, SSA_P32_D64ACC, SSA_P32_PLAIN as for ssa_create), thin_bits, block_size (step
- *     threads, each holding two pending steps; a multiple of 32 up to 224; 0 = 224), step_budget, first_run, cuda_stream, device.
- *     Other fields must keep their defaults (SSA_EUNSUPPORTED otherwise).
+ *     threads, each holding two pending steps; a multiple of 32 up to 224; 0 = 224), step_budget,
+ *     first_run, cuda_stream, device.  Other fields must keep their defaults (SSA_EUNSUPPORTED
+ *     otherwise).
  *   cap_bits_max: the runs may reach caps up to 2^cap_bits_max; 0 = what the count planes chosen
  *     for the initial cap hold; at most 15.  The planes per count are the smallest of 4, 8, 12, 16
  *     above it (caps up to 8, 128, 2048, 32768); a run whose cap would outgrow them stops with

@@ -49,9 +49,9 @@ enum LatCounter {
   kLatClockRounds = 2,  // rounds whose new steps might pass a time point: the clock ran first
   kLatReactions = 3,    // reactions of every run
   kLatHops = 4,         // hops of every run
-  kLatCapRaises = 5,    // doublings of a group's occupancy cap
+  kLatCapRaises = 5,    // raises of a group's occupancy cap
   kLatErrors = 6,       // groups that stopped with an error
-  kLatFlagged = 7       // steps admitted as possible cap doublings (nothing after them until they ran)
+  kLatFlagged = 7       // steps admitted as possible cap raises (nothing after them until they ran)
 };
 
 // Per-group stop status (LatticeLaunch::group_status).

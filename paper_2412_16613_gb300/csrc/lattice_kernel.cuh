@@ -552,14 +552,14 @@ __device__ __forceinline__ int clock_run(const LatticeLaunch& p, const LatSmem& 
 //   B  (only if they can: the service warp, others waiting) the clock in step order up to the
 //      first step that would pass it: no step from there on is admitted until the snapshot;
 //   C  (step threads) the cap check: the first new step that might push a neighbour above the cap
-//      m is the last admitted until it has run (only it can double the cap, which changes K and
+//      m is the last admitted until it has run (only it can raise the cap, which changes K and
 //      the rate of every later step);
 //   D  (step threads) one wave: every pending step that no earlier pending step's closed
 //      neighbourhood (site and four neighbours) meets runs, up to one per step thread, all at
 //      once; lo moves to the first step still pending;
 //   meanwhile the service warp sums the clock of the new steps (when B did not) and replays the
 //   steps finished before this round into the runs' totals.
-// When every step before a stop (snapshot or t_end, a possible cap doubling, the step budget) has
+// When every step before a stop (snapshot or t_end, a possible cap raise, the step budget) has
 // run, the stop is handled and admission resumes.
 template <int P, int KW>
 __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid_constant__ LatticeLaunch p) {
@@ -876,12 +876,14 @@ __global__ void __launch_bounds__(kLatMaxBlock + 32) lattice_kernel(const __grid
 #pragma unroll
             for (int k = 0; k < 4; ++k) c5[j][k + 1] = n4[k];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
-              atomicMin(&S.stamp[c5[j][k]], (uint32_t)off);
-              // the records the step will read, brought to L1 while the wave is sorted out
-              const uint32_t* r = planes + (size_t)c5[j][k] * p.rec;
-              asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
-              asm volatile("prefetch.global.L1 [%0];" ::"l"(r + p.rec - 1));
+            for (int k = 0; k < 5; ++k) atomicMin(&S.stamp[c5[j][k]], (uint32_t)off);
+            if (off >= (int)(hi0 - lo0)) {  // admitted this round: bring its records to L1
+#pragma unroll
+              for (int k = 0; k < 5; ++k) {
+                const uint32_t* r = planes + (size_t)c5[j][k] * p.rec;
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(r + p.rec - 1));
+              }
             }
           }
         }
