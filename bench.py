@@ -85,16 +85,18 @@ def device_sm_count_and_max_mhz(index: int):
 def layout_name(bits: int) -> str:
     """The layouts counter 9 reports: one thread / three warps, and the general kernel's mode."""
     names = [n for bit, n in ((1, "thread"), (2, "warps"), (4, "general incremental"), (8, "general products"),
-                              (16, "tail one run per thread")) if bits & bit]
+                              (16, "tail one run per thread"), (32, "planes in registers")) if bits & bit]
     return "+".join(names) or "none"
 
 
 def general_ops_per_group_step(K: int, b: int, products: bool) -> int:
     """Word operations of one group step of Frank's model on the general kernel.  Per reaction:
-    the running-sum add and the comparison (3K), and either a b x b schoolbook product (3 b^2:
-    AND, sum, carry) or the change of h_r (two scaled counts, 4 ops a plane, and a small constant,
-    2 ops a plane: 10K).  Per species the change planes (3R) and the masked add (2b).  The Philox
-    calls (20 LOP3 each)."""
+    the selection of its changer word (3K: the running sum and the comparison, or the subtraction
+    of h_r from what is left of n and its borrow, 2K, as the kernel does it), and either a b x b
+    schoolbook product (3 b^2: AND, sum, carry) or the change of h_r (two scaled counts, 4 ops a
+    plane, and a small constant, 2 ops a plane: 10K).  Per species the change planes (3R) and the
+    masked add (2b).  The Philox calls (20 LOP3 each).  The per-unit figure keeps 3K so that it
+    does not move with the kernel's way of doing the selection."""
     per_reaction = 3 * K + (3 * b * b if products else 10 * K)
     return 3 * per_reaction + 3 * (2 * b + 3 * 3) + 20 * ((K + 2 + 3) // 4)
 
@@ -370,6 +372,10 @@ def main():
                          "power-of-two bound that follows each group's state")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 2],
                     help="0: Frank's kernels; 2: the general-network kernel on the same workload")
+    ap.add_argument("--recompute", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="ssa_options.recompute on the general engine: 0 the library's choice (planes in "
+                         "registers where the network fits), 1 products every step, 2 incremental, 3 "
+                         "incremental with the planes in shared memory")
     ap.add_argument("--budget", type=int, default=0,
                     help="stop every group after this many steps (profiling one phase of a launch; the "
                          "line then covers that phase only and says so)")
@@ -424,7 +430,8 @@ def main():
     first_run = sharding.weak_shard(RUNS_PER_GPU, rank)[0] if WORKLOAD != "c3" else 0
     opt = pkg.ssa_default_options(cuda_stream=stream, device=local, precision=args.precision,
                                   block_size=args.block, first_run=first_run, layout=args.layout,
-                                  pad_pow2=PAD, engine=ENGINE, tail_groups=args.tail, step_budget=args.budget)
+                                  pad_pow2=PAD, engine=ENGINE, tail_groups=args.tail, step_budget=args.budget,
+                                  recompute=args.recompute)
     if WORKLOAD == "c3":
         opt.first_run = 0
         ctx = pkg.ssa_create_batch(pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS, BATCH["init"], BATCH["rates"],

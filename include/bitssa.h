@@ -150,8 +150,13 @@ typedef struct {
                                 linear in the counts before it (App. A generalised to any
                                 mass-action network); 1 recomputes every h_r by bit-sliced products
                                 at every step (Sec. 4.1); 0 (default) incremental unless ssa_tune
-                                found products faster on the caller's workload.  Same runs in
-                                every mode. */
+                                found products faster on the caller's workload.  Incremental mode
+                                keeps a group's count planes and every h_r in the thread's
+                                registers when the network has at most 4 species and 4 reactions,
+                                K is at most 22 and the counts fit the planes the products read
+                                (every network with a reaction of order 2), else in shared memory;
+                                3 is incremental mode with the planes in shared memory always.
+                                Same runs in every mode. */
   int32_t clock;             /* SSA_CLOCK_GROUP (default): the 32 runs of a group share one clock (one
                                 waiting time per group and step, the paper's one tau for all copies,
                                 end of Sec. 4, Eq. equation-tau): each run is an exact sample path, but
@@ -206,7 +211,8 @@ enum {
                                    the layouts that ran (bit 0 SSA_LAYOUT_THREAD, bit 1
                                    SSA_LAYOUT_WARPS: 1, 2, or 3 for a batch that used both;
                                    0 no bit-sliced launch; on the general kernel also bit 2
-                                   with propensities incremented, bit 3 recomputed by products;
+                                   with propensities incremented, bit 3 recomputed by products,
+                                   bit 5 the planes kept in registers (ssa_options.recompute);
                                    bit 4: some groups were finished one run per thread, see
                                    ssa_options.tail_groups) */
   SSA_FIELD_ENS_ABSORBED = 6    /* uint64[n_ens][4]: runs absorbed with outcome species 0, 1, 2,

@@ -1,8 +1,9 @@
-// general_instance.cu -- one instantiation of the general-network bit-sliced kernel;
-// compiled once per K (number of propensity planes) with -DBITSSA_K=<K>.
+// general_instance.cu -- one instantiation of the general-network bit-sliced kernels (planes in
+// shared memory; planes in registers up to kRegMaxK); compiled once per K (number of propensity
+// planes) with -DBITSSA_K=<K>.
 #include <cuda_runtime.h>
 
-#include "general_kernel.cuh"
+#include "general_reg.cuh"
 
 #ifndef BITSSA_K
 #error "compile with -DBITSSA_K=<planes>"
@@ -13,12 +14,30 @@
 
 namespace bitssa {
 
-// variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64)
+// variant: bit 0 = batch (ensemble table), bit 1 = product clock (SSA_P64), bit 2 = planes in
+// registers (p.net.regs at launch)
+namespace {
+template <bool REG, bool BATCH, bool PROD>
+constexpr auto general_entry() {
+  if constexpr (REG && BITSSA_K <= kRegMaxK) return general_reg_kernel<BITSSA_K, BATCH, PROD>;
+  else return general_kernel<BITSSA_K, BATCH, PROD>;
+}
+}  // namespace
+
 int BITSSA_CAT(general_launch_k, BITSSA_K)(const FrankLaunch& p, int grid, int block, int smem,
                                             void* stream) {
   const cudaStream_t st = (cudaStream_t)stream;
   const bool prod = p.precision == kP64;
-  if (p.ens_table) {
+  if (p.net.regs && BITSSA_K > kRegMaxK) return (int)cudaErrorInvalidValue;
+  if (p.net.regs) {
+    if (p.ens_table) {
+      if (prod) general_entry<true, true, true>()<<<grid, block, smem, st>>>(p);
+      else general_entry<true, true, false>()<<<grid, block, smem, st>>>(p);
+    } else {
+      if (prod) general_entry<true, false, true>()<<<grid, block, smem, st>>>(p);
+      else general_entry<true, false, false>()<<<grid, block, smem, st>>>(p);
+    }
+  } else if (p.ens_table) {
     if (prod) general_kernel<BITSSA_K, true, true><<<grid, block, smem, st>>>(p);
     else general_kernel<BITSSA_K, true, false><<<grid, block, smem, st>>>(p);
   } else {
@@ -31,11 +50,15 @@ int BITSSA_CAT(general_launch_k, BITSSA_K)(const FrankLaunch& p, int grid, int b
 namespace {
 template <typename F>
 int with_kernel(int variant, F f) {
-  switch (variant & 3) {
+  switch (variant & 7) {
     case 0: return f(general_kernel<BITSSA_K, false, false>);
     case 1: return f(general_kernel<BITSSA_K, true, false>);
     case 2: return f(general_kernel<BITSSA_K, false, true>);
-    default: return f(general_kernel<BITSSA_K, true, true>);
+    case 3: return f(general_kernel<BITSSA_K, true, true>);
+    case 4: return f(general_entry<true, false, false>());
+    case 5: return f(general_entry<true, true, false>());
+    case 6: return f(general_entry<true, false, true>());
+    default: return f(general_entry<true, true, true>());
   }
 }
 }  // namespace

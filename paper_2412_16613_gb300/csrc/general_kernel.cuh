@@ -26,8 +26,9 @@
 //   1. Philox words of attempt 0: the K planes of n (rejection and partial redraw above
 //      lambda_int unless the bound is padded to 2^K) and the clock's two words.
 //   2. Clock, snapshots (state before the event), t_end.
-//   3. For r = 0..R-1: h_r, S += h_r, lt_r = [n < S], xi_r = lt_r & ~lt_{r-1}
-//      (Eq. equation-changer); a lane with n >= S_R fires nothing (a ghost or null event).
+//   3. For r = 0..R-1: xi_r = [S_{r-1} <= n < S_r] (Eq. equation-changer), taken as the borrow
+//      of n - h_0 - ... - h_r out of the r-th subtraction; a lane with n >= S_R fires nothing (a
+//      ghost or null event).
 //   4. Thinning of reactions with k_r < k_max.
 //   5. x_i += sum_r xi_r nu_ri for every species (Eq. equation-v), two's complement.
 //   6. Absorption: a lane none of whose reactions with k_r > 0 has a nonzero propensity.
@@ -126,6 +127,23 @@ __device__ __forceinline__ uint32_t general_live(const Network& net, const Ensem
   return m;
 }
 
+// h (K planes) = x (x - 1) / 2 for the W planes of x: the product is even and below 2^(K+1);
+// its plane 0 is dropped.
+template <int K, int W>
+__device__ __forceinline__ void half_square(uint32_t (&h)[K], const uint32_t (&x)[W]) {
+  uint32_t xm[W];
+  uint32_t borrow = 0xFFFFFFFFu;  // x - 1
+#pragma unroll
+  for (int i = 0; i < W; ++i) {
+    xm[i] = x[i] ^ borrow;
+    borrow &= ~x[i];
+  }
+  uint32_t p[K + 1];
+  bs::multiply(p, x, xm);
+#pragma unroll
+  for (int i = 0; i < K; ++i) h[i] = p[i + 1];
+}
+
 // h (K planes) = the propensity of reaction r in every lane, from the count planes.
 template <int K>
 __device__ __forceinline__ void general_propensity(uint32_t (&h)[K], const Network& net, int r,
@@ -146,31 +164,21 @@ __device__ __forceinline__ void general_propensity(uint32_t (&h)[K], const Netwo
     bs::multiply(h, xa, xb);
     return;
   }
-  // h = x_a (x_a - 1) / 2: the product is even and below 2^(K+1); drop its plane 0
-  uint32_t xm[BM];
-  uint32_t borrow = 0xFFFFFFFFu;  // x_a - 1
-#pragma unroll
-  for (int i = 0; i < BM; ++i) {
-    xm[i] = xa[i] ^ borrow;
-    borrow &= ~xa[i];
-  }
-  uint32_t p[K + 1];
-  bs::multiply(p, xa, xm);
-#pragma unroll
-  for (int i = 0; i < K; ++i) h[i] = p[i + 1];
+  half_square(h, xa);
 }
 
 // h (K planes) += d x for a lane-wise d in [-2, 2] (three two's-complement planes) and an
-// unsigned x (W planes): the lanes with |d| = 1 add x, with |d| = 2 add 2x, negated where d < 0
-// (complemented, plus one at the carry-in).
+// unsigned x (W planes): the lanes with |d| = 1 add x, with |d| = 2 add 2x (x one plane up),
+// negated where d < 0 (complemented, plus one at the carry-in).  A plane of the addend is
+// (nz & (two ? x_{i-1} : x_i)) ^ neg: two three-input operations.
 template <int K, int W>
 __device__ __forceinline__ void add_scaled(uint32_t (&h)[K], const uint32_t (&x)[W], const uint32_t (&d)[3]) {
-  const uint32_t one = d[0], two = d[1] & ~d[0], neg = d[2];
+  const uint32_t nz = d[0] | d[1], two = d[1] & ~d[0], neg = d[2];
   uint32_t carry = neg;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const uint32_t xi = i < W ? x[i] : 0u, xm = (i >= 1 && i - 1 < W) ? x[i - 1] : 0u;
-    const uint32_t t = ((one & xi) | (two & xm)) ^ neg;
+    const uint32_t t = (nz & ((two & xm) | (~two & xi))) ^ neg;
     const uint32_t s = bs::xor3(h[i], t, carry);
     carry = bs::maj(h[i], t, carry);
     h[i] = s;
@@ -191,8 +199,47 @@ __device__ __forceinline__ void add_small(uint32_t (&h)[K], const uint32_t (&c)[
   }
 }
 
+// The constant term of a homodimer's change, d_a (d_a - 1) / 2: 3, 1, 0, 0, 1 for d_a = -2..2,
+// as the low planes and the sign plane add_small takes.
+__device__ __forceinline__ void same_constant(const uint32_t (&da)[3], uint32_t (&cst)[4]) {
+  const uint32_t m2 = da[1] & ~da[0];  // |d| = 2
+  cst[0] = da[1] & (da[2] | ~da[0]);   // d = -2, -1 or 2
+  cst[1] = m2 & da[2];                 // d = -2
+  cst[2] = 0u;
+  cst[3] = 0u;
+}
+
+// The constant term of a pair's change, d_a d_b: magnitude 1, 2 or 4, negative when exactly one
+// of them is; two's complement of -m: m1 -> ...1111, m2 -> ...1110, m4 -> ...1100.
+__device__ __forceinline__ void pair_constant(const uint32_t (&da)[3], const uint32_t (&db)[3], uint32_t (&cst)[4]) {
+  const uint32_t a1 = da[0], a2 = da[1] & ~da[0], b1 = db[0], b2 = db[1] & ~db[0];
+  const uint32_t m1 = a1 & b1, m2 = (a1 & b2) | (a2 & b1), m4 = a2 & b2;
+  const uint32_t neg = (da[2] ^ db[2]) & (m1 | m2 | m4);
+  cst[0] = m1;
+  cst[1] = (m2 & ~neg) | (neg & (m1 | m2));
+  cst[2] = (m4 & ~neg) | (neg & (m1 | m2 | m4));
+  cst[3] = neg;
+}
+
 // h_r += its change in this step (see the file header), from the counts before the event and
 // the change planes of every species.
+// m -= h over K planes, modulo 2^K; returns the lanes that borrow out of the top plane.  Taking
+// h_0, h_1, ... off n in turn, the subtraction of h_r is the first to borrow exactly where
+// S_{r-1} <= n < S_r (the running value n - S_r stays above -2^K, so it borrows at most once
+// while S_R < 2^K): the changer word of reaction r (Eq. equation-changer) at one subtraction per
+// reaction instead of a sum and a comparison.
+template <int K>
+__device__ __forceinline__ uint32_t sub_borrow(uint32_t (&m)[K], const uint32_t (&h)[K]) {
+  uint32_t borrow = 0u;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const uint32_t mi = m[i];
+    m[i] = bs::xor3(mi, h[i], borrow);
+    borrow = bs::maj(~mi, h[i], borrow);
+  }
+  return borrow;
+}
+
 template <int K>
 __device__ __forceinline__ void general_increment(const Network& net, int r, const CountPlanes& c) {
   using Sh = GeneralShape<K>;
@@ -211,9 +258,8 @@ __device__ __forceinline__ void general_increment(const Network& net, int r, con
     uint32_t xa[BM];
     load_planes(xa, c, a);
     add_scaled(h, xa, da);
-    const uint32_t m2 = da[1] & ~da[0];               // |d| = 2
-    const uint32_t cst[4] = {da[1] & (da[2] | ~da[0]),  // d = -2, -1 or 2
-                             m2 & da[2], 0u, 0u};       // d = -2
+    uint32_t cst[4];
+    same_constant(da, cst);
     add_small(h, cst);
   } else {  // + d_b x_a + d_a x_b + d_a d_b
     const uint32_t db[3] = {c.change(b, 0), c.change(b, 1), c.change(b, 2)};
@@ -222,12 +268,8 @@ __device__ __forceinline__ void general_increment(const Network& net, int r, con
     load_planes(xb, c, b);
     add_scaled(h, xa, db);
     add_scaled(h, xb, da);
-    // d_a d_b: magnitude 1, 2 or 4, negative when exactly one of them is
-    const uint32_t a1 = da[0], a2 = da[1] & ~da[0], b1 = db[0], b2 = db[1] & ~db[0];
-    const uint32_t m1 = a1 & b1, m2 = (a1 & b2) | (a2 & b1), m4 = a2 & b2;
-    const uint32_t neg = (da[2] ^ db[2]) & (m1 | m2 | m4);
-    // two's complement of -m: m1 -> ...1111, m2 -> ...1110, m4 -> ...1100
-    const uint32_t cst[4] = {m1, (m2 & ~neg) | (neg & (m1 | m2)), (m4 & ~neg) | (neg & (m1 | m2 | m4)), neg};
+    uint32_t cst[4];
+    pair_constant(da, db, cst);
     add_small(h, cst);
   }
 #pragma unroll
@@ -257,23 +299,31 @@ __device__ __forceinline__ long long general_row0(uint32_t sgroup, const Ensembl
   return e.run_offset + ((long long)sgroup - e.group_base) * 32;
 }
 
-template <int K, bool PROD>
-__device__ __forceinline__ void general_capture(const FrankLaunch& p, const GeneralState<PROD>& s,
-                                                const Ensemble& e, int snap, const CountPlanes& c,
-                                                unsigned int* s_hist) {
+// One snapshot of a group: the ee histogram and, if kept, every run's counts; count(s, l) reads
+// species s of lane l.
+template <bool PROD, class Count>
+__device__ __forceinline__ void capture_counts(const FrankLaunch& p, const GeneralState<PROD>& s,
+                                               const Ensemble& e, int snap, unsigned int* s_hist, Count&& count) {
   const Network& net = p.net;
-  const int B = count_planes(e);
   for (int l = 0; l < s.nvalid; ++l) {
-    const int cx = net.hist_x >= 0 ? lane_count(c, net.hist_x, B, l) : 0;
-    const int cy = net.hist_y >= 0 ? lane_count(c, net.hist_y, B, l) : 0;
+    const int cx = net.hist_x >= 0 ? count(net.hist_x, l) : 0;
+    const int cy = net.hist_y >= 0 ? count(net.hist_y, l) : 0;
     const int bin = ee_bin(cx, cy);
     if (s_hist) atomicAdd(&s_hist[snap * kHistBins + bin], 1u);
     else atomicAdd(&p.hist[((long long)s.ens * p.n_snap + snap) * kHistBins + bin], 1ull);
     if (p.snap_counts) {
       int* o = p.snap_counts + ((long long)snap * p.n_runs_total + general_row0(s.sgroup, e) + l) * net.S;
-      for (int sp = 0; sp < net.S; ++sp) o[sp] = lane_count(c, sp, B, l);
+      for (int sp = 0; sp < net.S; ++sp) o[sp] = count(sp, l);
     }
   }
+}
+
+template <int K, bool PROD>
+__device__ __forceinline__ void general_capture(const FrankLaunch& p, const GeneralState<PROD>& s,
+                                                const Ensemble& e, int snap, const CountPlanes& c,
+                                                unsigned int* s_hist) {
+  const int B = count_planes(e);
+  capture_counts(p, s, e, snap, s_hist, [&](int sp, int l) { return lane_count(c, sp, B, l); });
 }
 
 template <int K, bool PROD>
@@ -326,27 +376,25 @@ __device__ __forceinline__ void general_init(const FrankLaunch& p, GeneralState<
     for (; s.snap < p.n_snap; ++s.snap) general_capture<K, PROD>(p, s, e, s.snap, c, s_hist);
 }
 
-// One group step (see the file header).
-template <int K, bool PROD>
-__device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
-                                             const Threshold* thr, const CountPlanes& c, unsigned int* s_hist,
-                                             unsigned int& errors) {
-  using Sh = GeneralShape<K>;
-  constexpr int NC0 = Sh::NC0;
-  const Network& net = p.net;
-  const int B = count_planes(e);
+// Steps (1) and (2) of a group step: the Philox words of attempt 0 (w) and n, redrawn where it is
+// at or above lambda_int, then the clock, with capture(snap) called for every snapshot the event
+// passes.  False when the group stops at this step (t_end passed, the step budget, a failed
+// redraw); the event is then not applied.
+template <int K, bool PROD, class Capture>
+__device__ __forceinline__ bool general_draw(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                             const Threshold* thr, uint32_t (&n)[K],
+                                             uint32_t (&w)[4 * GeneralShape<K>::NC0], unsigned int& errors,
+                                             Capture&& capture) {
+  constexpr int NC0 = GeneralShape<K>::NC0;
   const PhiloxKey key{(uint32_t)e.seed, (uint32_t)(e.seed >> 32)};
   const int precision = p.precision;
-
   if (p.step_budget > 0 && (long long)s.step >= p.step_budget) {
     errors |= kErrTimeout;
     s.done = true;
-    return;
+    return false;
   }
   // (1) the random words of attempt 0; n, redrawn where it is at or above lambda_int
-  uint32_t w[4 * NC0];
   philox4x32_10_block<NC0>(w, stream_counter(s.sgroup, s.step, 0u, 0u, 0u), 0u, key);
-  uint32_t n[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) n[i] = w[i];
   // the paper's shared draw (Sec. 4, step a): lane 0's n, redrawn whether or not it is live
@@ -354,7 +402,7 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
   if (need && !redraw_n<K>(n, e, s.sgroup, s.step, need, key, s.redraws)) {
     errors |= kErrRedraw;
     s.done = true;
-    return;
+    return false;
   }
   if (e.shared_n) {
 #pragma unroll
@@ -367,23 +415,77 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
   while (crossed) {
     if (s.snap >= p.n_snap) {  // t_end passed: the event is not applied
       s.done = true;
-      return;
+      return false;
     }
-    general_capture<K, PROD>(p, s, e, s.snap, c, s_hist);
+    capture(s.snap);
     ++s.snap;
     nx.aim(thr[s.snap]);
     if constexpr (PROD) crossed = clock_crosses(nx);
     else crossed = clock_crosses(nx, precision);
   }
   s.clk = nx;
+  return true;
+}
 
-  // (3) the CDF walk over the reactions in order: S = sum_{p<=r} h_p, xi_r = [S_{r-1} <= n < S_r]
+// Step (4) of a group step: thinning of the reactions with k_r < k_max, for the first RN reactions
+// (xi beyond the network's R are zero): U (q bits, most significant first, from word K+2 of w
+// on, then further Philox calls of the step) < T_r keeps the event.
+template <int K, int RN, bool PROD>
+__device__ __forceinline__ void general_thin(uint32_t (&xi)[RN], const uint32_t (&w)[4 * GeneralShape<K>::NC0],
+                                             const Ensemble& e, const GeneralState<PROD>& s) {
+  if (!e.thin) return;
+  constexpr int NC0 = GeneralShape<K>::NC0;
+  const PhiloxKey key{(uint32_t)e.seed, (uint32_t)(e.seed >> 32)};
+  uint32_t tested = 0u;
+#pragma unroll
+  for (int r = 0; r < RN; ++r)
+    if (!((e.thin_always >> r) & 1u)) tested |= xi[r];
+  uint32_t und = tested & s.live, rej = tested & ~s.live;
+  const int q = e.thin_bits;
+  auto bit = [&](int i, uint32_t word) {
+    const int pos = q - 1 - i;
+    uint32_t tb = 0u;
+#pragma unroll
+    for (int r = 0; r < RN; ++r)
+      if ((((unsigned long long)e.thin_T[r] >> pos) & 1ull) != 0ull) tb |= xi[r];
+    const uint32_t lower = und & ~word & tb;
+    const uint32_t higher = und & word & ~tb;
+    rej |= higher;
+    und &= ~(lower | higher);
+  };
+  int i = 0;
+#pragma unroll
+  for (int k = K + 2; k < 4 * NC0; ++k)
+    if (k - (K + 2) < q) bit(i++, w[k]);
+  for (uint32_t call = NC0; und != 0u && i < q; ++call) {
+    const uint4 rw = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, call), key);
+    const uint32_t wv[4] = {rw.x, rw.y, rw.z, rw.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (i < q) bit(i++, wv[j]);
+  }
+  rej |= und;  // U == T: not below
+#pragma unroll
+  for (int r = 0; r < RN; ++r) xi[r] &= ~rej;
+}
+
+// One group step (see the file header).
+template <int K, bool PROD>
+__device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                             const Threshold* thr, const CountPlanes& c, unsigned int* s_hist,
+                                             unsigned int& errors) {
+  using Sh = GeneralShape<K>;
+  const Network& net = p.net;
+  const int B = count_planes(e);
+  uint32_t n[K], w[4 * Sh::NC0];
+  if (!general_draw<K, PROD>(p, s, e, thr, n, w, errors,
+                             [&](int snap) { general_capture<K, PROD>(p, s, e, snap, c, s_hist); }))
+    return;
+
+  // (3) the CDF walk over the reactions in order: xi_r = [S_{r-1} <= n < S_r], S_r = sum_{p<=r} h_p,
+  // as the borrow of n - S_{r-1} - h_r
   uint32_t xi[kMaxReactions];
   {
-    uint32_t S[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) S[i] = 0u;
-    uint32_t lt_prev = 0u;
 #pragma unroll 1
     for (int r = 0; r < net.R; ++r) {
       uint32_t h[K];
@@ -393,10 +495,7 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
       } else {
         general_propensity<K>(h, net, r, c, B);
       }
-      bs::add_signed(S, h, 0u);
-      const uint32_t lt = bs::less_than(n, S);
-      const uint32_t x = lt & ~lt_prev;
-      lt_prev = lt;
+      const uint32_t x = sub_borrow(n, h);
       // (a run-time r cannot index a register array: place x by an unrolled compare)
 #pragma unroll
       for (int q = 0; q < kMaxReactions; ++q)
@@ -407,40 +506,8 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
       if (q >= net.R) xi[q] = 0u;
   }
 
-  // (4) thinning for k_r < k_max: U (q bits, most significant first, from word K+2 on) < T_r
-  if (e.thin) {
-    uint32_t tested = 0u;
-#pragma unroll
-    for (int r = 0; r < kMaxReactions; ++r)
-      if (!((e.thin_always >> r) & 1u)) tested |= xi[r];
-    uint32_t und = tested & s.live, rej = tested & ~s.live;
-    const int q = e.thin_bits;
-    auto bit = [&](int i, uint32_t word) {
-      const int pos = q - 1 - i;
-      uint32_t tb = 0u;
-#pragma unroll
-      for (int r = 0; r < kMaxReactions; ++r)
-        if ((((unsigned long long)e.thin_T[r] >> pos) & 1ull) != 0ull) tb |= xi[r];
-      const uint32_t lower = und & ~word & tb;
-      const uint32_t higher = und & word & ~tb;
-      rej |= higher;
-      und &= ~(lower | higher);
-    };
-    int i = 0;
-#pragma unroll
-    for (int k = K + 2; k < 4 * NC0; ++k)
-      if (k - (K + 2) < q) bit(i++, w[k]);
-    for (uint32_t call = NC0; und != 0u && i < q; ++call) {
-      const uint4 rw = philox4x32_10(stream_counter(s.sgroup, s.step, 0u, 0u, call), key);
-      const uint32_t wv[4] = {rw.x, rw.y, rw.z, rw.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (i < q) bit(i++, wv[j]);
-    }
-    rej |= und;  // U == T: not below
-#pragma unroll
-    for (int r = 0; r < kMaxReactions; ++r) xi[r] &= ~rej;
-  }
+  // (4) thinning for k_r < k_max
+  general_thin<K>(xi, w, e, s);
 
   // (5) the counts: x_s += sum_r xi_r nu_rs (nu in [-2, 2]: three two's-complement planes)
   uint32_t fired = 0u;
@@ -492,7 +559,7 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
   const uint32_t now_live = general_live<K>(net, e, c) & s.live;
   uint32_t newly = s.live & ~now_live;
   if (newly) {
-    const double tn = s.clk.time(e, precision);
+    const double tn = s.clk.time(e, p.precision);
     s.lane_steps += (unsigned long long)__popc(newly) * s.step;
     const long long row0 = general_row0(s.sgroup, e);
     while (newly) {
@@ -509,18 +576,18 @@ __device__ __forceinline__ void general_step(const FrankLaunch& p, GeneralState<
 }
 
 // Outputs of a finished group: final counts, outcomes, per-ensemble tallies, counters.
-template <int K, bool PROD>
-__device__ __forceinline__ void general_finish(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
-                                               const CountPlanes& c) {
+// count(s, l) reads species s of lane l.
+template <bool PROD, class Count>
+__device__ __forceinline__ void finish_counts(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                              Count&& count) {
   const Network& net = p.net;
-  const int B = count_planes(e);
   unsigned long long outc[4] = {0, 0, 0, 0};
   const long long row0 = general_row0(s.sgroup, e);
   for (int l = 0; l < s.nvalid; ++l) {
     int* o = p.final_counts + (row0 + l) * net.S;
     int nz = 0, who = -1;
     for (int sp = 0; sp < net.S; ++sp) {
-      const int v = lane_count(c, sp, B, l);
+      const int v = count(sp, l);
       o[sp] = v;
       if (v) {
         ++nz;
@@ -553,16 +620,23 @@ __device__ __forceinline__ void general_finish(const FrankLaunch& p, GeneralStat
   atomicMax(&p.counters[kMaxGroupSteps], s.step);
 }
 
+template <int K, bool PROD>
+__device__ __forceinline__ void general_finish(const FrankLaunch& p, GeneralState<PROD>& s, const Ensemble& e,
+                                               const CountPlanes& c) {
+  const int B = count_planes(e);
+  finish_counts(p, s, e, [&](int sp, int l) { return lane_count(c, sp, B, l); });
+}
+
 // Planes stored per species: enough for the products' reads and for the counts themselves.
 __host__ __device__ constexpr int general_planes(int BM, int B) { return BM > B ? BM : B; }
 
-// The persistent kernel: the queue, warp-synchronous loop and histogram handling of the
-// Frank kernel.  Dynamic shared memory: the histogram (single ensemble), the count planes of
-// every thread of the block, the scratch words of every thread, and in incremental mode the K
-// planes of every h_r of every thread.
-template <int K, bool BATCH, bool PROD>
-__global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ FrankLaunch p) {
-  extern __shared__ unsigned int s_mem[];
+// The persistent loop of the general kernels: the queue, warp-synchronous loop and histogram
+// handling of the Frank kernel.  init(s, e, thr, group, ens, s_hist) sets up a group,
+// step(s, e, thr, s_hist, errors) runs one step, finish(s, e) writes a finished group's outputs.
+// The histogram (single ensemble) is the first n_snap * 65 words of the dynamic shared memory.
+template <bool BATCH, bool PROD, class Init, class Step, class Finish>
+__device__ __forceinline__ void general_queue(const FrankLaunch& p, unsigned int* s_mem, Init&& init, Step&& step,
+                                              Finish&& finish) {
   const bool smem_hist = !BATCH && p.n_snap > 0;
   unsigned int* s_hist = smem_hist ? s_mem : nullptr;
   const int hist_words = smem_hist ? p.n_snap * kHistBins : 0;
@@ -570,12 +644,6 @@ __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ Fr
     for (int i = threadIdx.x; i < hist_words; i += blockDim.x) s_mem[i] = 0u;
     __syncthreads();
   }
-  const int planes = general_planes(GeneralShape<K>::BM, p.net.B);
-  const int count_words = p.net.S * planes, h_words = p.net.incremental ? p.net.R * K : 0;
-  uint32_t* const warp_base = s_mem + hist_words + (threadIdx.x >> 5) * 32 * (count_words + kGeneralScratch + h_words) +
-                              (threadIdx.x & 31);
-  const CountPlanes c{warp_base, warp_base + 32 * count_words, warp_base + 32 * (count_words + kGeneralScratch),
-                      planes, K};
   unsigned int errors = 0u;
   GeneralState<PROD> s;
   s.done = true;
@@ -587,21 +655,21 @@ __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ Fr
       if (item >= p.item_end) {
         exhausted = true;
       } else if (!BATCH) {
-        general_init<K, PROD>(p, s, p.ens, thr, item, 0, c, s_hist);
+        init(s, p.ens, thr, item, 0, s_hist);
         active = true;
       } else {
         const int ei = p.item_ens[item];
         thr = p.thr + (long long)ei * (p.n_snap + 1);
-        general_init<K, PROD>(p, s, p.ens_table[ei], thr, p.item_group[item], ei, c, nullptr);
+        init(s, p.ens_table[ei], thr, (long long)p.item_group[item], ei, (unsigned int*)nullptr);
         active = true;
       }
     }
     if (__all_sync(0xFFFFFFFFu, exhausted && !active)) break;
     if (active) {
       const Ensemble& e = BATCH ? p.ens_table[s.ens] : p.ens;
-      if (!s.done) general_step<K, PROD>(p, s, e, thr, c, s_hist, errors);
+      if (!s.done) step(s, e, thr, s_hist, errors);
       if (s.done) {
-        general_finish<K, PROD>(p, s, e, c);
+        finish(s, e);
         active = false;
       }
     }
@@ -614,6 +682,28 @@ __global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ Fr
     for (int i = threadIdx.x; i < hist_words; i += blockDim.x)
       if (s_mem[i]) atomicAdd(&p.hist[i], (unsigned long long)s_mem[i]);
   }
+}
+
+// The general kernel with its planes in shared memory.  Dynamic shared memory: the histogram
+// (single ensemble), the count planes of every thread of the block, the scratch words of every
+// thread, and in incremental mode the K planes of every h_r of every thread.
+template <int K, bool BATCH, bool PROD>
+__global__ void __launch_bounds__(256) general_kernel(const __grid_constant__ FrankLaunch p) {
+  extern __shared__ unsigned int s_mem[];
+  const int hist_words = (!BATCH && p.n_snap > 0) ? p.n_snap * kHistBins : 0;
+  const int planes = general_planes(GeneralShape<K>::BM, p.net.B);
+  const int count_words = p.net.S * planes, h_words = p.net.incremental ? p.net.R * K : 0;
+  uint32_t* const warp_base = s_mem + hist_words + (threadIdx.x >> 5) * 32 * (count_words + kGeneralScratch + h_words) +
+                              (threadIdx.x & 31);
+  const CountPlanes c{warp_base, warp_base + 32 * count_words, warp_base + 32 * (count_words + kGeneralScratch),
+                      planes, K};
+  general_queue<BATCH, PROD>(
+      p, s_mem,
+      [&](GeneralState<PROD>& s, const Ensemble& e, const Threshold* thr, long long group, int ens,
+          unsigned int* s_hist) { general_init<K, PROD>(p, s, e, thr, group, ens, c, s_hist); },
+      [&](GeneralState<PROD>& s, const Ensemble& e, const Threshold* thr, unsigned int* s_hist,
+          unsigned int& errors) { general_step<K, PROD>(p, s, e, thr, c, s_hist, errors); },
+      [&](GeneralState<PROD>& s, const Ensemble& e) { general_finish<K, PROD>(p, s, e, c); });
 }
 
 }  // namespace bitssa

@@ -39,6 +39,10 @@ constexpr int kMaxSpecies = 8;   // general networks: species
 constexpr int kMaxReactions = 8; // general networks: reactions
 constexpr int kMaxCountPlanes = 17;  // counts up to N_tot = 65536
 constexpr int kGeneralScratch = 5 * kMaxSpecies;  // general kernel: scratch words per thread
+// general networks whose count planes and propensities a thread keeps in registers
+constexpr int kRegSpecies = 4;    // species
+constexpr int kRegReactions = 4;  // reactions
+constexpr int kRegMaxK = 22;      // propensity planes (larger K stays in shared memory)
 
 // Clock precision modes (same values as SSA_P64 ... in bitssa.h).
 enum Precision { kP64 = 0, kP32Kahan = 1, kP32D64Acc = 2, kP64LogSum = 3, kP32Plain = 4 };
@@ -61,6 +65,7 @@ enum Counter {
 constexpr int kLayoutGeneralIncremental = 4;
 constexpr int kLayoutGeneralProducts = 8;
 constexpr int kLayoutTail = 16;  // set by the device: some groups were finished one run per thread
+constexpr int kLayoutGeneralRegisters = 32;  // the general kernel kept its planes in registers
 
 // Error flags (OR-ed into the status word).
 enum ErrorFlag : uint32_t {
@@ -137,6 +142,7 @@ struct Network {
   unsigned int changes;              // bit s: some reaction changes species s
   int hist_x, hist_y;                // species binned by the ee histogram (x: "L", y: "D")
   int incremental;                   // 1: keep h_r and add its change every step; 0: products every step
+  int regs;                          // 1: count planes and h_r in registers (general_reg_kernel)
 };
 
 // Per-ensemble constants of a general network from their definitions: lambda_int =

@@ -396,7 +396,7 @@ int check_options(const ssa_options& o, std::string* why) {
   if (o.pad_pow2 == 2 && (o.engine == SSA_ENGINE_GENERAL || o.layout == SSA_LAYOUT_WARPS || o.shared_n))
     return (*why = "the state-following bound (pad_pow2 = 2) runs Frank's model on one thread per group",
             SSA_EUNSUPPORTED);
-  if (o.recompute < 0 || o.recompute > 2) return (*why = "recompute must be 0, 1 or 2", SSA_EINVAL);
+  if (o.recompute < 0 || o.recompute > 3) return (*why = "recompute must be 0, 1, 2 or 3", SSA_EINVAL);
   if (o.pad_pow2 && o.engine == SSA_ENGINE_THREAD_PER_RUN)
     return (*why = "pad_pow2 is a mode of the bit-sliced engines", SSA_EUNSUPPORTED);
   if (o.thin_bits < 1 || o.thin_bits > 64) return (*why = "thin_bits must be in [1, 64]", SSA_EINVAL);
@@ -620,11 +620,25 @@ bool ctx_warps(const ssa_ctx* c, long long groups) {
 
 // Shared memory of the general kernel per block, histogram excluded: the count planes of every
 // thread ([species][plane][thread] words; enough planes for the products at K), the scratch
-// words, and in incremental mode the K planes of every propensity.
-int general_smem(const ssa_ctx* c, int K, int block) {
+// words, and in incremental mode the K planes of every propensity; none with the planes in
+// registers.
+int general_smem(const ssa_ctx* c, int K, int block, bool regs) {
+  if (regs) return 0;
   const int BM = bit_length(frank_nmax(K));
   const int words = c->net.S * std::max(BM, c->net.B) + kGeneralScratch + (c->net.incremental ? c->net.R * K : 0);
   return words * block * (int)sizeof(uint32_t);
+}
+
+// Whether the general kernel's launch at K keeps its count planes and propensities in registers:
+// incremental mode not fixed to shared memory (recompute = 3), at most kRegSpecies species and
+// kRegReactions reactions, K at most kRegMaxK, and the counts of every ensemble at that K inside
+// the planes the products read (always so with a reaction of order 2).
+bool general_in_registers(const ssa_ctx* c, int K) {
+  if (!c->net.incremental || c->opt.recompute == 3) return false;
+  if (c->net.S > kRegSpecies || c->net.R > kRegReactions || K > kRegMaxK) return false;
+  for (const Ensemble& e : c->ens)
+    if (std::max(1, e.K) == K && bit_length(e.n_tot) > bit_length(frank_nmax(K))) return false;
+  return true;
 }
 
 // Launches of the general-network kernel: one for a single ensemble, one per K bucket (on the
@@ -632,15 +646,19 @@ int general_smem(const ssa_ctx* c, int K, int block) {
 int launch_general(ssa_ctx* c, FrankLaunch fl, int block, int clock_variant) {
   cudaError_t e;
   // the propensity mode: a fixed option wins, then the tuner's choice, then incremental
-  c->net.incremental = c->opt.recompute == 1 ? 0 : (c->opt.recompute == 2 ? 1 : (c->tuned_products == 1 ? 0 : 1));
+  c->net.incremental = c->opt.recompute == 1 ? 0 : (c->opt.recompute >= 2 ? 1 : (c->tuned_products == 1 ? 0 : 1));
+  c->net.regs = 0;
   fl.net = c->net;
   const int hist_smem = c->batch ? 0 : c->n_snap * kHistBins * (int)sizeof(unsigned int);
   c->layout_used = SSA_LAYOUT_THREAD | (c->net.incremental ? kLayoutGeneralIncremental : kLayoutGeneralProducts);
   if (!c->batch) {
     const int K = std::max(1, c->ens[0].K);
-    const int smem = hist_smem + general_smem(c, K, block);
+    const bool regs = general_in_registers(c, K);
+    fl.net.regs = regs ? 1 : 0;
+    if (regs) c->layout_used |= kLayoutGeneralRegisters;
+    const int smem = hist_smem + general_smem(c, K, block, regs);
     int occ = 0;
-    if (general_max_active_blocks(K, clock_variant, block, smem, &occ) != 0 || occ < 1)
+    if (general_max_active_blocks(K, clock_variant | (regs ? 4 : 0), block, smem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the general bit-sliced kernel (shared memory " +
                                     std::to_string(smem) + " bytes per block)");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;
@@ -666,14 +684,17 @@ int launch_general(ssa_ctx* c, FrankLaunch fl, int block, int clock_variant) {
     b.K = std::max(1, c->ranges[r].first);
     b.general = 1;
     b.block = block;
-    b.smem = general_smem(c, b.K, block);
+    const bool regs = general_in_registers(c, b.K);
+    if (regs) c->layout_used |= kLayoutGeneralRegisters;
+    b.smem = general_smem(c, b.K, block, regs);
     b.stream = (int)(r % c->side.size());
     b.fl = fl;
+    b.fl.net.regs = regs ? 1 : 0;
     b.fl.item_begin = c->ranges[r].second.first;
     b.fl.item_end = c->ranges[r].second.second;
     b.fl.queue = c->d_counters + kCounters + 1 + r;
     int occ = 0;
-    if (general_max_active_blocks(b.K, clock_variant | 1, block, b.smem, &occ) != 0 || occ < 1)
+    if (general_max_active_blocks(b.K, clock_variant | 1 | (regs ? 4 : 0), block, b.smem, &occ) != 0 || occ < 1)
       return fail(c, SSA_ECUDA, "occupancy query failed for the general bit-sliced kernel (shared memory " +
                                     std::to_string(b.smem) + " bytes per block)");
     const int bpsm = c->opt.blocks_per_sm ? std::min(c->opt.blocks_per_sm, occ) : occ;

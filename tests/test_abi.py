@@ -105,7 +105,7 @@ F_R, F_P = pkg.FRANK_REACTANTS, pkg.FRANK_PRODUCTS
      pkg.SSA_EUNSUPPORTED),                                                           # general: one layout
     (dict(reac=F_R, prod=F_P, engine=pkg.SSA_ENGINE_GENERAL, layout=pkg.SSA_LAYOUT_WARPS), pkg.SSA_EUNSUPPORTED),
     (dict(reac=F_R, prod=F_P, engine=3), pkg.SSA_EINVAL),
-    (dict(reac=F_R, prod=F_P, recompute=3), pkg.SSA_EINVAL),
+    (dict(reac=F_R, prod=F_P, recompute=4), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, clock=2), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, word_width=16), pkg.SSA_EINVAL),
     (dict(reac=F_R, prod=F_P, word_width=64), pkg.SSA_EUNSUPPORTED),

@@ -53,6 +53,16 @@ def _oracle_net(reac, prod, rates):
     return oracle.Network(reac, prod, rates)
 
 
+def _layout(reac, recompute):
+    """The layout word the general kernel reports: incremented (4) or recomputed (8) propensities,
+    and the planes in registers (32) for incremental mode on a network of at most 4 species and 4
+    reactions with a reaction of order 2 (its counts then fit the planes the products read)."""
+    if recompute == 1:
+        return pkg.SSA_LAYOUT_THREAD | 8
+    small = len(reac) <= 4 and len(reac[0]) <= 4 and max(sum(r) for r in reac) == 2
+    return pkg.SSA_LAYOUT_THREAD | 4 | (32 if small and recompute != 3 else 0)
+
+
 def _check(g, r, S, snaps):
     ok = assert_parity(g, r)
     assert np.all(g["final_counts"].sum(1) == r["final_counts"].sum(1))
@@ -65,10 +75,11 @@ def _check(g, r, S, snaps):
 
 
 @pytest.mark.parametrize("name", sorted(NETWORKS))
-@pytest.mark.parametrize("pad,recompute", [(0, 0), (1, 0), (0, 1), (1, 1), (1, 2)])
+@pytest.mark.parametrize("pad,recompute", [(0, 0), (1, 0), (0, 1), (1, 1), (1, 2), (0, 3), (1, 3)])
 def test_general_network_parity(name, pad, recompute):
     """Every run, snapshot and histogram, 3 groups and a ragged tail, against the oracle, with the
-    propensities kept and incremented (default) or recomputed by products every step."""
+    propensities kept and incremented (default; planes in registers where the network fits, in
+    shared memory with recompute = 3) or recomputed by products every step."""
     reac, prod, rates, init, t_end = NETWORKS[name]
     S = len(init)
     snaps = [t_end / 10, t_end / 3, t_end / 2]
@@ -78,7 +89,7 @@ def test_general_network_parity(name, pad, recompute):
     r = oracle.run(_oracle_net(reac, prod, rates), init, n, seed=41, t_end=t_end, snap_times=snaps,
                    threads=THREADS, pad_pow2=bool(pad))
     _check(g, r, S, snaps)
-    assert g["counters"]["layout"] == pkg.SSA_LAYOUT_THREAD | (8 if recompute == 1 else 4)
+    assert g["counters"]["layout"] == _layout(reac, recompute)
     if pad:
         assert g["counters"]["redraw_rounds"] == 0
 
@@ -154,15 +165,16 @@ def test_general_batch_against_oracle():
         off += runs[e]
 
 
-@pytest.mark.parametrize("recompute", [0, 1])
+@pytest.mark.parametrize("recompute", [0, 1, 3])
 @pytest.mark.parametrize("init,n,rates,pad", [((16, 16, 32), 64, (1.0, 1.0, 1.0), 0),
                                               ((256, 256, 512), 4096 + 17, (1.0, 1.0, 1.0), 1),
                                               ((256, 256, 512), 2048, (0.7, 1.0, 1.6), 0),
                                               ((2500, 2500, 5000), 256, (1.0, 1.0, 1.0), 0)])
 def test_frank_on_general_kernel_equals_frank_kernel(init, n, rates, pad, recompute):
     """Frank's model through the general kernel gives Frank's kernel's runs bit for bit: the
-    same stream and rule, with the propensities incremented by the general rule or recomputed
-    by products instead of Frank's hand-derived increments."""
+    same stream and rule, with the propensities incremented by the general rule (planes in
+    registers up to K = 22, or in shared memory) or recomputed by products instead of Frank's
+    hand-derived increments."""
     N = sum(init)
     t_end = 50.0 if N <= 1024 else 3e-4
     snaps = log_snapshots(t_end, 6)
@@ -216,7 +228,7 @@ def test_tuner_picks_a_general_mode_and_keeps_the_runs():
         pkg.ssa_destroy(ctx)
     for k in ("final_counts", "outcome", "t_abs", "ee_hist", "snap_counts"):
         assert np.array_equal(before[k], after[k]), k
-    assert after["counters"]["layout"] in (pkg.SSA_LAYOUT_THREAD | 4, pkg.SSA_LAYOUT_THREAD | 8)
+    assert after["counters"]["layout"] in (pkg.SSA_LAYOUT_THREAD | 4 | 32, pkg.SSA_LAYOUT_THREAD | 8)
 
 
 @pytest.mark.parametrize("pad,recompute", [(0, 2), (1, 2), (1, 1)])
