@@ -109,9 +109,9 @@ def test_plain_fp32_sum_is_the_worse_control(runs):
 
 
 def test_fp32_batched_form_against_fp64():
-    """The batched form (the benchmark spec's FP32 batched form): 24 ensembles of the batched workload's
-    recipe (N_tot log-uniform, here in [16, 4096]; rates uniform in [0.5, 2]), 2048 runs each, in
-    one batch, fp32 Kahan clocks against fp64.  Same seeds: the same runs, times within fp32
+    """The FP32 batched form: 24 ensembles of the batched workload's recipe (N_tot log-uniform,
+    here in [16, 4096]; rates uniform in [0.5, 2]), 2048 runs each, in one batch, fp32 Kahan
+    clocks against fp64.  Same seeds: the same runs, times within fp32
     rounding.  Independent seeds: per ensemble the mean absorption time over group means (the
     groups are independent) as a z-score; their squares sum to a chi-square with 24 degrees."""
     import torch
