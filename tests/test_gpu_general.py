@@ -94,6 +94,24 @@ def test_general_network_parity(name, pad, recompute):
         assert g["counters"]["redraw_rounds"] == 0
 
 
+@pytest.mark.parametrize("N,regs", [(1700, True), (2500, False)])
+def test_general_register_plane_limit(N, regs):
+    """Moran at N_tot = 1700 (lambda_int = N (N - 1) has K = 22 planes, the most a thread keeps in
+    registers) and 2500 (K = 23, shared memory): every run and snapshot against the oracle, and
+    the layout bit of the mode that ran."""
+    reac, prod, rates, _, _ = NETWORKS["moran"]
+    init = (N // 2, N - N // 2)
+    t_end = 2e-3
+    snaps = [t_end / 2]
+    n = 64 + 5
+    g = gpu_run(init, n, seed=23, t_end=t_end, snaps=snaps, rates=rates, reac=reac, prod=prod, pad_pow2=1)
+    r = oracle.run(_oracle_net(reac, prod, rates), init, n, seed=23, t_end=t_end, snap_times=snaps,
+                   threads=THREADS, pad_pow2=True)
+    _check(g, r, 2, snaps)
+    assert g["counters"]["layout"] == pkg.SSA_LAYOUT_THREAD | 4 | (32 if regs else 0)
+    assert g["counters"]["reactions"] > 0
+
+
 @pytest.mark.parametrize("name", ["moran", "sir", "four"])
 def test_general_per_run_initial_states(name):
     reac, prod, rates, init, t_end = NETWORKS[name]
